@@ -1,0 +1,214 @@
+"""Pins for the oracle's interaction sums.
+
+The cell-list result is pinned by O(N^2) brute force on small inputs (the
+definition of Sec. 2 with no grid), by closed forms (a single pair, the
+h -> infinity limit, a dyadic lattice), by the invariants of the method
+(symmetric neighbour relation, antisymmetric vector sums), and by the
+candidate counts the paper prints (Sec. 7.2 table).  CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_16091_gb300 import workloads as W
+
+
+def run(x, y, z, lo, hi, rc, h):
+    b = oracle.bin_particles(x, y, z, lo, hi, rc)
+    assert b.ok
+    r = oracle.interact(b, rc, h)
+    u = lambda a: oracle.unpermute(a, b.perm)
+    return b, r, (u(r.S), u(r.Vx), u(r.Vy), u(r.Vz), u(r.nbr))
+
+
+CASES = [
+    # (n, lo, hi, rc)
+    (1500, (0, 0, 0), (1, 1, 1), 0.125),
+    (2000, (-1.0, 0.5, 2.0), (1.0, 1.5, 2.25), 0.11),   # non-cubic, lo != 0, one cell in z
+    (800, (0, 0, 0), (1, 1, 1), 0.6),                    # one cell per axis
+    (1200, (0, 0, 0), (1, 1, 1), 0.34),                  # 2 cells per axis: every cell neighbours every other
+    (3000, (0, 0, 0), (2, 1, 0.5), 0.07),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_cell_list_equals_brute_force(case):
+    n, lo, hi, rc = case
+    x, y, z = W.uniform(n, 11 + n, lo, hi)
+    h = rc / 2
+    b, r, (S, Vx, Vy, Vz, nb) = run(x, y, z, lo, hi, rc, h)
+    bS, bVx, bVy, bVz, bnb = oracle.brute(x, y, z, rc, h)
+    assert np.array_equal(nb, bnb)
+    for a, ref in ((S, bS), (Vx, bVx), (Vy, bVy), (Vz, bVz)):
+        assert np.allclose(a, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_clustered_equals_brute_force():
+    w = W.scaled(W.CLUSTERED, 4000)
+    x, y, z = w.positions()
+    b, r, (S, Vx, Vy, Vz, nb) = run(x, y, z, w.lo, w.hi, w.rc, w.h)
+    bS, bVx, bVy, bVz, bnb = oracle.brute(x, y, z, w.rc, w.h)
+    assert np.array_equal(nb, bnb)
+    assert np.allclose(S, bS, rtol=1e-12) and np.allclose(Vx, bVx, rtol=1e-12, atol=1e-15)
+
+
+def test_single_pair_closed_form():
+    """Two particles at distance r < r_c: S = exp(-r^2/h^2) on both sides,
+    V_i = (p_j - p_i) K, V_j = -V_i; at distance >= r_c nothing."""
+    rc, h = 0.25, 0.125
+    pi = np.array([0.30, 0.40, 0.50], np.float32)
+    pj = np.array([0.40, 0.45, 0.375], np.float32)
+    d = pj.astype(np.float64) - pi.astype(np.float64)
+    K = math.exp(-float(d @ d) / (h * h))
+    _, _, (S, Vx, Vy, Vz, nb) = run([pi[0], pj[0]], [pi[1], pj[1]], [pi[2], pj[2]],
+                                    (0, 0, 0), (1, 1, 1), rc, h)
+    assert nb.tolist() == [1, 1]
+    assert S[0] == pytest.approx(K, rel=1e-15) and S[1] == pytest.approx(K, rel=1e-15)
+    assert Vx[0] == pytest.approx(d[0] * K, rel=1e-14)
+    assert Vy[0] == pytest.approx(d[1] * K, rel=1e-14)
+    assert Vz[0] == pytest.approx(d[2] * K, rel=1e-14)
+    assert (Vx[1], Vy[1], Vz[1]) == (-Vx[0], -Vy[0], -Vz[0])
+    far = np.float32(0.30 + 0.2501)
+    _, _, (S, Vx, _, _, nb) = run([0.30, far], [0.4, 0.4], [0.5, 0.5], (0, 0, 0), (1, 1, 1), rc, h)
+    assert nb.tolist() == [0, 0] and S.tolist() == [0.0, 0.0]
+
+
+def test_cutoff_is_strict():
+    """r_ij < r_c is strict (Sec. 2): a pair exactly r_c apart does not
+    interact; one a float step closer does."""
+    rc = 0.25
+    x0 = np.float32(0.5)
+    _, _, (_, _, _, _, nb) = run([x0, x0 + np.float32(rc)], [0.5, 0.5], [0.5, 0.5],
+                                 (0, 0, 0), (1, 1, 1), rc, 0.1)
+    assert nb.tolist() == [0, 0]
+    x1 = np.nextafter(x0 + np.float32(rc), np.float32(0))
+    _, _, (_, _, _, _, nb) = run([x0, x1], [0.5, 0.5], [0.5, 0.5], (0, 0, 0), (1, 1, 1), rc, 0.1)
+    assert nb.tolist() == [1, 1]
+
+
+def test_wide_kernel_limit():
+    """h -> infinity makes K = 1: S_i = n_i and V_i = sum_j p_j - n_i p_i."""
+    w = W.scaled(W.SMALL, 3000)
+    x, y, z = w.positions()
+    _, _, (S, Vx, Vy, Vz, nb) = run(x, y, z, w.lo, w.hi, w.rc, 1e30)
+    assert np.array_equal(S, nb.astype(np.float64))
+    # the n_i partners of i are its n_i nearest other particles
+    pos = np.stack([x, y, z], 1).astype(np.float64)
+    rng = np.random.default_rng(5)
+    for i in rng.choice(len(x), 50, replace=False):
+        js = np.argsort(((pos - pos[i]) ** 2).sum(1), kind="stable")
+        js = js[js != i][:nb[i]]
+        expect = pos[js].sum(0) - nb[i] * pos[i]
+        got = np.array([Vx[i], Vy[i], Vz[i]])
+        assert np.allclose(got, expect, rtol=1e-12, atol=1e-14)
+
+
+def test_antisymmetry_and_symmetry():
+    """Each pair is counted once from each side: sum n_i is even, the
+    relation is symmetric, sum_i V_i = 0 to FP64 rounding, and
+    sum_i S_i = 2 sum_{i<j} K_ij."""
+    w = W.scaled(W.SMALL, 6000)
+    x, y, z = w.positions()
+    b, r, (S, Vx, Vy, Vz, nb) = run(x, y, z, w.lo, w.hi, w.rc, w.h)
+    assert int(nb.sum()) % 2 == 0
+    for V, A in ((r.Vx, r.absVx), (r.Vy, r.absVy), (r.Vz, r.absVz)):
+        assert abs(V.sum()) <= 1e-13 * A.sum()
+    # explicit unordered sum over pairs, i < j, with the same predicate
+    P = np.stack([x, y, z], 1)
+    tot = 0.0
+    for i in range(len(x)):
+        d = (P[i + 1:] - P[i]).astype(np.float32)
+        r2 = (d[:, 0] * d[:, 0]).astype(np.float32)
+        r2 = (r2 + d[:, 1] * d[:, 1]).astype(np.float32)
+        r2 = (r2 + d[:, 2] * d[:, 2]).astype(np.float32)
+        # keep clear of the 1-ulp band where fma and non-fma r2 could differ
+        sel = r2 < np.float32(w.rc) * np.float32(w.rc) * np.float32(0.999)
+        dd = P[i + 1:][sel].astype(np.float64) - P[i].astype(np.float64)
+        tot += np.exp(-(dd ** 2).sum(1) / (w.h * w.h)).sum()
+    # pairs in the excluded band contribute at most its count * exp(-0.999*4)
+    band = int(nb.sum()) // 2
+    assert S.sum() >= 2 * tot * (1 - 1e-12)
+    assert S.sum() - 2 * tot <= 2 * band * math.exp(-0.999 * 4.0)
+
+
+def test_dyadic_lattice_closed_form():
+    """Simple cubic lattice, spacing a = 1/16, points at (i + 1/2) a.  With
+    a < r_c < a*sqrt(2) each point interacts with its axis neighbours only:
+    n = 6 inside, fewer on the faces; S = n exp(-a^2/h^2); V = 0 inside."""
+    m = 16
+    a = 1.0 / m
+    g = ((np.arange(m) + 0.5) / m).astype(np.float32)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    x, y, z = X.ravel(), Y.ravel(), Z.ravel()
+    rc, h = 1.2 * a, 0.5 * a
+    _, _, (S, Vx, Vy, Vz, nb) = run(x, y, z, (0, 0, 0), (1, 1, 1), rc, h)
+    ix, iy, iz = (np.rint(v * m - 0.5).astype(int) for v in (x, y, z))
+    expect = sum(((i > 0).astype(int) + (i < m - 1).astype(int)) for i in (ix, iy, iz))
+    assert np.array_equal(nb, expect)
+    K = math.exp(-(a * a) / (h * h))
+    assert np.allclose(S, expect * K, rtol=1e-14)
+    inner = (ix > 0) & (ix < m - 1) & (iy > 0) & (iy < m - 1) & (iz > 0) & (iz < m - 1)
+    assert np.all(Vx[inner] == 0) and np.all(Vy[inner] == 0) and np.all(Vz[inner] == 0)
+    # a face point misses the neighbour outside: V points inward with |V| = a K
+    face = (ix == 0) & (iy > 0) & (iy < m - 1) & (iz > 0) & (iz < m - 1)
+    assert np.allclose(Vx[face], a * K, rtol=1e-14)
+
+
+def test_coincident_particles_interact():
+    """Self-exclusion is by identity: k copies of one point see k-1
+    neighbours each with K = 1 and zero vector sum."""
+    k = 9
+    x = np.full(k, 0.3, np.float32)
+    _, _, (S, Vx, Vy, Vz, nb) = run(x, x, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05)
+    assert nb.tolist() == [k - 1] * k
+    assert S.tolist() == [float(k - 1)] * k
+    assert np.all(Vx == 0) and np.all(Vy == 0) and np.all(Vz == 0)
+
+
+def test_empty_and_lonely():
+    b = oracle.bin_particles([], [], [], (0, 0, 0), (1, 1, 1), 0.1)
+    r = oracle.interact(b, 0.1, 0.05)
+    assert len(r.S) == 0 and r.candidates == 0
+    _, r, (S, *_ , nb) = run([0.5], [0.5], [0.5], (0, 0, 0), (1, 1, 1), 0.1, 0.05)
+    assert nb.tolist() == [0] and S.tolist() == [0.0]
+
+
+def test_exact_occupancy_candidate_count():
+    """With exactly m particles in every cell of a d^3 grid, the clipped
+    27-stencil holds (3d-2)^3 m^2 - m d^3 ordered candidate pairs in total
+    (per axis the clipped neighbour counts sum to 3d - 2)."""
+    for d, m in ((5, 3), (8, 1), (3, 7)):
+        rng = np.random.default_rng(d * 10 + m)
+        cells = np.stack(np.meshgrid(*[np.arange(d)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        cells = np.repeat(cells, m, axis=0)
+        p = ((cells + rng.uniform(0.05, 0.95, cells.shape)) / d).astype(np.float32)
+        b = oracle.bin_particles(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), W.rc_for_cells(d))
+        assert b.dims == (d, d, d) and np.all(b.counts == m)
+        r = oracle.interact(b, W.rc_for_cells(d), 0.05)
+        assert r.candidates == (3 * d - 2) ** 3 * m * m - m * d ** 3
+
+
+def test_paper_candidates_per_particle(golden_dir):
+    """The 'interactions per particle' column of the Sec. 7.2 table is the
+    mean number of other particles in the clipped 27-cell stencil.  With
+    d = 2 every cell neighbours every other, so it is exactly N - 1; for the
+    larger uniform cases our seeded draw lands within sampling noise (2 %)."""
+    rows = json.load(open(os.path.join(golden_dir, "paper_candidates_per_particle.json")))["rows"]
+    for row in rows:
+        d, m, v = row["d"], row["m"], row["value"]
+        n = m * d ** 3
+        if n > 400_000:
+            continue
+        x, y, z = W.uniform(n, 7)
+        rc = W.rc_for_cells(d)
+        b = oracle.bin_particles(x, y, z, (0, 0, 0), (1, 1, 1), rc)
+        r = oracle.interact(b, rc, rc / 2)
+        per = r.candidates / n
+        if d == 2:
+            assert per == n - 1 == v
+        elif n >= 5000:
+            assert abs(per / v - 1) < 0.02, (d, m, per, v)
