@@ -1,0 +1,188 @@
+/*
+ * pi.h -- C ABI of libpi: cutoff-radius pair interactions on a regular cell
+ * grid, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of arXiv 2406.16091 (Algis, Bramas, Darles, Aveneau):
+ *   Sec. 2  bin the particles -- cell index of each particle from its
+ *           position, per-cell count with atomics, exclusive prefix sum over
+ *           the counts (Fig. 1: C+1 offsets, the last one N), scatter into
+ *           cell-sorted structure-of-arrays copies -- then, for every
+ *           particle i, sum a kernel K(r_ij) over all j != i with
+ *           r_ij < r_c found in its own cell and the 26 neighbouring cells.
+ *   Sec. 3  the cell width is at least r_c; inputs are positions, the
+ *           per-cell counts and start offsets; outputs are per-particle
+ *           values in SoA form.
+ *
+ * Conventions for every call:
+ *   - Device pointers are plain CUDA device addresses of the device that was
+ *     current when the context was created.  Host pointers are marked so.
+ *   - Every call is asynchronous on the given stream unless it says it
+ *     synchronises; a NULL stream is the legacy default stream.
+ *   - Calls return a pi_status.  Argument errors are detected on the host
+ *     and returned at once, with nothing enqueued.  Errors found by the GPU
+ *     (a position outside the box, a device-side wait that ran out) are kept
+ *     in a device error word and returned by pi_sync_status(); after such an
+ *     error the outputs of the failed step are undefined, and the library
+ *     stays usable (the next pi_bin clears the word).
+ *   - Nothing aborts, nothing throws across the ABI, no device wait is
+ *     unbounded.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef PI_H
+#define PI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque, library-owned.  Holds the grid and every device buffer binning needs. */
+typedef struct pi_ctx pi_ctx;
+
+/* A CUDA stream handle (identical to cudaStream_t / CUstream). */
+typedef struct CUstream_st* pi_stream;
+
+/* Simulation box: half-open [lo, hi) per axis, not periodic (Alg. 5 clips
+ * the neighbour range with Max(0, .) and Min(limit, .)). */
+typedef struct {
+    float lo[3];
+    float hi[3];
+} pi_box;
+
+typedef enum {
+    PI_OK = 0,
+    PI_ERR_INVALID_ARG = 1, /* bad argument, detected on the host */
+    PI_ERR_CAPACITY = 2,    /* n > n_max, or an internal size limit */
+    PI_ERR_OUT_OF_BOX = 3,  /* some position outside [lo, hi) or NaN (device) */
+    PI_ERR_NOT_BINNED = 4,  /* pi_interact before a successful pi_bin */
+    PI_ERR_CUDA = 5,        /* a CUDA runtime call failed; see pi_last_error() */
+    PI_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (device) */
+    PI_ERR_NOMEM = 7        /* device allocation failed */
+} pi_status;
+
+/* Output order of pi_interact. */
+enum {
+    PI_ORDER_SORTED = 0,   /* out[k] belongs to the particle in sorted slot k */
+    PI_ORDER_ORIGINAL = 1  /* out[i] belongs to input particle i */
+};
+
+/* Keys of pi_set_option(). */
+enum {
+    /* Interaction algorithm.  PI_ALGO_TILED (default) stages neighbour X-rows
+     * of cells in shared memory; PI_ALGO_PPNL is Alg. 1 of the paper
+     * (Par-Part-NoLoop: one thread per particle, sources read from global
+     * memory), kept as the in-library comparator. */
+    PI_OPT_ALGO = 1,
+    /* Accumulation: PI_PREC_FP32 (default) plain FP32 sums; PI_PREC_KAHAN
+     * compensated FP32 sums per particle and output. */
+    PI_OPT_PRECISION = 2,
+    /* Upper bound, in nanoseconds, of every device-side wait (default 1e9). */
+    PI_OPT_WAIT_LIMIT_NS = 3,
+    /* Test hook for the failure path: when 1, the first tile of the scan
+     * never publishes its prefix, so the other tiles' bounded waits run out
+     * and pi_sync_status() returns PI_ERR_TIMEOUT.  Default 0. */
+    PI_OPT_TEST_WITHHOLD_SCAN = 4
+};
+enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
+enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
+
+/* Creates a context on the current CUDA device for boxes of the given shape.
+ *   box   host pointer; lo < hi on every axis, all finite.
+ *   r_c   cutoff radius > 0.  Cells per axis n_d = max(1, floor((hi_d -
+ *         lo_d) / r_c)) computed in FP64, so every cell is at least r_c wide
+ *         (Sec. 3); C = nx*ny*nz must stay below 2^31.
+ *   n_max largest particle count a later pi_bin may pass, 0 <= n_max < 2^31 - 64.
+ *   out   receives the context; the caller owns it and frees it with pi_destroy.
+ * Allocates all device buffers once (about 28 B per particle + 8 B per cell).
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA. */
+pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out);
+
+/* Frees the context and its device buffers (synchronises the device first).
+ * NULL is accepted. */
+pi_status pi_destroy(pi_ctx* ctx);
+
+/* Binning (Sec. 2, Fig. 1).  x, y, z: device arrays of n FP32 positions
+ * (SoA, caller-owned, read only).  0 <= n <= n_max; n = 0 is a valid no-op
+ * that leaves an empty grid.  Enqueues, on `stream`:
+ *   a1/a2  cell index of each particle, cell = cx + nx*(cy + ny*cz) with
+ *          c_d = clamp(floor((x_d - lo_d) * inv_w_d), 0, n_d - 1) in FP32,
+ *          and a warp-aggregated atomic count per cell;
+ *   a3     a single-pass exclusive scan (C+1 offsets, offsets[C] = n) that
+ *          also records M_C, the largest cell count (Sec. 5.1);
+ *   a4     a stable scatter: inside a cell, particles keep input order.
+ * Results stay in the context; read them with pi_binned().
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_CAPACITY (n > n_max), PI_ERR_CUDA; a
+ * position outside [lo, hi) is reported later as PI_ERR_OUT_OF_BOX. */
+pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
+                 pi_stream stream);
+
+/* Interaction (Sec. 2, Sec. 3) over the particles of the last pi_bin: for
+ * every particle i, with d_ij = p_j - p_i and the pair test done in FP32 as
+ * r2 = fma(dz,dz,fma(dy,dy,dx*dx)) < fl32(r_c*r_c):
+ *   nbr[i] = number of j != i passing the test,
+ *   S[i]   = sum_j K_ij,  K_ij = exp(-r_ij^2 / h^2),
+ *   V[i]   = sum_j d_ij K_ij   (Vx, Vy, Vz).
+ * S, Vx, Vy, Vz: device FP32 arrays of n entries (caller-owned, written).
+ * nbr: device uint32 array of n entries, or NULL to skip the counts.
+ * h > 0 and finite.  out_order: PI_ORDER_SORTED or PI_ORDER_ORIGINAL.
+ * Output arrays must not alias each other or the inputs of pi_bin.
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
+pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
+                      uint32_t* nbr, int out_order, pi_stream stream);
+
+/* End-to-end step through host memory: copies n positions from the host
+ * arrays hx, hy, hz into context-owned device buffers, runs pi_bin and
+ * pi_interact, copies the outputs back into the host arrays hS, hVx, hVy,
+ * hVz (and hnbr unless NULL), then synchronises `stream` and returns the
+ * step's status (device-side errors included).  Pinned host memory gives
+ * asynchronous copies; pageable memory works too.  The device staging
+ * buffers are allocated on the first call (n_max entries).
+ * Errors: those of pi_bin, pi_interact and pi_sync_status, PI_ERR_NOMEM. */
+pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
+                      int64_t n, float h, float* hS, float* hVx, float* hVy, float* hVz,
+                      uint32_t* hnbr, int out_order, pi_stream stream);
+
+/* Grid dimensions (nx, ny, nz) into dims (host array of 3). */
+pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3]);
+
+/* Borrowed device pointers to the binning results, valid until the next
+ * pi_bin or pi_destroy (any pointer argument may be NULL):
+ *   counts[C] particles per cell; offsets[C+1] start of each cell in sorted
+ *   order, offsets[C] = n; perm[n] input index of sorted slot k;
+ *   sx, sy, sz[n] positions in sorted order. */
+pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t** offsets,
+                    const uint32_t** perm, const float** sx, const float** sy,
+                    const float** sz);
+
+/* Copies the binning results of the last pi_bin into caller-owned device
+ * buffers, asynchronously on `stream` (any pointer may be NULL to skip it):
+ * counts[C], offsets[C+1] (uint32), perm[n] (uint32), sx, sy, sz[n] (FP32),
+ * with C and n as in pi_binned().  Errors: PI_ERR_INVALID_ARG,
+ * PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
+pi_status pi_copy_binned(const pi_ctx* ctx, uint32_t* counts, uint32_t* offsets, uint32_t* perm,
+                         float* sx, float* sy, float* sz, pi_stream stream);
+
+/* Synchronises `stream`, then returns the device-side status of the work
+ * enqueued so far (PI_ERR_TIMEOUT, PI_ERR_OUT_OF_BOX, PI_ERR_CAPACITY or
+ * PI_OK) and, if max_per_cell is not NULL, M_C of the last pi_bin. */
+pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell);
+
+/* Sets an option (keys PI_OPT_*).  Host-side only; takes effect for work
+ * enqueued afterwards.  Errors: PI_ERR_INVALID_ARG for an unknown key or value. */
+pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
+
+/* Number of kernels this context has launched since pi_create (host counter). */
+pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count);
+
+/* Static text for a status code. */
+const char* pi_status_str(pi_status s);
+
+/* Text of the last CUDA error seen by this host thread ("" if none). */
+const char* pi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PI_H */

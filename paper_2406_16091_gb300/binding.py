@@ -1,0 +1,189 @@
+"""Thin ctypes binding of libpi (include/pi.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as device pointers, streams as
+their CUDA handles, and every step of the path runs in libpi's kernels.  The
+library is loaded from the package directory; if it is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpi.so")
+
+# status codes (pi_status)
+PI_OK = 0
+PI_ERR_INVALID_ARG = 1
+PI_ERR_CAPACITY = 2
+PI_ERR_OUT_OF_BOX = 3
+PI_ERR_NOT_BINNED = 4
+PI_ERR_CUDA = 5
+PI_ERR_TIMEOUT = 6
+PI_ERR_NOMEM = 7
+
+PI_ORDER_SORTED = 0
+PI_ORDER_ORIGINAL = 1
+
+PI_OPT_ALGO = 1
+PI_OPT_PRECISION = 2
+PI_OPT_WAIT_LIMIT_NS = 3
+PI_OPT_TEST_WITHHOLD_SCAN = 4
+PI_ALGO_TILED = 0
+PI_ALGO_PPNL = 1
+PI_PREC_FP32 = 0
+PI_PREC_KAHAN = 1
+
+
+class PiBox(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
+
+
+class PiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {status_str(status)} ({status})"
+        extra = last_error()
+        if status == PI_ERR_CUDA and extra:
+            msg += f": {extra}"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def load():
+    """Loads libpi.so from the package directory (build it with
+    ``paper_2406_16091_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpi.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "pi_create": ([ctypes.POINTER(PiBox), f32, i64, ctypes.POINTER(P)], i32),
+        "pi_destroy": ([P], i32),
+        "pi_bin": ([P, P, P, P, i64, P], i32),
+        "pi_interact": ([P, f32, P, P, P, P, P, i32, P], i32),
+        "pi_run_host": ([P, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
+        "pi_grid": ([P, P], i32),
+        "pi_binned": ([P] + [ctypes.POINTER(P)] * 6, i32),
+        "pi_copy_binned": ([P, P, P, P, P, P, P, P], i32),
+        "pi_sync_status": ([P, P, ctypes.POINTER(ctypes.c_uint32)], i32),
+        "pi_set_option": ([P, i32, i64], i32),
+        "pi_launch_count": ([P, ctypes.POINTER(ctypes.c_uint64)], i32),
+        "pi_status_str": ([i32], ctypes.c_char_p),
+        "pi_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def status_str(s: int) -> str:
+    return load().pi_status_str(int(s)).decode()
+
+
+def last_error() -> str:
+    return load().pi_last_error().decode()
+
+
+def _check(st: int, where: str) -> int:
+    if st != PI_OK:
+        raise PiError(st, where)
+    return st
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor / array / int, or None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def pi_create(lo, hi, r_c: float, n_max: int):
+    box = PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi))
+    out = ctypes.c_void_p()
+    _check(load().pi_create(ctypes.byref(box), float(r_c), int(n_max), ctypes.byref(out)), "pi_create")
+    return out.value
+
+
+def pi_destroy(ctx) -> None:
+    _check(load().pi_destroy(ctx), "pi_destroy")
+
+
+def pi_bin(ctx, x, y, z, n: int, stream=None) -> None:
+    _check(load().pi_bin(ctx, _ptr(x), _ptr(y), _ptr(z), int(n), _stream(stream)), "pi_bin")
+
+
+def pi_interact(ctx, h: float, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTED,
+                stream=None) -> None:
+    _check(load().pi_interact(ctx, float(h), _ptr(S), _ptr(Vx), _ptr(Vy), _ptr(Vz), _ptr(nbr),
+                              int(out_order), _stream(stream)), "pi_interact")
+
+
+def pi_run_host(ctx, x, y, z, n: int, h: float, S, Vx, Vy, Vz, nbr=None,
+                out_order: int = PI_ORDER_ORIGINAL, stream=None) -> int:
+    """Host arrays in and out; returns the step's status (raises on error)."""
+    return _check(load().pi_run_host(ctx, _ptr(x), _ptr(y), _ptr(z), int(n), float(h), _ptr(S),
+                                     _ptr(Vx), _ptr(Vy), _ptr(Vz), _ptr(nbr), int(out_order),
+                                     _stream(stream)), "pi_run_host")
+
+
+def pi_grid(ctx):
+    dims = (ctypes.c_int32 * 3)()
+    _check(load().pi_grid(ctx, ctypes.cast(dims, ctypes.c_void_p)), "pi_grid")
+    return tuple(dims)
+
+
+def pi_binned(ctx) -> dict:
+    ptrs = [ctypes.c_void_p() for _ in range(6)]
+    _check(load().pi_binned(ctx, *[ctypes.byref(p) for p in ptrs]), "pi_binned")
+    names = ("counts", "offsets", "perm", "sx", "sy", "sz")
+    return {k: p.value for k, p in zip(names, ptrs)}
+
+
+def pi_copy_binned(ctx, counts=None, offsets=None, perm=None, sx=None, sy=None, sz=None,
+                   stream=None) -> None:
+    _check(load().pi_copy_binned(ctx, _ptr(counts), _ptr(offsets), _ptr(perm), _ptr(sx), _ptr(sy),
+                                 _ptr(sz), _stream(stream)), "pi_copy_binned")
+
+
+def pi_sync_status(ctx, stream=None, raise_on_error: bool = True):
+    """Synchronises and returns (status, max_per_cell)."""
+    m = ctypes.c_uint32()
+    st = load().pi_sync_status(ctx, _stream(stream), ctypes.byref(m))
+    if raise_on_error:
+        _check(st, "pi_sync_status")
+    return st, int(m.value)
+
+
+def pi_set_option(ctx, key: int, value: int) -> None:
+    _check(load().pi_set_option(ctx, int(key), int(value)), "pi_set_option")
+
+
+def pi_launch_count(ctx) -> int:
+    c = ctypes.c_uint64()
+    _check(load().pi_launch_count(ctx, ctypes.byref(c)), "pi_launch_count")
+    return int(c.value)

@@ -1,0 +1,469 @@
+// pi_api.cu -- host side of the libpi C ABI (declared in include/pi.h).
+//
+// Argument checks, the device arena of a context, the launch sequence of a
+// step and the mapping of device error bits to pi_status.  No compute
+// happens here: every step of the path is one of the kernels in pi_bin.cu
+// and pi_interact.cu.
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pi.h"
+#include "pi_internal.cuh"
+
+using pi::Ctrl;
+using pi::Grid;
+
+struct pi_ctx {
+    pi_box box;
+    float rc;
+    int64_t n_max;
+    Grid g;
+    int64_t C;
+    int device;
+    int num_sms;
+
+    // device arena and its parts
+    void* arena;
+    Ctrl* ctrl;
+    uint32_t* counts;
+    uint32_t* offsets;
+    unsigned long long* scan_status;
+    uint32_t* cell;
+    uint32_t* rank;
+    uint32_t* perm_u;
+    uint32_t* perm;
+    float* sx;
+    float* sy;
+    float* sz;
+    float4* P;
+
+    // host-buffer path (allocated on first use)
+    void* io;
+    float* io_x;
+    float* io_y;
+    float* io_z;
+    float* io_S;
+    float* io_Vx;
+    float* io_Vy;
+    float* io_Vz;
+    uint32_t* io_nbr;
+
+    int64_t n;         // particles of the last pi_bin
+    int binned;        // a pi_bin has been enqueued since the last failure
+    uint32_t epoch;    // scan launch epoch
+    uint64_t launches; // kernels launched
+    uint32_t tiled_seq; // launches of the tiled interaction kernel
+    int algo;
+    int precision;
+    uint64_t wait_limit_ns;
+    int withhold_scan;
+    float slack;
+};
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+pi_status cuda_fail(cudaError_t e, const char* what)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s)", what, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return PI_ERR_NOMEM;
+    return PI_ERR_CUDA;
+}
+
+#define PI_TRY(call)                                       \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Makes the context's device current for the scope of a call.
+struct DeviceScope {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            changed = (err == cudaSuccess);
+        }
+    }
+    ~DeviceScope()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carves aligned pieces out of one allocation.
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count)
+    {
+        off = align_up(off, 256);
+        size_t at = off;
+        off += count * sizeof(T);
+        return at;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* pi_status_str(pi_status s)
+{
+    switch (s) {
+        case PI_OK: return "ok";
+        case PI_ERR_INVALID_ARG: return "invalid argument";
+        case PI_ERR_CAPACITY: return "capacity exceeded";
+        case PI_ERR_OUT_OF_BOX: return "position outside the box";
+        case PI_ERR_NOT_BINNED: return "interaction requested before binning";
+        case PI_ERR_CUDA: return "CUDA error";
+        case PI_ERR_TIMEOUT: return "device-side wait timed out";
+        case PI_ERR_NOMEM: return "device allocation failed";
+    }
+    return "unknown status";
+}
+
+const char* pi_last_error(void) { return g_last_error; }
+
+pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
+{
+    if (!box || !out) return PI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!(r_c > 0.0f) || std::isinf(r_c)) return PI_ERR_INVALID_ARG;
+    if (n_max < 0 || n_max >= (int64_t)2147483647 - 64) return PI_ERR_INVALID_ARG;
+    Grid g{};
+    int64_t C = 1;
+    float max_abs = 0.f, min_w = FLT_MAX;
+    for (int d = 0; d < 3; ++d) {
+        const double lo = box->lo[d], hi = box->hi[d];
+        if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return PI_ERR_INVALID_ARG;
+        double n = std::floor((hi - lo) / (double)r_c);
+        if (n < 1.0) n = 1.0;
+        if (n > 2147483647.0) return PI_ERR_INVALID_ARG;
+        g.lo[d] = box->lo[d];
+        g.hi[d] = box->hi[d];
+        g.n[d] = (int32_t)n;
+        g.inv_w[d] = (float)(n / (hi - lo));
+        C *= (int64_t)n;
+        if (C >= ((int64_t)1 << 31) - 1) return PI_ERR_INVALID_ARG;
+        max_abs = std::fmax(max_abs, std::fmax(std::fabs(box->lo[d]), std::fabs(box->hi[d])));
+        min_w = std::fmin(min_w, (float)((hi - lo) / n));
+    }
+
+    pi_ctx* c = new (std::nothrow) pi_ctx();
+    if (!c) return PI_ERR_NOMEM;
+    c->box = *box;
+    c->rc = r_c;
+    c->n_max = n_max;
+    c->g = g;
+    c->C = C;
+    c->algo = PI_ALGO_TILED;
+    c->precision = PI_PREC_FP32;
+    c->wait_limit_ns = 1000000000ull;
+    c->slack = 1e-5f * min_w + 16.0f * FLT_EPSILON * max_abs;
+    c->epoch = 0;
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        pi_status st = cuda_fail(e, "pi_create: device query");
+        delete c;
+        return st;
+    }
+
+    const size_t nm = (size_t)n_max;
+    const size_t tiles = ((size_t)C + 1 + pi::SCAN_TILE - 1) / pi::SCAN_TILE;
+    Carver k;
+    const size_t o_ctrl = k.take<Ctrl>(1);
+    const size_t o_counts = k.take<uint32_t>((size_t)C + 4);
+    const size_t zero_end = k.off;  // ctrl + counts are cleared by every pi_bin
+    const size_t o_offsets = k.take<uint32_t>((size_t)C + 1 + 16);
+    const size_t o_status = k.take<unsigned long long>(tiles);
+    const size_t o_cell = k.take<uint32_t>(nm + 4);
+    const size_t o_rank = k.take<uint32_t>(nm + 4);
+    const size_t o_permu = k.take<uint32_t>(nm + 4);
+    const size_t o_perm = k.take<uint32_t>(nm + 4);
+    const size_t o_sx = k.take<float>(nm + pi::SORTED_PAD);
+    const size_t o_sy = k.take<float>(nm + pi::SORTED_PAD);
+    const size_t o_sz = k.take<float>(nm + pi::SORTED_PAD);
+    const size_t o_P = k.take<float4>(nm + 4);
+    const size_t total = align_up(k.off, 256);
+
+    e = cudaMalloc(&c->arena, total);
+    if (e != cudaSuccess) {
+        pi_status st = cuda_fail(e, "pi_create: cudaMalloc");
+        delete c;
+        return st;
+    }
+    char* base = (char*)c->arena;
+    c->ctrl = (Ctrl*)(base + o_ctrl);
+    c->counts = (uint32_t*)(base + o_counts);
+    c->offsets = (uint32_t*)(base + o_offsets);
+    c->scan_status = (unsigned long long*)(base + o_status);
+    c->cell = (uint32_t*)(base + o_cell);
+    c->rank = (uint32_t*)(base + o_rank);
+    c->perm_u = (uint32_t*)(base + o_permu);
+    c->perm = (uint32_t*)(base + o_perm);
+    c->sx = (float*)(base + o_sx);
+    c->sy = (float*)(base + o_sy);
+    c->sz = (float*)(base + o_sz);
+    c->P = (float4*)(base + o_P);
+    (void)zero_end;
+    // everything starts at zero: an empty grid, no error, stale-free scan descriptors
+    e = cudaMemset(c->arena, 0, total);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        pi_status st = cuda_fail(e, "pi_create: clear");
+        cudaFree(c->arena);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return PI_OK;
+}
+
+pi_status pi_destroy(pi_ctx* ctx)
+{
+    if (!ctx) return PI_OK;
+    DeviceScope ds(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (ctx->io) cudaFree(ctx->io);
+    cudaError_t e2 = cudaFree(ctx->arena);
+    delete ctx;
+    if (e != cudaSuccess) return cuda_fail(e, "pi_destroy: synchronize");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "pi_destroy: cudaFree");
+    return PI_OK;
+}
+
+pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3])
+{
+    if (!ctx || !dims) return PI_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d) dims[d] = ctx->g.n[d];
+    return PI_OK;
+}
+
+pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t** offsets,
+                    const uint32_t** perm, const float** sx, const float** sy, const float** sz)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (counts) *counts = ctx->counts;
+    if (offsets) *offsets = ctx->offsets;
+    if (perm) *perm = ctx->perm;
+    if (sx) *sx = ctx->sx;
+    if (sy) *sy = ctx->sy;
+    if (sz) *sz = ctx->sz;
+    return PI_OK;
+}
+
+pi_status pi_copy_binned(const pi_ctx* ctx, uint32_t* counts, uint32_t* offsets, uint32_t* perm,
+                         float* sx, float* sy, float* sz, pi_stream stream)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (!ctx->binned) return PI_ERR_NOT_BINNED;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_copy_binned: set device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t C = (size_t)ctx->C, n = (size_t)ctx->n;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (counts) PI_TRY(cudaMemcpyAsync(counts, ctx->counts, C * 4, k, s));
+    if (offsets) PI_TRY(cudaMemcpyAsync(offsets, ctx->offsets, (C + 1) * 4, k, s));
+    if (n > 0) {
+        if (perm) PI_TRY(cudaMemcpyAsync(perm, ctx->perm, n * 4, k, s));
+        if (sx) PI_TRY(cudaMemcpyAsync(sx, ctx->sx, n * 4, k, s));
+        if (sy) PI_TRY(cudaMemcpyAsync(sy, ctx->sy, n * 4, k, s));
+        if (sz) PI_TRY(cudaMemcpyAsync(sz, ctx->sz, n * 4, k, s));
+    }
+    return PI_OK;
+}
+
+pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    switch (key) {
+        case PI_OPT_ALGO:
+            if (value != PI_ALGO_TILED && value != PI_ALGO_PPNL) return PI_ERR_INVALID_ARG;
+            ctx->algo = (int)value;
+            return PI_OK;
+        case PI_OPT_PRECISION:
+            if (value != PI_PREC_FP32 && value != PI_PREC_KAHAN) return PI_ERR_INVALID_ARG;
+            ctx->precision = (int)value;
+            return PI_OK;
+        case PI_OPT_WAIT_LIMIT_NS:
+            if (value < 1000 || value > (int64_t)60000000000ll) return PI_ERR_INVALID_ARG;
+            ctx->wait_limit_ns = (uint64_t)value;
+            return PI_OK;
+        case PI_OPT_TEST_WITHHOLD_SCAN:
+            if (value != 0 && value != 1) return PI_ERR_INVALID_ARG;
+            ctx->withhold_scan = (int)value;
+            return PI_OK;
+    }
+    return PI_ERR_INVALID_ARG;
+}
+
+pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count)
+{
+    if (!ctx || !count) return PI_ERR_INVALID_ARG;
+    *count = ctx->launches;
+    return PI_OK;
+}
+
+pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
+                 pi_stream stream)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (n < 0) return PI_ERR_INVALID_ARG;
+    if (n > ctx->n_max) return PI_ERR_CAPACITY;
+    if (n > 0 && (!x || !y || !z)) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_bin: set device");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->binned = 0;
+    ctx->tiled_seq = 0;  // k_zero clears both row-counter slots
+    ctx->epoch = (ctx->epoch % 0x3ffffffeu) + 1u;  // 30-bit, never 0
+    const uint32_t nn = (uint32_t)n;
+    const uint32_t C = (uint32_t)ctx->C;
+
+    // control block + counts are one contiguous zeroed prefix of the arena
+    const size_t zero_words = ((char*)(ctx->counts + C) - (char*)ctx->ctrl + 3) / 4;
+    PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, zero_words, s));
+    ctx->launches += 1;
+    if (nn > 0) {
+        PI_TRY(pi::launch_hist(x, y, z, nn, ctx->g, ctx->counts, ctx->cell, ctx->rank, ctx->ctrl,
+                               ctx->num_sms, s));
+        ctx->launches += 1;
+    }
+    PI_TRY(pi::launch_scan(ctx->counts, C, ctx->offsets, ctx->scan_status, ctx->ctrl, ctx->epoch,
+                           ctx->wait_limit_ns, ctx->withhold_scan, s));
+    ctx->launches += 1;
+    if (nn > 0) {
+        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, nn, ctx->offsets, ctx->perm_u, ctx->ctrl,
+                                  ctx->num_sms, s));
+        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->cell, nn, ctx->offsets, x, y, z, ctx->perm,
+                                    ctx->sx, ctx->sy, ctx->sz, ctx->P, ctx->ctrl, ctx->num_sms, s));
+        ctx->launches += 2;
+    }
+    ctx->n = n;
+    ctx->binned = 1;
+    return PI_OK;
+}
+
+pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
+                      uint32_t* nbr, int out_order, pi_stream stream)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (!(h > 0.0f) || std::isinf(h)) return PI_ERR_INVALID_ARG;
+    if (out_order != PI_ORDER_SORTED && out_order != PI_ORDER_ORIGINAL) return PI_ERR_INVALID_ARG;
+    if (!ctx->binned) return PI_ERR_NOT_BINNED;
+    if (ctx->n > 0 && (!S || !Vx || !Vy || !Vz)) return PI_ERR_INVALID_ARG;
+    if (ctx->n == 0) return PI_OK;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_interact: set device");
+
+    pi::InteractArgs a{};
+    a.P = ctx->P;
+    a.sx = ctx->sx;
+    a.sy = ctx->sy;
+    a.sz = ctx->sz;
+    a.offsets = ctx->offsets;
+    a.perm = ctx->perm;
+    a.n = (uint32_t)ctx->n;
+    a.g = ctx->g;
+    a.rc2 = ctx->rc * ctx->rc;  // FP32 product, round to nearest
+    const double hd = (double)h;
+    a.kscale = (float)(-1.4426950408889634 / (hd * hd));  // -log2(e) / h^2
+    a.S = S;
+    a.Vx = Vx;
+    a.Vy = Vy;
+    a.Vz = Vz;
+    a.nbr = nbr;
+    a.original_order = out_order == PI_ORDER_ORIGINAL;
+    a.ctrl = ctx->ctrl;
+    a.slack = ctx->slack;
+    a.wait_limit_ns = ctx->wait_limit_ns;
+    a.seq = ctx->tiled_seq;
+    int launched = 0;
+    cudaError_t e;
+    const bool kahan = ctx->precision == PI_PREC_KAHAN;
+    if (ctx->algo == PI_ALGO_PPNL)
+        e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, (cudaStream_t)stream, &launched);
+    else {
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, (cudaStream_t)stream, &launched);
+        ctx->tiled_seq += 1;
+    }
+    ctx->launches += (uint64_t)launched;
+    if (e != cudaSuccess) return cuda_fail(e, "pi_interact: launch");
+    return PI_OK;
+}
+
+pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_sync_status: set device");
+    PI_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    Ctrl h{};
+    PI_TRY(cudaMemcpy(&h, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    if (max_per_cell) *max_per_cell = h.max_per_cell;
+    if (h.error & pi::ERR_TIMEOUT) return PI_ERR_TIMEOUT;
+    if (h.error & pi::ERR_OUT_OF_BOX) return PI_ERR_OUT_OF_BOX;
+    if (h.error & pi::ERR_CAPACITY) return PI_ERR_CAPACITY;
+    return PI_OK;
+}
+
+pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz, int64_t n,
+                      float h, float* hS, float* hVx, float* hVy, float* hVz, uint32_t* hnbr,
+                      int out_order, pi_stream stream)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (n < 0) return PI_ERR_INVALID_ARG;
+    if (n > ctx->n_max) return PI_ERR_CAPACITY;
+    if (n > 0 && (!hx || !hy || !hz || !hS || !hVx || !hVy || !hVz)) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_run_host: set device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nm = (size_t)ctx->n_max + 4;
+    if (!ctx->io) {
+        PI_TRY(cudaMalloc(&ctx->io, nm * 8 * sizeof(float)));
+        float* f = (float*)ctx->io;
+        ctx->io_x = f;
+        ctx->io_y = f + nm;
+        ctx->io_z = f + 2 * nm;
+        ctx->io_S = f + 3 * nm;
+        ctx->io_Vx = f + 4 * nm;
+        ctx->io_Vy = f + 5 * nm;
+        ctx->io_Vz = f + 6 * nm;
+        ctx->io_nbr = (uint32_t*)(f + 7 * nm);
+    }
+    const size_t bytes = (size_t)n * sizeof(float);
+    if (n > 0) {
+        PI_TRY(cudaMemcpyAsync(ctx->io_x, hx, bytes, cudaMemcpyHostToDevice, s));
+        PI_TRY(cudaMemcpyAsync(ctx->io_y, hy, bytes, cudaMemcpyHostToDevice, s));
+        PI_TRY(cudaMemcpyAsync(ctx->io_z, hz, bytes, cudaMemcpyHostToDevice, s));
+    }
+    pi_status st = pi_bin(ctx, ctx->io_x, ctx->io_y, ctx->io_z, n, stream);
+    if (st != PI_OK) return st;
+    st = pi_interact(ctx, h, ctx->io_S, ctx->io_Vx, ctx->io_Vy, ctx->io_Vz,
+                     hnbr ? ctx->io_nbr : nullptr, out_order, stream);
+    if (st != PI_OK) return st;
+    if (n > 0) {
+        PI_TRY(cudaMemcpyAsync(hS, ctx->io_S, bytes, cudaMemcpyDeviceToHost, s));
+        PI_TRY(cudaMemcpyAsync(hVx, ctx->io_Vx, bytes, cudaMemcpyDeviceToHost, s));
+        PI_TRY(cudaMemcpyAsync(hVy, ctx->io_Vy, bytes, cudaMemcpyDeviceToHost, s));
+        PI_TRY(cudaMemcpyAsync(hVz, ctx->io_Vz, bytes, cudaMemcpyDeviceToHost, s));
+        if (hnbr) PI_TRY(cudaMemcpyAsync(hnbr, ctx->io_nbr, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    return pi_sync_status(ctx, stream, nullptr);
+}
+
+}  // extern "C"

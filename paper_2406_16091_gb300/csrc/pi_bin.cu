@@ -1,0 +1,391 @@
+// pi_bin.cu -- binning kernels (arXiv 2406.16091, Sec. 2 and Fig. 1).
+//
+//   k_zero       clears the control block and the per-cell counts
+//   k_hist       a1 + a2: cell index of each particle (float4 SoA loads) and a
+//                warp-aggregated atomic histogram; the value returned by the
+//                atomic is kept as a provisional slot inside the cell
+//   k_scan       a3: single-pass exclusive scan over the C+1 counts with
+//                decoupled lookback (dynamic tile ticket, bounded waits), and
+//                M_C, the largest count (Sec. 5.1 keeps it during the scan)
+//   k_scatter    a4, first half: provisional slot -> perm_u (the paper's
+//                atomic scatter, whose order inside a cell is arbitrary)
+//   k_stabilise  a4, second half: rank each particle among its cell's members
+//                by input index, which makes the order stable, and gather the
+//                sorted positions; also writes the per-cell x-ordered copy P
+//                that the tiled interaction stages
+//
+// All kernels are HBM- or L2-bound integer work; none uses tensor cores.
+#include "pi_internal.cuh"
+
+namespace pi {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void k_zero(uint32_t* __restrict__ p, size_t n_words)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint4* p4 = reinterpret_cast<uint4*>(p);
+    size_t n4 = n_words / 4;
+    for (size_t k = i; k < n4; k += stride) p4[k] = make_uint4(0, 0, 0, 0);
+    for (size_t k = n4 * 4 + i; k < n_words; k += stride) p[k] = 0;
+}
+
+// One warp-aggregated increment of counts[key]; returns the old count plus
+// the lane's position among the lanes of its warp with the same key.
+// Every lane of the warp must call it; key == 0xffffffff means "no particle".
+__device__ __forceinline__ uint32_t aggregated_rank(uint32_t key, uint32_t* counts, unsigned lane)
+{
+    unsigned peers = __match_any_sync(FULL, key);
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader && key != 0xffffffffu) base = atomicAdd(&counts[key], __popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    return base + __popc(peers & lanemask_lt());
+}
+
+// a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
+// float4 per component when the arrays are 16-byte aligned.  The loop bound
+// is warp-uniform so that every lane takes part in the match/shuffle.
+__global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
+                                              const float* __restrict__ y,
+                                              const float* __restrict__ z, uint32_t n, Grid g,
+                                              uint32_t* __restrict__ counts,
+                                              uint32_t* __restrict__ cell_out,
+                                              uint32_t* __restrict__ rank_out,
+                                              Ctrl* __restrict__ ctrl, int vec)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t groups = (n + 3u) / 4u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    bool all_ok = true;
+    for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < groups; g0 += stride) {
+        const uint32_t grp = g0 + lane;
+        const uint32_t i0 = grp * 4u;
+        float px[4], py[4], pz[4];
+        bool valid[4];
+        const bool full = (grp < groups) && (i0 + 4u <= n);
+        if (full && vec) {
+            float4 a = __ldcs(reinterpret_cast<const float4*>(x) + grp);
+            float4 b = __ldcs(reinterpret_cast<const float4*>(y) + grp);
+            float4 c = __ldcs(reinterpret_cast<const float4*>(z) + grp);
+            px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
+            py[0] = b.x; py[1] = b.y; py[2] = b.z; py[3] = b.w;
+            pz[0] = c.x; pz[1] = c.y; pz[2] = c.z; pz[3] = c.w;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid[j] = true;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t i = i0 + j;
+                valid[j] = (grp < groups) && (i < n);
+                px[j] = valid[j] ? x[i] : 0.f;
+                py[j] = valid[j] ? y[i] : 0.f;
+                pz[j] = valid[j] ? z[i] : 0.f;
+            }
+        }
+        uint32_t cell[4], rank[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            bool ok = true;
+            uint32_t c = cell_of(px[j], py[j], pz[j], g, ok);
+            all_ok &= ok | !valid[j];
+            cell[j] = c;
+            rank[j] = aggregated_rank(valid[j] ? c : 0xffffffffu, counts, lane);
+        }
+        if (full) {
+            reinterpret_cast<uint4*>(cell_out)[grp] = make_uint4(cell[0], cell[1], cell[2], cell[3]);
+            reinterpret_cast<uint4*>(rank_out)[grp] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (valid[j]) {
+                    cell_out[i0 + j] = cell[j];
+                    rank_out[i0 + j] = rank[j];
+                }
+        }
+    }
+    if (!all_ok) atomicOr(&ctrl->error, ERR_OUT_OF_BOX);
+}
+
+// ---- a3: decoupled-lookback exclusive scan --------------------------------
+//
+// Tile descriptor (64 bits): value in bits 0..31, flag in bits 32..33
+// (1 = tile aggregate, 2 = inclusive prefix), launch epoch in bits 34..63.
+// A descriptor from another launch has another epoch and reads as "not
+// ready", so the array never needs clearing between launches.
+
+constexpr uint32_t FLAG_AGG = 1u, FLAG_INCL = 2u;
+
+__device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, uint32_t flag, uint32_t v)
+{
+    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | v;
+}
+
+__device__ __forceinline__ void publish(unsigned long long* p, unsigned long long w)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long peek(const unsigned long long* p)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restrict__ counts, uint32_t C,
+                                                       uint32_t* __restrict__ offsets,
+                                                       unsigned long long* __restrict__ status,
+                                                       Ctrl* __restrict__ ctrl, uint32_t epoch,
+                                                       uint64_t wait_limit_ns, int withhold_first)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_warp_sum[SCAN_THREADS / 32];
+    __shared__ uint32_t s_warp_max[SCAN_THREADS / 32];
+    __shared__ uint32_t s_prefix;
+
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl->ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t items = (uint64_t)C + 1;  // item C is a zero count -> offsets[C] = total
+    const uint64_t my0 = (uint64_t)tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+
+    uint32_t v[SCAN_ITEMS];
+    if (my0 + SCAN_ITEMS <= C) {
+        const uint4* src = reinterpret_cast<const uint4*>(counts + my0);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+            uint4 u = src[q];
+            v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = (my0 + k < C) ? counts[my0 + k] : 0u;
+    }
+    uint32_t run = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        uint32_t t = v[k];
+        mx = max(mx, t);
+        v[k] = run;  // exclusive inside the thread
+        run += t;
+    }
+    // block-wide exclusive scan of the per-thread totals
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+    if (lane == 31) s_warp_sum[warp] = incl;
+    if (lane == 0) s_warp_max[warp] = mx;
+    __syncthreads();
+    uint32_t warp_excl = 0, tile_sum = 0, tile_max = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        uint32_t t = s_warp_sum[w];
+        if (w < (int)warp) warp_excl += t;
+        tile_sum += t;
+        tile_max = max(tile_max, s_warp_max[w]);
+    }
+    const uint32_t thread_excl = warp_excl + incl - run;
+
+    if (warp == 0) {
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0 && !withhold_first) publish(&status[0], pack_status(epoch, FLAG_INCL, tile_sum));
+        } else {
+            if (lane == 0) publish(&status[tile], pack_status(epoch, FLAG_AGG, tile_sum));
+            const uint64_t t0 = global_ns();
+            int64_t p = (int64_t)tile - 1;
+            bool timed_out = false;
+            for (;;) {
+                const int64_t q = p - (int64_t)lane;
+                uint32_t flag = FLAG_INCL, val = 0;
+                for (;;) {
+                    if (q >= 0) {
+                        unsigned long long w = peek(&status[q]);
+                        flag = ((uint32_t)(w >> 34) == epoch) ? (uint32_t)(w >> 32) & 3u : 0u;
+                        val = (uint32_t)w;
+                    }
+                    if (__ballot_sync(FULL, flag == 0u) == 0u) break;
+                    const bool late = __shfl_sync(FULL, (global_ns() - t0) > wait_limit_ns, 0);
+                    if (late) { timed_out = true; break; }
+                    __nanosleep(64);
+                }
+                if (timed_out) break;
+                const unsigned incl_mask = __ballot_sync(FULL, flag == FLAG_INCL);
+                const int stop = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                prefix += warp_sum((int)lane <= stop ? val : 0u);
+                if (incl_mask) break;
+                p -= 32;
+            }
+            if (lane == 0) {
+                if (timed_out) atomicOr(&ctrl->error, ERR_TIMEOUT);
+                // publish even after a timeout so that later tiles finish quickly
+                publish(&status[tile], pack_status(epoch, FLAG_INCL, prefix + tile_sum));
+            }
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (tile_max) atomicMax(&ctrl->max_per_cell, tile_max);
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s_prefix + thread_excl;
+    if (my0 + SCAN_ITEMS <= items) {
+        uint4* dst = reinterpret_cast<uint4*>(offsets + my0);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / 4; ++q)
+            dst[q] = make_uint4(base + v[4 * q], base + v[4 * q + 1], base + v[4 * q + 2],
+                                base + v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k)
+            if (my0 + k < items) offsets[my0 + k] = base + v[k];
+    }
+}
+
+// ---- a4 ---------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cell,
+                                                 const uint32_t* __restrict__ rank, uint32_t n,
+                                                 const uint32_t* __restrict__ offsets,
+                                                 uint32_t* __restrict__ perm_u,
+                                                 Ctrl* __restrict__ ctrl)
+{
+    if (load_error(ctrl)) return;
+    bool bad = false;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t c = cell[i];
+        const uint32_t slot = offsets[c] + rank[i];
+        if (slot < offsets[c + 1]) perm_u[slot] = i;
+        else bad = true;
+    }
+    if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
+}
+
+// Stable order: the final slot of particle i inside cell c is the number of
+// members of c with a smaller input index.  One thread per provisional slot.
+// The same pass ranks i among its cell's members by x (ties by input index)
+// and writes P, the x-ordered copy the tiled interaction stages: because the
+// cells of an X-row are contiguous and monotone in x, every X-row of P is
+// sorted by x as a whole.  P[.].w holds the stable slot of the particle.
+__global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ perm_u,
+                                                   const uint32_t* __restrict__ cell, uint32_t n,
+                                                   const uint32_t* __restrict__ offsets,
+                                                   const float* __restrict__ x,
+                                                   const float* __restrict__ y,
+                                                   const float* __restrict__ z,
+                                                   uint32_t* __restrict__ perm,
+                                                   float* __restrict__ sx, float* __restrict__ sy,
+                                                   float* __restrict__ sz, float4* __restrict__ P,
+                                                   Ctrl* __restrict__ ctrl)
+{
+    if (load_error(ctrl)) return;
+    bool bad = false;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = perm_u[k];
+        if (i >= n) { bad = true; continue; }
+        const uint32_t c = cell[i];
+        const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
+        const float xi = x[i];
+        uint32_t r = 0, xr = 0;
+        for (uint32_t q = s0; q < s1; ++q) {
+            const uint32_t j = perm_u[q];
+            if (j >= n) { bad = true; break; }
+            const float xj = x[j];
+            r += (j < i) ? 1u : 0u;
+            xr += (xj < xi || (xj == xi && j < i)) ? 1u : 0u;
+        }
+        const uint32_t dst = s0 + r;
+        if (dst >= s1 || s0 + xr >= s1) { bad = true; continue; }
+        const float yi = y[i], zi = z[i];
+        perm[dst] = i;
+        sx[dst] = xi;
+        sy[dst] = yi;
+        sz[dst] = zi;
+        P[s0 + xr] = make_float4(xi, yi, zi, __uint_as_float(dst));
+    }
+    if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
+}
+
+inline int grid_for(uint64_t work, int threads, int num_sms, int per_sm)
+{
+    uint64_t b = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_zero(uint32_t* p, size_t n_words, cudaStream_t s)
+{
+    int blocks = (int)((n_words / 4 + 255) / 256);
+    blocks = blocks < 1 ? 1 : (blocks > 1184 ? 1184 : blocks);
+    k_zero<<<blocks, 256, 0, s>>>(p, n_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n, const Grid& g,
+                        uint32_t* counts, uint32_t* cell, uint32_t* rank, Ctrl* ctrl, int num_sms,
+                        cudaStream_t s)
+{
+    const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
+    const uint64_t groups = ((uint64_t)n + 3) / 4;
+    k_hist<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(x, y, z, n, g, counts, cell, rank,
+                                                             ctrl, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
+                        unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
+                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s)
+{
+    const uint64_t tiles = ((uint64_t)C + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, C, offsets, status, ctrl, epoch,
+                                                    wait_limit_ns, withhold_first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, uint32_t n,
+                           const uint32_t* offsets, uint32_t* perm_u, Ctrl* ctrl, int num_sms,
+                           cudaStream_t s)
+{
+    k_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(cell, rank, n, offsets, perm_u, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stabilise(const uint32_t* perm_u, const uint32_t* cell, uint32_t n,
+                             const uint32_t* offsets, const float* x, const float* y,
+                             const float* z, uint32_t* perm, float* sx, float* sy, float* sz,
+                             float4* P, Ctrl* ctrl, int num_sms, cudaStream_t s)
+{
+    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, cell, n, offsets, x, y, z,
+                                                             perm, sx, sy, sz, P, ctrl);
+    return cudaGetLastError();
+}
+
+}  // namespace pi

@@ -1,0 +1,252 @@
+"""GPU parity: every output of the CUDA path against the oracle, element by
+element, on seeded inputs.
+
+Bit-exact: counts, offsets, M_C, the stable permutation, the sorted
+positions and the neighbour counts.  Within 1e-5 of sum|terms| per particle:
+S, Vx, Vy, Vz.  Sizes run from empty and ragged inputs through several tiles
+of every kernel to the full benchmark workloads, in the launch configuration
+the benchmark times.
+"""
+import numpy as np
+import pytest
+
+from paper_2406_16091_gb300 import binding as B
+from paper_2406_16091_gb300 import workloads as W
+
+from gpu_harness import check_binning, check_interaction, oracle_run, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = [B.PI_ALGO_TILED, B.PI_ALGO_PPNL]
+
+
+def _case(w):
+    x, y, z = w.positions()
+    return x, y, z, w.lo, w.hi, w.rc, w.h
+
+
+SMALL_CASES = {
+    "small": W.SMALL,
+    "ragged_4099": W.scaled(W.SMALL, 4099),
+    "ragged_1023_ppc1": W.scaled(W.SCALE_VARIANTS[1], 1023),
+    "ppc32_20000": W.scaled(W.SCALE_VARIANTS[32], 20000),
+    "clustered_60000": W.scaled(W.CLUSTERED, 60000),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL_CASES))
+@pytest.mark.parametrize("algo", ALGOS)
+def test_small_workloads(name, algo):
+    x, y, z, lo, hi, rc, h = _case(SMALL_CASES[name])
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo)
+    check_binning(g, b)
+    check_interaction(g, r)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 33, 127, 4097])
+def test_tiny_and_ragged_sizes(n):
+    x, y, z = W.uniform(n, 100 + n)
+    rc = 0.2
+    b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2)
+    for algo in ALGOS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo, n_max=n + 7)
+        check_binning(g, b)
+        if n:
+            check_interaction(g, r)
+
+
+def test_non_cubic_box_with_offset():
+    lo, hi = (-1.0, 0.5, 2.0), (1.0, 1.5, 2.25)
+    x, y, z = W.uniform(30000, 77, lo, hi)
+    rc = 0.031
+    b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2)
+    for algo in ALGOS:
+        g = run_gpu(x, y, z, lo, hi, rc, rc / 2, algo=algo)
+        check_binning(g, b)
+        check_interaction(g, r)
+
+
+def test_long_rows_longer_than_a_chunk():
+    """300 cells along X, few per cell: X-rows are split into several chunks."""
+    lo, hi = (0.0, 0.0, 0.0), (3.0, 0.04, 0.04)
+    x, y, z = W.uniform(3000, 5, lo, hi)
+    rc = 0.01
+    b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2)
+    assert b.dims[0] == 300
+    g = run_gpu(x, y, z, lo, hi, rc, rc / 2)
+    check_binning(g, b)
+    check_interaction(g, r)
+
+
+def test_dense_cell_overflows_shared_memory():
+    """A cluster whose neighbour rows hold more particles than one staged
+    chunk fits: that chunk is read from global memory instead."""
+    rng = np.random.default_rng(3)
+    bg = rng.random((20000, 3)).astype(np.float32)
+    cl = (0.5 + 0.004 * rng.standard_normal((6000, 3))).astype(np.float32)
+    p = np.concatenate([bg, cl])
+    rc = 1.0 / 64
+    b, r = oracle_run(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), rc, rc / 2)
+    assert b.max_per_cell > 300
+    for algo in ALGOS:
+        g = run_gpu(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo)
+        check_binning(g, b)
+        check_interaction(g, r)
+
+
+def test_lattice_on_cell_faces():
+    """Dyadic lattice points sitting exactly on cell faces, spacing = r_c:
+    every axis neighbour is exactly r_c away and must not count."""
+    m = 32
+    g1 = (np.arange(m) / m).astype(np.float32)
+    X, Y, Z = np.meshgrid(g1, g1, g1, indexing="ij")
+    x, y, z = X.ravel(), Y.ravel(), Z.ravel()
+    rc = 1.0 / m
+    b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2)
+    assert r.nbr.max() == 0
+    for algo in ALGOS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo)
+        check_binning(g, b)
+        check_interaction(g, r)
+    rc2 = 1.5 / m
+    b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc2, rc2 / 2)
+    for algo in ALGOS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc2, rc2 / 2, algo=algo)
+        check_binning(g, b)
+        check_interaction(g, r)
+
+
+def test_coincident_particles():
+    x = np.full(50, 0.3, np.float32)
+    y = np.full(50, 0.6, np.float32)
+    b, r = oracle_run(x, y, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05)
+    for algo in ALGOS:
+        g = run_gpu(x, y, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05, algo=algo)
+        check_binning(g, b)
+        check_interaction(g, r)
+        assert np.all(g["S"] == 49.0)
+
+
+def test_original_order_output():
+    x, y, z, lo, hi, rc, h = _case(W.scaled(W.SMALL, 10000))
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    for algo in ALGOS:
+        g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, order=B.PI_ORDER_ORIGINAL)
+        check_interaction(g, r, perm=b.perm)
+
+
+def test_kahan_precision_mode():
+    """Compensated accumulation: same counts, and no larger error than the
+    plain FP32 sums on a 32-per-cell workload."""
+    x, y, z, lo, hi, rc, h = _case(W.scaled(W.SCALE_VARIANTS[32], 40000))
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    for algo in ALGOS:
+        plain = check_interaction(run_gpu(x, y, z, lo, hi, rc, h, algo=algo), r)
+        kahan = check_interaction(
+            run_gpu(x, y, z, lo, hi, rc, h, algo=algo, precision=B.PI_PREC_KAHAN), r)
+        assert kahan["S"] <= plain["S"] * 1.01 + 1e-9
+
+
+def test_repeat_is_deterministic():
+    x, y, z, lo, hi, rc, h = _case(W.scaled(W.CLUSTERED, 50000))
+    a = run_gpu(x, y, z, lo, hi, rc, h, repeat=1)
+    c = run_gpu(x, y, z, lo, hi, rc, h, repeat=3)
+    for k in ("counts", "offsets", "perm", "sx", "nbr", "S", "Vx", "Vy", "Vz"):
+        assert np.array_equal(a[k].view(np.uint32), c[k].view(np.uint32)), k
+
+
+# ---- full-size workloads, in the launch configuration bench.py times -------------
+
+FULL = ["small", "scale", "scale_ppc1", "scale_ppc2", "scale_ppc4", "scale_ppc16",
+        "scale_ppc32", "clustered"]
+
+
+@pytest.mark.parametrize("name", FULL)
+def test_full_size_workloads(name):
+    w = W.WORKLOADS[name]
+    x, y, z, lo, hi, rc, h = _case(w)
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    g = run_gpu(x, y, z, lo, hi, rc, h)
+    check_binning(g, b)
+    check_interaction(g, r)
+    # each within-cutoff pair is seen from both sides
+    assert int(g["nbr"].astype(np.int64).sum()) % 2 == 0
+
+
+# ---- failure paths: no fault, the status comes back and the context recovers ----
+
+def test_out_of_box_reported_then_recovers():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    x, y, z = W.uniform(5000, 9)
+    bad = x.copy()
+    bad[1234] = 1.5
+    ctx = B.pi_create((0, 0, 0), (1, 1, 1), 0.1, 5000)
+    try:
+        s = torch.cuda.current_stream()
+        tb, ty, tz = (torch.from_numpy(a).to(dev) for a in (bad, y, z))
+        out = [torch.empty(5000, device=dev) for _ in range(4)]
+        B.pi_bin(ctx, tb, ty, tz, 5000, s)
+        B.pi_interact(ctx, 0.05, *out, None, B.PI_ORDER_SORTED, s)
+        st, _ = B.pi_sync_status(ctx, s, raise_on_error=False)
+        assert st == B.PI_ERR_OUT_OF_BOX
+        tx = torch.from_numpy(x).to(dev)
+        B.pi_bin(ctx, tx, ty, tz, 5000, s)
+        B.pi_interact(ctx, 0.05, *out, None, B.PI_ORDER_SORTED, s)
+        st, _ = B.pi_sync_status(ctx, s, raise_on_error=False)
+        assert st == B.PI_OK
+        with pytest.raises(B.PiError) as e:
+            B.pi_bin(ctx, tx, ty, tz, 5001, s)
+        assert e.value.status == B.PI_ERR_CAPACITY
+    finally:
+        B.pi_destroy(ctx)
+
+
+def test_scan_wait_times_out_and_recovers():
+    """The first scan tile withholds its prefix (a flag nothing sets): the
+    other tiles' bounded waits run out, the status is PI_ERR_TIMEOUT, and the
+    next step succeeds."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    w = W.scaled(W.SCALE, 200000)
+    x, y, z = w.positions()
+    ctx = B.pi_create(w.lo, w.hi, w.rc, w.n)
+    try:
+        dims = B.pi_grid(ctx)
+        assert dims[0] * dims[1] * dims[2] > 4096  # at least two scan tiles
+        s = torch.cuda.current_stream()
+        tx, ty, tz = (torch.from_numpy(a).to(dev) for a in (x, y, z))
+        out = [torch.empty(w.n, device=dev) for _ in range(4)]
+        B.pi_set_option(ctx, B.PI_OPT_WAIT_LIMIT_NS, 20_000_000)
+        B.pi_set_option(ctx, B.PI_OPT_TEST_WITHHOLD_SCAN, 1)
+        B.pi_bin(ctx, tx, ty, tz, w.n, s)
+        B.pi_interact(ctx, w.h, *out, None, B.PI_ORDER_SORTED, s)
+        st, _ = B.pi_sync_status(ctx, s, raise_on_error=False)
+        assert st == B.PI_ERR_TIMEOUT
+        B.pi_set_option(ctx, B.PI_OPT_TEST_WITHHOLD_SCAN, 0)
+        B.pi_bin(ctx, tx, ty, tz, w.n, s)
+        B.pi_interact(ctx, w.h, *out, None, B.PI_ORDER_SORTED, s)
+        st, mpc = B.pi_sync_status(ctx, s, raise_on_error=False)
+        assert st == B.PI_OK and mpc > 0
+    finally:
+        B.pi_destroy(ctx)
+
+
+def test_host_buffer_step_matches_device_step():
+    torch = pytest.importorskip("torch")
+    x, y, z, lo, hi, rc, h = _case(W.scaled(W.SMALL, 20000))
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    n = len(x)
+    ctx = B.pi_create(lo, hi, rc, n)
+    try:
+        hx, hy, hz = (torch.from_numpy(a).pin_memory() for a in (x, y, z))
+        outs = [torch.empty(n).pin_memory() for _ in range(4)]
+        nb = torch.empty(n, dtype=torch.int32).pin_memory()
+        B.pi_run_host(ctx, hx, hy, hz, n, h, *outs, nb, B.PI_ORDER_ORIGINAL,
+                      torch.cuda.current_stream())
+        g = {"S": outs[0].numpy(), "Vx": outs[1].numpy(), "Vy": outs[2].numpy(),
+             "Vz": outs[3].numpy(), "nbr": nb.numpy().view(np.uint32)}
+        check_interaction(g, r, perm=b.perm)
+    finally:
+        B.pi_destroy(ctx)
