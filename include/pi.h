@@ -172,6 +172,36 @@ pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell);
  * enqueued afterwards.  Errors: PI_ERR_INVALID_ARG for an unknown key or value. */
 pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
 
+/* Exclusive scan of per-cell counts that allocates nothing.
+ *
+ * No passage of the paper corresponds to this entry point: it is the scan of
+ * pi_bin's step a3 offered on its own to callers that cannot allocate device
+ * memory -- code whose device memory is reserved up front by another
+ * allocator (a framework's caching allocator, a solver that owns a fixed
+ * budget), or a latency-critical loop that must not call cudaMalloc/cudaFree,
+ * which can synchronise the whole device.
+ *
+ *   counts  device array of C uint32 counts (caller-owned, read only).
+ *   C       1 <= C <= 16,777,216 (2^24); larger C returns PI_ERR_CAPACITY.
+ *   offsets device array of C+1 uint32 (caller-owned, written):
+ *           offsets[c] = sum of counts[0..c-1], offsets[C] = the total.
+ *   result  optional device array of 2 uint32 (caller-owned, written):
+ *           result[0] = the largest count (M_C), result[1] = device error
+ *           bits (0 = ok; non-zero means a bounded wait ran out and offsets
+ *           are undefined).  May be NULL.
+ * Asynchronous on `stream`.  Calls no cudaMalloc, cudaFree or allocating
+ * routine: the scan's scratch (a 256-byte control block and one 8-byte
+ * descriptor per 4096 counts, about 33 KB in all) is one fixed __device__
+ * array that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the array and clears what it needs first, so
+ * calls that may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_CAPACITY, PI_ERR_CUDA. */
+pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, uint32_t* offsets,
+                                 uint32_t* result, pi_stream stream);
+
 /* Number of kernels this context has launched since pi_create (host counter). */
 pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count);
 

@@ -73,6 +73,7 @@ def load():
         "pi_grid": ([P, P], i32),
         "pi_binned": ([P] + [ctypes.POINTER(P)] * 6, i32),
         "pi_copy_binned": ([P, P, P, P, P, P, P, P], i32),
+        "pi_scan_counts_noalloc": ([P, i64, P, P, P], i32),
         "pi_sync_status": ([P, P, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pi_set_option": ([P, i32, i64], i32),
         "pi_launch_count": ([P, ctypes.POINTER(ctypes.c_uint64)], i32),
@@ -168,6 +169,14 @@ def pi_copy_binned(ctx, counts=None, offsets=None, perm=None, sx=None, sy=None, 
                    stream=None) -> None:
     _check(load().pi_copy_binned(ctx, _ptr(counts), _ptr(offsets), _ptr(perm), _ptr(sx), _ptr(sy),
                                  _ptr(sz), _stream(stream)), "pi_copy_binned")
+
+
+def pi_scan_counts_noalloc(counts, C: int, offsets, result=None, stream=None) -> None:
+    """Exclusive scan of C device counts into C+1 device offsets using the
+    library's fixed scratch array (no allocation); result (2 uint32, device)
+    receives M_C and the device error bits."""
+    _check(load().pi_scan_counts_noalloc(_ptr(counts), int(C), _ptr(offsets), _ptr(result),
+                                         _stream(stream)), "pi_scan_counts_noalloc")
 
 
 def pi_sync_status(ctx, stream=None, raise_on_error: bool = True):

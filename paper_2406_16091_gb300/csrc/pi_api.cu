@@ -117,6 +117,14 @@ struct Carver {
 
 }  // namespace
 
+namespace pi {
+// Lets other translation units report a message through pi_last_error().
+void set_last_error_text(const char* text)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s", text);
+}
+}  // namespace pi
+
 extern "C" {
 
 const char* pi_status_str(pi_status s)
