@@ -29,11 +29,13 @@ struct pi_ctx {
     void* arena;
     Ctrl* ctrl;
     uint32_t* counts;
+    uint32_t* xbins;
     uint32_t* offsets;
     unsigned long long* scan_status;
     uint32_t* cell;
     uint32_t* rank;
     uint32_t* perm_u;
+    float4* pos_u;
     uint32_t* perm;
     float* sx;
     float* sy;
@@ -195,12 +197,14 @@ pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
     Carver k;
     const size_t o_ctrl = k.take<Ctrl>(1);
     const size_t o_counts = k.take<uint32_t>((size_t)C + 4);
-    const size_t zero_end = k.off;  // ctrl + counts are cleared by every pi_bin
+    const size_t o_xbins = k.take<uint32_t>((size_t)C + 4);
+    const size_t zero_end = k.off;  // ctrl, counts and xbins are cleared by every pi_bin
     const size_t o_offsets = k.take<uint32_t>((size_t)C + 1 + 16);
     const size_t o_status = k.take<unsigned long long>(tiles);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
     const size_t o_permu = k.take<uint32_t>(nm + 4);
+    const size_t o_posu = k.take<float4>(nm + 4);
     const size_t o_perm = k.take<uint32_t>(nm + 4);
     const size_t o_sx = k.take<float>(nm + pi::SORTED_PAD);
     const size_t o_sy = k.take<float>(nm + pi::SORTED_PAD);
@@ -217,11 +221,13 @@ pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
     char* base = (char*)c->arena;
     c->ctrl = (Ctrl*)(base + o_ctrl);
     c->counts = (uint32_t*)(base + o_counts);
+    c->xbins = (uint32_t*)(base + o_xbins);
     c->offsets = (uint32_t*)(base + o_offsets);
     c->scan_status = (unsigned long long*)(base + o_status);
     c->cell = (uint32_t*)(base + o_cell);
     c->rank = (uint32_t*)(base + o_rank);
     c->perm_u = (uint32_t*)(base + o_permu);
+    c->pos_u = (float4*)(base + o_posu);
     c->perm = (uint32_t*)(base + o_perm);
     c->sx = (float*)(base + o_sx);
     c->sy = (float*)(base + o_sy);
@@ -342,8 +348,8 @@ pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, in
     const uint32_t nn = (uint32_t)n;
     const uint32_t C = (uint32_t)ctx->C;
 
-    // control block + counts are one contiguous zeroed prefix of the arena
-    const size_t zero_words = ((char*)(ctx->counts + C) - (char*)ctx->ctrl + 3) / 4;
+    // control block, counts and xbins are one contiguous zeroed prefix of the arena
+    const size_t zero_words = ((char*)(ctx->xbins + C) - (char*)ctx->ctrl + 3) / 4;
     PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, zero_words, s));
     ctx->launches += 1;
     if (nn > 0) {
@@ -355,10 +361,11 @@ pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, in
                            ctx->wait_limit_ns, ctx->withhold_scan, s));
     ctx->launches += 1;
     if (nn > 0) {
-        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, nn, ctx->offsets, ctx->perm_u, ctx->ctrl,
-                                  ctx->num_sms, s));
-        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->cell, nn, ctx->offsets, x, y, z, ctx->perm,
-                                    ctx->sx, ctx->sy, ctx->sz, ctx->P, ctx->ctrl, ctx->num_sms, s));
+        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, ctx->offsets, ctx->perm_u,
+                                  ctx->pos_u, ctx->ctrl, ctx->num_sms, s));
+        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->pos_u, nn, ctx->g, ctx->offsets, ctx->perm,
+                                    ctx->sx, ctx->sy, ctx->sz, ctx->P, ctx->xbins, ctx->ctrl,
+                                    ctx->num_sms, s));
         ctx->launches += 2;
     }
     ctx->n = n;
@@ -380,6 +387,7 @@ pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, floa
 
     pi::InteractArgs a{};
     a.P = ctx->P;
+    a.xbins = ctx->xbins;
     a.sx = ctx->sx;
     a.sy = ctx->sy;
     a.sz = ctx->sz;
@@ -400,6 +408,8 @@ pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, floa
     a.slack = ctx->slack;
     a.wait_limit_ns = ctx->wait_limit_ns;
     a.seq = ctx->tiled_seq;
+    for (int d = 0; d < 3; ++d)
+        a.cell_w[d] = (float)(((double)ctx->box.hi[d] - (double)ctx->box.lo[d]) / (double)ctx->g.n[d]);
     int launched = 0;
     cudaError_t e;
     const bool kahan = ctx->precision == PI_PREC_KAHAN;

@@ -7,12 +7,13 @@
 //   k_scan       a3: single-pass exclusive scan over the C+1 counts with
 //                decoupled lookback (dynamic tile ticket, bounded waits), and
 //                M_C, the largest count (Sec. 5.1 keeps it during the scan)
-//   k_scatter    a4, first half: provisional slot -> perm_u (the paper's
-//                atomic scatter, whose order inside a cell is arbitrary)
+//   k_scatter    a4, first half: each particle (and its position) to its
+//                provisional slot (the paper's atomic scatter, whose order
+//                inside a cell is arbitrary)
 //   k_stabilise  a4, second half: rank each particle among its cell's members
-//                by input index, which makes the order stable, and gather the
-//                sorted positions; also writes the per-cell x-ordered copy P
-//                that the tiled interaction stages
+//                by input index, which makes the order stable; write the
+//                sorted positions, the per-cell x-ordered copy P that the
+//                tiled interaction stages, and each cell's x-sub-bin starts
 //
 // All kernels are HBM- or L2-bound integer work; none uses tensor cores.
 #include "pi_internal.cuh"
@@ -38,19 +39,6 @@ __global__ void k_zero(uint32_t* __restrict__ p, size_t n_words)
     size_t n4 = n_words / 4;
     for (size_t k = i; k < n4; k += stride) p4[k] = make_uint4(0, 0, 0, 0);
     for (size_t k = n4 * 4 + i; k < n_words; k += stride) p[k] = 0;
-}
-
-// One warp-aggregated increment of counts[key]; returns the old count plus
-// the lane's position among the lanes of its warp with the same key.
-// Every lane of the warp must call it; key == 0xffffffff means "no particle".
-__device__ __forceinline__ uint32_t aggregated_rank(uint32_t key, uint32_t* counts, unsigned lane)
-{
-    unsigned peers = __match_any_sync(FULL, key);
-    int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if ((int)lane == leader && key != 0xffffffffu) base = atomicAdd(&counts[key], __popc(peers));
-    base = __shfl_sync(FULL, base, leader);
-    return base + __popc(peers & lanemask_lt());
 }
 
 // a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
@@ -93,15 +81,29 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                 pz[j] = valid[j] ? z[i] : 0.f;
             }
         }
-        uint32_t cell[4], rank[4];
+        // all four matches, then all four atomics, then the shuffles: the
+        // atomics of one lane are in flight together instead of one by one
+        uint32_t cell[4], rank[4], key[4];
+        unsigned peers[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             bool ok = true;
-            uint32_t c = cell_of(px[j], py[j], pz[j], g, ok);
+            cell[j] = cell_of(px[j], py[j], pz[j], g, ok);
             all_ok &= ok | !valid[j];
-            cell[j] = c;
-            rank[j] = aggregated_rank(valid[j] ? c : 0xffffffffu, counts, lane);
+            key[j] = valid[j] ? cell[j] : 0xffffffffu;
+            peers[j] = __match_any_sync(FULL, key[j]);
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int leader = __ffs(peers[j]) - 1;
+            rank[j] = 0;
+            if ((int)lane == leader && key[j] != 0xffffffffu)
+                rank[j] = atomicAdd(&counts[key[j]], __popc(peers[j]));
+        }
+        const unsigned lt = lanemask_lt();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            rank[j] = __shfl_sync(FULL, rank[j], __ffs(peers[j]) - 1) + __popc(peers[j] & lt);
         if (full) {
             reinterpret_cast<uint4*>(cell_out)[grp] = make_uint4(cell[0], cell[1], cell[2], cell[3]);
             reinterpret_cast<uint4*>(rank_out)[grp] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
@@ -269,63 +271,83 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
 // ---- a4 ---------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cell,
-                                                 const uint32_t* __restrict__ rank, uint32_t n,
+                                                 const uint32_t* __restrict__ rank,
+                                                 const float* __restrict__ x,
+                                                 const float* __restrict__ y,
+                                                 const float* __restrict__ z, uint32_t n,
                                                  const uint32_t* __restrict__ offsets,
                                                  uint32_t* __restrict__ perm_u,
+                                                 float4* __restrict__ pos_u,
                                                  Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
     bool bad = false;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t c = cell[i];
-        const uint32_t slot = offsets[c] + rank[i];
-        if (slot < offsets[c + 1]) perm_u[slot] = i;
-        else bad = true;
+        const uint32_t c = cell[i], r = rank[i];
+        const float px = x[i], py = y[i], pz = z[i];
+        const uint32_t slot = offsets[c] + r;
+        if (slot < offsets[c + 1]) {
+            perm_u[slot] = i;
+            pos_u[slot] = make_float4(px, py, pz, __uint_as_float(c));
+        } else {
+            bad = true;
+        }
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
 
-// Stable order: the final slot of particle i inside cell c is the number of
-// members of c with a smaller input index.  One thread per provisional slot.
-// The same pass ranks i among its cell's members by x (ties by input index)
-// and writes P, the x-ordered copy the tiled interaction stages: because the
-// cells of an X-row are contiguous and monotone in x, every X-row of P is
-// sorted by x as a whole.  P[.].w holds the stable slot of the particle.
+// a4, second half, one thread per provisional slot k.  The members of k's
+// cell sit contiguously in perm_u / pos_u, so every member read is coalesced
+// across the warp.  From them the thread computes
+//   - the stable rank: members with a smaller input index (input order
+//     inside the cell), and writes perm, sx, sy, sz at that slot;
+//   - the x-rank: members with smaller x (ties by input index), and writes
+//     P[s0 + x-rank] = (x, y, z, stable slot).  The cells of an X-row are
+//     contiguous and monotone in x, so every X-row of P is sorted by x as a
+//     whole -- the tiled interaction stages such rows;
+//   - (the member of x-rank 0 only) xbins[c]: bytes 0..2 = members whose
+//     x-sub-bin is < 1, < 2, < 3, sub-bin = floor(4 (x - lo) inv_w) - 4 cx
+//     clamped to [0, 3] (monotone in x); byte 3 = 1 when the cell has more
+//     than 255 members, bytes 0..2 then 0 (every sub-bin starts at the cell).
 __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ perm_u,
-                                                   const uint32_t* __restrict__ cell, uint32_t n,
-                                                   const uint32_t* __restrict__ offsets,
-                                                   const float* __restrict__ x,
-                                                   const float* __restrict__ y,
-                                                   const float* __restrict__ z,
+                                                   const float4* __restrict__ pos_u, uint32_t n,
+                                                   Grid g, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
                                                    float* __restrict__ sx, float* __restrict__ sy,
                                                    float* __restrict__ sz, float4* __restrict__ P,
+                                                   uint32_t* __restrict__ xbins,
                                                    Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
     bool bad = false;
+    const float inv4 = g.inv_w[0] * 4.0f;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t i = perm_u[k];
-        if (i >= n) { bad = true; continue; }
-        const uint32_t c = cell[i];
+        const float4 pk = pos_u[k];
+        const uint32_t c = __float_as_uint(pk.w);
+        if (i >= n || c >= (uint32_t)g.n[0] * (uint32_t)g.n[1] * (uint32_t)g.n[2]) { bad = true; continue; }
         const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
-        const float xi = x[i];
-        uint32_t r = 0, xr = 0;
+        if (k < s0 || k >= s1) { bad = true; continue; }
+        const int cx4 = 4 * (int)(c % (uint32_t)g.n[0]);
+        uint32_t r = 0, xr = 0, b1 = 0, b2 = 0, b3 = 0;
         for (uint32_t q = s0; q < s1; ++q) {
             const uint32_t j = perm_u[q];
-            if (j >= n) { bad = true; break; }
-            const float xj = x[j];
+            const float xq = pos_u[q].x;
             r += (j < i) ? 1u : 0u;
-            xr += (xj < xi || (xj == xi && j < i)) ? 1u : 0u;
+            xr += (xq < pk.x || (xq == pk.x && j < i)) ? 1u : 0u;
+            const int sb =
+                min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), inv4)) - cx4, 0), 3);
+            b1 += sb < 1 ? 1u : 0u;
+            b2 += sb < 2 ? 1u : 0u;
+            b3 += sb < 3 ? 1u : 0u;
         }
         const uint32_t dst = s0 + r;
-        if (dst >= s1 || s0 + xr >= s1) { bad = true; continue; }
-        const float yi = y[i], zi = z[i];
         perm[dst] = i;
-        sx[dst] = xi;
-        sy[dst] = yi;
-        sz[dst] = zi;
-        P[s0 + xr] = make_float4(xi, yi, zi, __uint_as_float(dst));
+        sx[dst] = pk.x;
+        sy[dst] = pk.y;
+        sz[dst] = pk.z;
+        P[s0 + xr] = make_float4(pk.x, pk.y, pk.z, __uint_as_float(dst));
+        if (xr == 0) xbins[c] = (s1 - s0 > 255u) ? (1u << 24) : (b1 | (b2 << 8) | (b3 << 16));
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
@@ -370,21 +392,22 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, uint32_t n,
-                           const uint32_t* offsets, uint32_t* perm_u, Ctrl* ctrl, int num_sms,
-                           cudaStream_t s)
+cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
+                           const float* y, const float* z, uint32_t n, const uint32_t* offsets,
+                           uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
-    k_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(cell, rank, n, offsets, perm_u, ctrl);
+    k_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(cell, rank, x, y, z, n, offsets,
+                                                           perm_u, pos_u, ctrl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stabilise(const uint32_t* perm_u, const uint32_t* cell, uint32_t n,
-                             const uint32_t* offsets, const float* x, const float* y,
-                             const float* z, uint32_t* perm, float* sx, float* sy, float* sz,
-                             float4* P, Ctrl* ctrl, int num_sms, cudaStream_t s)
+cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n, const Grid& g,
+                             const uint32_t* offsets, uint32_t* perm, float* sx, float* sy,
+                             float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl, int num_sms,
+                             cudaStream_t s)
 {
-    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, cell, n, offsets, x, y, z,
-                                                             perm, sx, sy, sz, P, ctrl);
+    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, pos_u, n, g, offsets, perm, sx,
+                                                             sy, sz, P, xbins, ctrl);
     return cudaGetLastError();
 }
 

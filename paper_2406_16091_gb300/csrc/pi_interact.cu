@@ -10,21 +10,26 @@
 //   k_interact_ppnl   Alg. 1 (Par-Part-NoLoop): one thread per particle,
 //                     sources read straight from global memory.  Kept as the
 //                     comparator the paper measures its speedups against.
-//   k_interact_tiled  reads P, the copy of the sorted particles written by
-//                     binning in which every cell is ordered by x and .w
-//                     carries the stable slot; every X-row of P is sorted by
-//                     x as a whole.  One CTA per X-row of target cells (rows handed out
-//                     dynamically), processed in chunks of consecutive cells.
-//                     The 9 neighbour rows (y +- 1, z +- 1) of a chunk are
-//                     contiguous ranges of P; each is staged into shared memory
-//                     with one cp.async.bulk copy (Sec. 5.2 loads pencils along
-//                     X; here the whole 3x3 bundle of pencils is loaded at once
+//   k_interact_tiled  reads P, the x-ordered copy written by binning: the
+//                     sorted particles with every cell ordered by x, as float4
+//                     (x, y, z, stable slot); every X-row of P is sorted by x
+//                     as a whole.  One CTA per X-row of target
+//                     cells (rows handed out dynamically), in chunks of
+//                     consecutive cells.  The 9 neighbour rows (y +- 1,
+//                     z +- 1) of a chunk are contiguous ranges of P, each
+//                     staged into shared memory with one cp.async.bulk copy
+//                     (Sec. 5.2 loads pencils along X; here
+//                     the whole 3x3 bundle of pencils is loaded at once
 //                     because the sorted order makes each one contiguous).
 //                     Each thread holds one target in registers and, per
 //                     neighbour row, scans only the x-window
 //                     [x_i - w_r, x_i + w_r], w_r = sqrt(rc^2 - d_yz^2), where
-//                     d_yz is the target's distance to the row in y and z --
-//                     sources outside it cannot pass the pair test.
+//                     d_yz is the target's distance to the row in y and z:
+//                     sources outside it cannot pass the pair test.  Pairs
+//                     of candidates are evaluated with packed f32x2
+//                     arithmetic.
+#include <type_traits>
+
 #include "pi_internal.cuh"
 
 namespace pi {
@@ -63,6 +68,22 @@ template <class Acc>
 struct Sums {
     Acc s, vx, vy, vz;
     uint32_t n = 0;
+
+    // One candidate without a branch: K is computed for every candidate and
+    // zeroed when the pair test fails (the tiled kernel's inner loop, where
+    // a divergent branch per candidate costs more than the exp2).
+    __device__ __forceinline__ void pair_nb(float dx, float dy, float dz, float rc2, float kscale)
+    {
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        const bool in = r2 < rc2;
+        const float e = ex2_approx(__fmul_rn(r2, kscale));
+        const float K = in ? e : 0.f;
+        s.add(K);
+        vx.addmul(dx, K);
+        vy.addmul(dy, K);
+        vz.addmul(dz, K);
+        n += in ? 1u : 0u;
+    }
 
     // One candidate source at FP32 offset (dx, dy, dz) from the target.
     __device__ __forceinline__ void pair(float dx, float dy, float dz, float rc2, float kscale)
@@ -121,21 +142,39 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 
 // ---- tiled interaction ----------------------------------------------------------
 
-constexpr int TT = 128;      // threads per CTA; at most TT targets per chunk
-constexpr int CAP = 2048;    // staged particles per chunk (32 KB of float4)
-constexpr int MAXLX = 128;   // cells per chunk along X (table size)
+constexpr int TT = 128;                     // threads per CTA = targets per chunk
+constexpr int CAP = 1280;                   // staged particles per chunk (20 KB of float4)
+constexpr int MAXLX = 64;                   // target cells per chunk along X
+constexpr int BPC = 4;                      // x-bins per cell in the staged-row lookup
+constexpr int RBINS = (MAXLX + 2) * BPC + 2;
 
-struct Tables {
-    uint32_t cs[9][MAXLX + 4];  // start of each cell of a row, relative to the row
-    uint32_t gbeg[9];           // first index of each row in P
-    int sbeg[9];                // first index of each row in the staged buffer
-    int rlen[9];                // particles in each row (0 for rows outside the grid)
-    int xa, xb;                 // source cells [xa, xb] of every row
-    int x1;                     // end of the target cells of the chunk
-    int mode;                   // 0: staged in shared memory, 1: read from global
-    int total;                  // staged particles
-    uint32_t row;               // current X-row
-    int failed;                 // a bounded wait ran out: the CTA stops
+// One chunk: target cells [x0, x1) of an X-row, source cells [xa, xb] of the
+// 9 neighbour rows (row r has dy = r % 3 - 1, dz = r / 3 - 1).  Row r holds
+// the particles [gbeg, gbeg + rlen) of P and lands at sbeg in the staging
+// buffer (float4 entries are 16 bytes, so every copy is 16-byte aligned).
+struct Plan {
+    uint32_t gbeg[9];
+    int rlen[9];
+    int sbeg[9];
+    int xa, xb;
+    int x1;
+    int mode;   // 0: rows staged in shared memory, 1: rows read from global
+    int total;  // staged particles
+};
+
+struct Smem {
+    float4 buf[CAP + 1];  // staged rows; one spare slot keeps a read one past the end inside
+    union {
+        // mode 0: per row, first staged index (absolute) whose x-bin is >= b
+        uint16_t bin[9][RBINS];
+        // mode 1: per row, start of each cell relative to the row
+        uint32_t cs[9][MAXLX + 4];
+    } tbl;
+    Plan plan;
+    int coarse[9];  // row holds a cell without sub-bin starts: end lookups use cell bounds
+    uint32_t row;
+    int failed;
+    uint64_t bar;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -188,207 +227,343 @@ __device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t phase, 
     }
 }
 
-// Picks the chunk [x0, x1) of target cells (warp 0).  Largest x1 such that
-// the chunk has at most TT targets and its 9 source rows hold at most CAP
-// particles; a single cell whose rows exceed CAP is read from global memory.
-__device__ void choose_chunk(const InteractArgs& a, Tables& t, int x0, int cy, int cz, unsigned lane)
+// Plans the chunk starting at x0 (warp 0, one pass of global loads): the
+// largest x1 such that the chunk has at most TT targets and its 9 source
+// rows hold at most CAP particles, plus each row's range.  A single cell
+// whose rows exceed CAP is read from global memory (mode 1).
+__device__ void plan_chunk(const InteractArgs& a, Plan& p, int x0, int cy, int cz, unsigned lane)
 {
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
     const uint32_t rb0 = (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
-    const uint32_t tgt0 = a.offsets[rb0 + x0];
+    const int xa = max(x0 - 1, 0);
     const int xmax = min(nx, x0 + MAXLX);
-    int best = 0;            // largest valid x1 found
-    bool first_fits = true;  // rows of [x0, x0+1) fit in CAP
+    uint32_t rb[9], rstart[9];
+    bool rok[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int by = cy + r % 3 - 1, bz = cz + r / 3 - 1;
+        rok[r] = by >= 0 && by < ny && bz >= 0 && bz < nz;
+        rb[r] = rok[r] ? (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) : 0u;
+        rstart[r] = rok[r] ? a.offsets[rb[r] + xa] : 0u;
+    }
+    const uint32_t tgt0 = a.offsets[rb0 + x0];
+    int best = 0;
+    bool first_fits = true;
+    uint32_t best_end[9], first_end[9];
     for (int base = x0 + 1; base <= xmax; base += 32) {
         const int x1 = base + (int)lane;
-        bool valid = false;
-        bool fits = true;
+        const int xb = min(x1, nx - 1);
+        bool valid = false, fits = true;
+        uint32_t rend[9];
         if (x1 <= xmax) {
             const uint32_t targets = a.offsets[rb0 + x1] - tgt0;
             uint32_t staged = 0;
-            const int xa = max(x0 - 1, 0), xb = min(x1, nx - 1);
 #pragma unroll
             for (int r = 0; r < 9; ++r) {
-                const int by = cy + r % 3 - 1, bz = cz + r / 3 - 1;
-                if (by < 0 || by >= ny || bz < 0 || bz >= nz) continue;
-                const uint32_t rb = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
-                staged += a.offsets[rb + xb + 1] - a.offsets[rb + xa];
+                rend[r] = rok[r] ? a.offsets[rb[r] + xb + 1] : 0u;
+                staged += rend[r] - rstart[r];
             }
             fits = staged <= (uint32_t)CAP;
             valid = fits && targets <= (uint32_t)TT;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 9; ++r) rend[r] = rstart[r];
         }
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (base == x0 + 1) first_fits = __shfl_sync(0xffffffffu, fits, 0);
-        if (vm) best = base + 31 - __clz(vm);
+        if (base == x0 + 1) {
+            first_fits = __shfl_sync(0xffffffffu, fits, 0);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) first_end[r] = __shfl_sync(0xffffffffu, rend[r], 0);
+        }
+        if (vm) {
+            const int L = 31 - __clz(vm);
+            best = base + L;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) best_end[r] = __shfl_sync(0xffffffffu, rend[r], L);
+        }
         if (vm != 0xffffffffu) break;
     }
+    int x1 = best, mode = 0;
+    if (best == 0) {
+        x1 = x0 + 1;
+        mode = first_fits ? 0 : 1;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) best_end[r] = first_end[r];
+    }
+    // lane r < 9 owns row r
+    uint32_t gb = 0, len = 0;
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+        if ((int)lane == r) {
+            gb = rstart[r];
+            len = best_end[r] - rstart[r];
+        }
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    if (lane < 9) {
+        p.gbeg[lane] = gb;
+        p.rlen[lane] = (int)len;
+        p.sbeg[lane] = (int)(incl - len);
+    }
+    if (lane == 8) p.total = (int)incl;
     if (lane == 0) {
-        if (best == 0) {
-            t.x1 = x0 + 1;
-            t.mode = first_fits ? 0 : 1;
-        } else {
-            t.x1 = best;
-            t.mode = 0;
+        p.xa = xa;
+        p.xb = min(x1, nx - 1);
+        p.x1 = x1;
+        p.mode = mode;
+    }
+}
+
+// x-bin used by the staged-row lookup: monotone in x (FP32 round-to-nearest
+// subtract and multiply, floor), relative to the first source cell xa.
+__device__ __forceinline__ int xbin(float x, float lo, float inv4, int base, int nb)
+{
+    const int b = __float2int_rd(__fmul_rn(__fsub_rn(x, lo), inv4)) - base;
+    return min(max(b, 0), nb - 1);
+}
+
+// Distances (minus slack, at least 0) from a target to the faces of its own
+// cell in y and z; a row offset by dy/dz is at least that far in y/z.
+struct Faces {
+    float y_lo, y_hi, z_lo, z_hi;
+};
+
+__device__ __forceinline__ Faces faces_of(const InteractArgs& a, float yt, float zt, int cy, int cz)
+{
+    const float wy = a.cell_w[1], wz = a.cell_w[2];
+    Faces f;
+    f.y_lo = fmaxf(yt - fmaf((float)cy, wy, a.g.lo[1]) - a.slack, 0.f);
+    f.y_hi = fmaxf(fmaf((float)(cy + 1), wy, a.g.lo[1]) - yt - a.slack, 0.f);
+    f.z_lo = fmaxf(zt - fmaf((float)cz, wz, a.g.lo[2]) - a.slack, 0.f);
+    f.z_hi = fmaxf(fmaf((float)(cz + 1), wz, a.g.lo[2]) - zt - a.slack, 0.f);
+    return f;
+}
+
+// Half-width of the x-window of row rr, or a negative value if the row is
+// out of reach.  Conservative: rc^2 is inflated by 2e-5 and the slack added.
+__device__ __forceinline__ float row_halfwidth(const InteractArgs& a, const Faces& f, int rr)
+{
+    const int dy = rr % 3 - 1, dz = rr / 3 - 1;
+    const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
+    const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
+    const float rcm2 = a.rc2 * 1.00002f;
+    const float t = rcm2 - fmaf(ey, ey, ez * ez);
+    if (!(t > 0.f)) return -1.f;
+    const float tt = fmaxf(t, 1e-30f);
+    return tt * rsqrtf(tt) + a.slack;
+}
+
+// Global-memory path (mode 1) for one target: per row, binary search of the
+// window start inside the cell of x - w, scan until x > x + w.
+template <class Acc>
+__device__ __forceinline__ void target_sums_global(const InteractArgs& a, const Smem& sm, float xt,
+                                                   float yt, float zt, int cy, int cz, Sums<Acc>& r)
+{
+    const Plan& p = sm.plan;
+    const Faces f = faces_of(a, yt, zt, cy, cz);
+#pragma unroll 1
+    for (int rr = 0; rr < 9; ++rr) {
+        const int len = p.rlen[rr];
+        if (len == 0) continue;
+        const float w = row_halfwidth(a, f, rr);
+        if (w < 0.f) continue;
+        const float xlo = xt - w, xhi = xt + w;
+        int k = axis_cell(xlo, a.g.lo[0], a.g.inv_w[0], a.g.n[0]) - p.xa;
+        k = min(max(k, 0), p.xb - p.xa);
+        const float4* row = a.P + p.gbeg[rr];
+        int lo = (int)sm.tbl.cs[rr][k], hi = (int)sm.tbl.cs[rr][k + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (row[mid].x < xlo) lo = mid + 1;
+            else hi = mid;
+        }
+        for (int j = lo; j < len; ++j) {
+            const float4 q = row[j];
+            if (q.x > xhi) break;
+            r.pair(__fsub_rn(q.x, xt), __fsub_rn(q.y, yt), __fsub_rn(q.z, zt), a.rc2, a.kscale);
         }
     }
 }
 
-// Sums of one target over the 9 rows.  SRC is the staged buffer (smem) or P.
-template <class Acc, bool SMEM>
-__device__ __forceinline__ void target_sums(const InteractArgs& a, const Tables& t, const float4* src,
-                                            float4 me, int cy, int cz, Sums<Acc>& r)
+// Two candidates at once with packed FP32 (f32x2) arithmetic: every element
+// is rounded exactly as the scalar operation would be, so the pair test and
+// the sums are those of Sums::pair_nb.
+struct PackedSums {
+    float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
+           vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
+
+    __device__ __forceinline__ void pair2(float2 px, float2 py, float2 pz, float2 mx, float2 my,
+                                          float2 mz, float rc2, float2 ks)
+    {
+        const float2 dx = __fadd2_rn(px, mx);
+        const float2 dy = __fadd2_rn(py, my);
+        const float2 dz = __fadd2_rn(pz, mz);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 t = __fmul2_rn(r2, ks);
+        const bool i0 = r2.x < rc2, i1 = r2.y < rc2;
+        const float e0 = ex2_approx(t.x), e1 = ex2_approx(t.y);
+        const float2 K = make_float2(i0 ? e0 : 0.f, i1 ? e1 : 0.f);
+        s = __fadd2_rn(s, K);
+        vx = __ffma2_rn(dx, K, vx);
+        vy = __ffma2_rn(dy, K, vy);
+        vz = __ffma2_rn(dz, K, vz);
+        n = __fadd2_rn(n, make_float2(i0 ? 1.f : 0.f, i1 ? 1.f : 0.f));
+    }
+};
+
+// Sums of one target over the staged rows (mode 0).  Per row: the x-window
+// from the row's lookup table, trimmed to [x - w, x + w] exactly; every
+// source in it is a candidate, taken two at a time.
+template <class Acc>
+__device__ __forceinline__ void target_sums_staged(const InteractArgs& a, const Smem& sm, float xt,
+                                                   float yt, float zt, int cy, int cz, int ncell,
+                                                   float inv4, Sums<Acc>& r)
 {
-    const float xt = me.x, yt = me.y, zt = me.z;
-    const float wy = 1.0f / a.g.inv_w[1], wz = 1.0f / a.g.inv_w[2];
-    // distances to the lower / upper faces of the own cell in y and z
-    const float fy_lo = fmaxf(yt - fmaf((float)cy, wy, a.g.lo[1]) - a.slack, 0.f);
-    const float fy_hi = fmaxf(fmaf((float)(cy + 1), wy, a.g.lo[1]) - yt - a.slack, 0.f);
-    const float fz_lo = fmaxf(zt - fmaf((float)cz, wz, a.g.lo[2]) - a.slack, 0.f);
-    const float fz_hi = fmaxf(fmaf((float)(cz + 1), wz, a.g.lo[2]) - zt - a.slack, 0.f);
-    const float rcm2 = a.rc2 * 1.00002f;
+    const Plan& p = sm.plan;
+    const Faces f = faces_of(a, yt, zt, cy, cz);
+    const int nb = ncell * BPC, base = BPC * p.xa;
+    constexpr bool packed = std::is_same<Acc, PlainAcc>::value;
+    PackedSums ps;
+    const float2 mx = make_float2(-xt, -xt), my = make_float2(-yt, -yt), mz = make_float2(-zt, -zt),
+                 ks = make_float2(a.kscale, a.kscale);
 #pragma unroll 1
     for (int rr = 0; rr < 9; ++rr) {
-        const int len = t.rlen[rr];
-        if (len == 0) continue;
-        const int dy = rr % 3 - 1, dz = rr / 3 - 1;
-        const float ey = dy < 0 ? fy_lo : (dy > 0 ? fy_hi : 0.f);
-        const float ez = dz < 0 ? fz_lo : (dz > 0 ? fz_hi : 0.f);
-        const float d2 = fmaf(ey, ey, ez * ez);
-        if (d2 >= rcm2) continue;
-        const float w = __fsqrt_rn(rcm2 - d2) + a.slack;
+        if (p.rlen[rr] == 0) continue;
+        const float w = row_halfwidth(a, f, rr);
+        if (w < 0.f) continue;
         const float xlo = xt - w, xhi = xt + w;
-        // first source with x >= xlo: start in the cell of xlo (cells are
-        // monotone in x), then binary search inside that cell
-        int k = axis_cell(xlo, a.g.lo[0], a.g.inv_w[0], a.g.n[0]) - t.xa;
-        k = max(k, 0);
-        const int kmax = t.xb - t.xa;
-        k = min(k, kmax);
-        const float4* rowg = SMEM ? (src + t.sbeg[rr]) : (src + t.gbeg[rr]);
-        int lo = t.cs[rr][k], hi = t.cs[rr][k + 1];
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (rowg[mid].x < xlo) lo = mid + 1;
-            else hi = mid;
+        int j = sm.tbl.bin[rr][xbin(xlo, a.g.lo[0], inv4, base, nb)];
+        int bh = xbin(xhi, a.g.lo[0], inv4, base, nb) + 1;
+        if (sm.coarse[rr]) bh = (bh + BPC - 1) / BPC * BPC;
+        int je = sm.tbl.bin[rr][bh];
+        while (j < je && sm.buf[j].x < xlo) ++j;
+        while (je > j && sm.buf[je - 1].x > xhi) --je;
+        // window [j, je): every source in it is a candidate
+        if (packed) {
+            for (; j + 1 < je; j += 2) {
+                const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
+                ps.pair2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z), mx,
+                         my, mz, a.rc2, ks);
+            }
+        } else {
+            for (; j + 1 < je; j += 2) {
+                const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
+                r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), a.rc2, a.kscale);
+                r.pair_nb(__fsub_rn(s1.x, xt), __fsub_rn(s1.y, yt), __fsub_rn(s1.z, zt), a.rc2, a.kscale);
+            }
         }
-        for (int j = lo; j < len; ++j) {
-            const float4 s = rowg[j];
-            if (s.x > xhi) break;
-            r.pair(__fsub_rn(s.x, xt), __fsub_rn(s.y, yt), __fsub_rn(s.z, zt), a.rc2, a.kscale);
+        if (j < je) {
+            const float4 s0 = sm.buf[j];
+            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), a.rc2, a.kscale);
         }
+    }
+    if (packed) {
+        r.s.add(ps.s.x + ps.s.y);
+        r.vx.add(ps.vx.x + ps.vx.y);
+        r.vy.add(ps.vy.x + ps.vy.y);
+        r.vz.add(ps.vz.x + ps.vz.y);
+        r.n += (uint32_t)(ps.n.x + ps.n.y);
     }
 }
 
 template <class Acc>
-__global__ void __launch_bounds__(TT) k_interact_tiled(InteractArgs a)
+__global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
 {
-    __shared__ __align__(16) float4 buf[CAP];
-    __shared__ Tables t;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ Smem sm;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
     const uint32_t rows = (uint32_t)ny * (uint32_t)nz;
+    const float inv4 = a.g.inv_w[0] * (float)BPC;
     // K(0) of this hardware path: the self pair adds exactly this to S
     const float k0 = ex2_approx(0.f);
 
-    if (threadIdx.x == 0) {
-        t.failed = 0;
-        bar_init(&bar, 1);
+    if (tid == 0) {
+        sm.failed = 0;
+        bar_init(&sm.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     uint32_t phase = 0;
 
     for (;;) {
-        if (threadIdx.x == 0) t.row = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
+        if (tid == 0) sm.row = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
         __syncthreads();
-        const uint32_t row = t.row;
-        if (row >= rows || t.failed) break;
+        const uint32_t row = sm.row;
+        if (row >= rows || sm.failed) break;
         const int cy = (int)(row % (uint32_t)ny), cz = (int)(row / (uint32_t)ny);
         const uint32_t rb0 = (uint32_t)nx * row;
 
         for (int x0 = 0; x0 < nx;) {
-            if (warp == 0) choose_chunk(a, t, x0, cy, cz, lane);
-            __syncthreads();
-            const int x1 = t.x1;
-            const int xa = max(x0 - 1, 0), xb = min(x1, nx - 1);
-            // row ranges (warp 0, one lane per row)
             if (warp == 0) {
-                uint32_t gb = 0, len = 0;
-                if (lane < 9) {
-                    const int by = cy + (int)lane % 3 - 1, bz = cz + (int)lane / 3 - 1;
-                    if (by >= 0 && by < ny && bz >= 0 && bz < nz) {
-                        const uint32_t rb = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
-                        gb = a.offsets[rb + xa];
-                        len = a.offsets[rb + xb + 1] - gb;
-                    }
-                }
-                uint32_t incl = len;
-#pragma unroll
-                for (int o = 1; o < 16; o <<= 1) {
-                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= (unsigned)o) incl += v;
-                }
-                if (lane < 9) {
-                    t.gbeg[lane] = gb;
-                    t.rlen[lane] = (int)len;
-                    t.sbeg[lane] = (int)(incl - len);
-                }
-                if (lane == 8) t.total = (int)incl;
-                if (lane == 0) {
-                    t.xa = xa;
-                    t.xb = xb;
+                if (lane < 9) sm.coarse[lane] = 0;
+                plan_chunk(a, sm.plan, x0, cy, cz, lane);
+                __syncwarp();
+                if (lane == 0 && sm.plan.mode == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_expect_tx(&sm.bar, (uint32_t)sm.plan.total * 16u);
+                    for (int rr = 0; rr < 9; ++rr)
+                        if (sm.plan.rlen[rr] > 0)
+                            bulk_g2s(&sm.buf[sm.plan.sbeg[rr]], a.P + sm.plan.gbeg[rr],
+                                     (uint32_t)sm.plan.rlen[rr] * 16u, &sm.bar);
                 }
             }
             __syncthreads();
-            // per-row cell start tables (relative to the row start)
-            const int ncell = xb - xa + 1;
-            for (int e = threadIdx.x; e < 9 * (ncell + 1); e += TT) {
+            const Plan& p = sm.plan;
+            const int x1 = p.x1, mode = p.mode, xa = p.xa;
+            const int ncell = p.xb - xa + 1;
+            // Row lookup tables, built from the offsets and the per-cell
+            // sub-bin starts while the bulk copies are in flight.
+            for (int e = tid; e < 9 * (ncell + 1); e += TT) {
                 const int rr = e / (ncell + 1), k = e % (ncell + 1);
+                if (p.rlen[rr] == 0) continue;
                 const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
-                uint32_t v = 0;
-                if (by >= 0 && by < ny && bz >= 0 && bz < nz) {
-                    const uint32_t rb = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
-                    v = a.offsets[rb + xa + k] - t.gbeg[rr];
+                const uint32_t cidx = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xa + k;
+                const uint32_t g = a.offsets[cidx];
+                if (mode == 0) {
+                    const int start = p.sbeg[rr] + (int)(g - p.gbeg[rr]);
+                    if (k == ncell) {
+                        sm.tbl.bin[rr][BPC * ncell] = (uint16_t)start;
+                    } else {
+                        const uint32_t w = a.xbins[cidx];
+                        if (w >> 24) sm.coarse[rr] = 1;
+                        sm.tbl.bin[rr][BPC * k] = (uint16_t)start;
+                        sm.tbl.bin[rr][BPC * k + 1] = (uint16_t)(start + (int)(w & 255u));
+                        sm.tbl.bin[rr][BPC * k + 2] = (uint16_t)(start + (int)((w >> 8) & 255u));
+                        sm.tbl.bin[rr][BPC * k + 3] = (uint16_t)(start + (int)((w >> 16) & 255u));
+                    }
+                } else {
+                    sm.tbl.cs[rr][k] = g - p.gbeg[rr];
                 }
-                t.cs[rr][k] = v;
             }
-            const int mode = t.mode;
-            if (mode == 0 && threadIdx.x == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                bar_expect_tx(&bar, (uint32_t)t.total * 16u);
-                for (int rr = 0; rr < 9; ++rr)
-                    if (t.rlen[rr] > 0)
-                        bulk_g2s(&buf[t.sbeg[rr]], a.P + t.gbeg[rr], (uint32_t)t.rlen[rr] * 16u, &bar);
-            }
-            __syncthreads();
             if (mode == 0) {
-                if (!bar_wait_bounded(&bar, phase, a.wait_limit_ns)) {
-                    t.failed = 1;
+                if (!bar_wait_bounded(&sm.bar, phase, a.wait_limit_ns)) {
+                    sm.failed = 1;
                     atomicOr(&a.ctrl->error, ERR_TIMEOUT);
                     // let the copies in flight land before the CTA exits
-                    bar_wait_bounded(&bar, phase, a.wait_limit_ns);
+                    bar_wait_bounded(&sm.bar, phase, a.wait_limit_ns);
                 }
                 phase ^= 1u;
             }
-            __syncthreads();  // t.failed is uniform from here on
-            // targets: cells [x0, x1) of the centre row (row 4)
+            __syncthreads();  // tables ready; sm.failed is uniform from here on
             const uint32_t tb = a.offsets[rb0 + x0], te = a.offsets[rb0 + x1];
-            const int tloc = (int)(tb - t.gbeg[4]);
             const int ntarget = (int)(te - tb);
-            if (!t.failed) {
-                for (int q = threadIdx.x; q < ntarget; q += TT) {
+            // staged index of the first target (the centre row is row 4)
+            const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
+            if (!sm.failed) {
+                for (int q0 = 0; q0 < ntarget; q0 += TT) {
+                    const int q = q0 + (int)tid;
+                    if (q >= ntarget) continue;
                     Sums<Acc> r;
-                    float4 me;
-                    if (mode == 0) {
-                        me = buf[t.sbeg[4] + tloc + q];
-                        target_sums<Acc, true>(a, t, buf, me, cy, cz, r);
-                    } else {
-                        me = a.P[tb + q];
-                        target_sums<Acc, false>(a, t, a.P, me, cy, cz, r);
-                    }
+                    const float4 me = mode == 0 ? sm.buf[t0 + q] : a.P[tb + q];
+                    if (mode == 0) target_sums_staged<Acc>(a, sm, me.x, me.y, me.z, cy, cz, ncell, inv4, r);
+                    else target_sums_global<Acc>(a, sm, me.x, me.y, me.z, cy, cz, r);
                     store_out(a, __float_as_uint(me.w), r, k0, 1u);
                 }
             }
@@ -416,10 +591,12 @@ cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms
 {
     const uint32_t rows = (uint32_t)a.g.n[1] * (uint32_t)a.g.n[2];
     int per_sm = 0;
+    cudaError_t oe;
     if (kahan)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<KahanAcc>, TT, 0);
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<KahanAcc>, TT, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<PlainAcc>, TT, 0);
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<PlainAcc>, TT, 0);
+    if (oe != cudaSuccess) return oe;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = (uint64_t)num_sms * per_sm;
     if (grid > rows) grid = rows;

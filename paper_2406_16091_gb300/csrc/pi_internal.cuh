@@ -3,11 +3,13 @@
 // Layout of the device state of one context (one cudaMalloc arena):
 //   Ctrl            control words (scan ticket, error bits, M_C)
 //   counts[C]       particles per cell
+//   xbins[C]        per cell, where its 4 x-sub-bins start in P (k_xorder)
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
 //   cell[n_max]     cell of each input particle            (binning scratch)
 //   rank[n_max]     provisional slot inside its cell        (binning scratch)
 //   perm_u[n_max]   unstable slot -> input index            (binning scratch)
+//   pos_u[n_max]    float4 (x, y, z, cell) in unstable slot order (binning scratch)
 //   perm[n_max]     stable   slot -> input index
 //   sx, sy, sz      positions in sorted order
 //   P[n_max]        float4 (x, y, z, stable slot): sorted order, and inside
@@ -94,16 +96,17 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
                         uint64_t wait_limit_ns, int withhold_first, cudaStream_t s);
-cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, uint32_t n,
-                           const uint32_t* offsets, uint32_t* perm_u, Ctrl* ctrl, int num_sms,
-                           cudaStream_t s);
-cudaError_t launch_stabilise(const uint32_t* perm_u, const uint32_t* cell, uint32_t n,
-                             const uint32_t* offsets, const float* x, const float* y,
-                             const float* z, uint32_t* perm, float* sx, float* sy, float* sz,
-                             float4* P, Ctrl* ctrl, int num_sms, cudaStream_t s);
+cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
+                           const float* y, const float* z, uint32_t n, const uint32_t* offsets,
+                           uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s);
+cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n, const Grid& g,
+                             const uint32_t* offsets, uint32_t* perm, float* sx, float* sy,
+                             float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl, int num_sms,
+                             cudaStream_t s);
 
 struct InteractArgs {
     const float4* P;        // x-ordered copy: (x, y, z, stable slot as bits)
+    const uint32_t* xbins;  // per cell: starts of its 4 x-sub-bins (see k_xorder)
     const float* sx;
     const float* sy;
     const float* sz;
@@ -123,6 +126,7 @@ struct InteractArgs {
     float slack;            // absolute margin for the conservative windows
     uint64_t wait_limit_ns; // bound of every device-side wait
     uint32_t seq;           // launch number of the tiled kernel (row counter slot)
+    float cell_w[3];        // cell widths (hi - lo) / n, computed in FP64
 };
 
 // Each adds the number of kernels it launched to *launches.
