@@ -82,10 +82,24 @@ enum {
     /* Test hook for the failure path: when 1, the first tile of the scan
      * never publishes its prefix, so the other tiles' bounded waits run out
      * and pi_sync_status() returns PI_ERR_TIMEOUT.  Default 0. */
-    PI_OPT_TEST_WITHHOLD_SCAN = 4
+    PI_OPT_TEST_WITHHOLD_SCAN = 4,
+    /* Interaction kernel K (PI_KERNEL_*), default PI_KERNEL_GAUSSIAN. */
+    PI_OPT_KERNEL = 5
 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
 enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
+
+/* Interaction kernels K(r) (the h argument of pi_interact is their length):
+ *   PI_KERNEL_GAUSSIAN  exp(-r^2 / h^2).
+ *   PI_KERNEL_LJ        the Lennard-Jones potential of Sec. 7.1 with E0 = 1,
+ *                       length sigma = h and a softening of sigma/10:
+ *                       4 (s^6 - s^3), s = sigma^2 / (r^2 + sigma^2 / 100).
+ *   PI_KERNEL_LOWFLOP   1: the cheap synthetic kernel of Sec. 7.2 (S counts
+ *                       the neighbours, V sums their offsets).
+ *   PI_KERNEL_HIGHFLOP  the Lennard-Jones value followed by 150 FLOP that
+ *                       leave it unchanged: the expensive synthetic kernel of
+ *                       Sec. 7.2 (Fig. 7). */
+enum { PI_KERNEL_GAUSSIAN = 0, PI_KERNEL_LJ = 1, PI_KERNEL_LOWFLOP = 2, PI_KERNEL_HIGHFLOP = 3 };
 
 /* Creates a context on the current CUDA device for boxes of the given shape.
  *   box   host pointer; lo < hi on every axis, all finite.
@@ -143,7 +157,48 @@ pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float
                       int64_t n, float h, float* hS, float* hVx, float* hVy, float* hVz,
                       uint32_t* hnbr, int out_order, pi_stream stream);
 
-/* Grid dimensions (nx, ny, nz) into dims (host array of 3). */
+/* ---- Batches: many independent systems per context --------------------
+ *
+ * A batch context holds num_systems independent systems, each with its own
+ * box, cutoff and particle capacity; one pi_batch_bin / pi_batch_interact
+ * runs every step of the path for all of them in one launch per kernel
+ * (the interaction hands out the X-rows of all systems from one work
+ * queue).  Particles are concatenated in system order: in a call with
+ * counts n[0..S-1], system s owns the input entries and the sorted slots
+ * [P_s, P_s + n[s]), P_s = n[0] + ... + n[s-1]; its cells follow those of
+ * the systems before it in the counts/offsets arrays.  The single-system
+ * calls above are the num_systems = 1 case.
+ */
+
+/* Creates a batch context on the current device.  boxes, r_c and n_max are
+ * host arrays of num_systems entries (1 <= num_systems <= 2048), each
+ * checked as in pi_create; the total of the cells stays below 2^31 and the
+ * total of n_max below 2^31 - 64.
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA. */
+pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float* r_c,
+                          const int64_t* n_max, pi_ctx** out);
+
+/* Binning of every system (as pi_bin).  x, y, z: device arrays of the
+ * concatenated positions; n: host array of num_systems counts, 0 <= n[s] <=
+ * n_max[s].  Errors: as pi_bin. */
+pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float* z,
+                       const int64_t* n, pi_stream stream);
+
+/* Interaction of every system (as pi_interact).  h: host array of
+ * num_systems kernel lengths, each > 0 and finite.  Outputs are device
+ * arrays of the concatenated particles.  Errors: as pi_interact. */
+pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
+                            uint32_t* nbr, int out_order, pi_stream stream);
+
+/* Number of systems, total cells and total particle capacity (host outputs,
+ * any may be NULL). */
+pi_status pi_batch_info(const pi_ctx* ctx, int32_t* num_systems, int64_t* total_cells,
+                        int64_t* total_n_max);
+
+/* Grid dimensions (nx, ny, nz) of one system into dims (host array of 3). */
+pi_status pi_batch_grid(const pi_ctx* ctx, int32_t system, int32_t dims[3]);
+
+/* Grid dimensions (nx, ny, nz) of the first system into dims (host array of 3). */
 pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3]);
 
 /* Borrowed device pointers to the binning results, valid until the next

@@ -66,9 +66,9 @@ def lib():
         L.pio_exclusive_scan.restype = None
         L.pio_bin.argtypes = [P, P, P, i64, P, P, P, P, P, P, P, P, P, P]
         L.pio_bin.restype = ctypes.c_int
-        L.pio_interact.argtypes = [P, P, P, i64, P, P, f32, f32] + [P] * 10
+        L.pio_interact.argtypes = [P, P, P, i64, P, P, f32, f32, ctypes.c_int] + [P] * 10
         L.pio_interact.restype = ctypes.c_int
-        L.pio_brute.argtypes = [P, P, P, i64, f32, f32, P, P, P, P, P]
+        L.pio_brute.argtypes = [P, P, P, i64, f32, f32, ctypes.c_int, P, P, P, P, P]
         L.pio_brute.restype = ctypes.c_int
         L.pio_num_threads.argtypes = []
         L.pio_num_threads.restype = ctypes.c_int
@@ -173,9 +173,13 @@ class Interactions:
     candidates: int
 
 
-def interact(b: Binned, rc: float, h: float) -> Interactions:
+GAUSSIAN, LJ, LOWFLOP, HIGHFLOP = 0, 1, 2, 3
+
+
+def interact(b: Binned, rc: float, h: float, kernel: int = GAUSSIAN) -> Interactions:
     """Per-particle sums over the clipped 27-cell stencil (Sec. 2, Sec. 3),
-    in the sorted order of ``b``, FP64 accumulation."""
+    in the sorted order of ``b``, FP64 accumulation.  ``kernel``: GAUSSIAN,
+    LJ (Sec. 7.1, sigma = h), LOWFLOP or HIGHFLOP (Sec. 7.2)."""
     n = len(b.sx)
     out = [np.zeros(n, np.float64) for _ in range(4)]
     nbr = np.zeros(n, np.uint32)
@@ -183,21 +187,21 @@ def interact(b: Binned, rc: float, h: float) -> Interactions:
     cand = np.zeros(1, np.uint64)
     d = np.asarray(b.dims, np.int32)
     st = lib().pio_interact(_p(b.sx), _p(b.sy), _p(b.sz), n, _p(b.offsets), _p(d),
-                            ctypes.c_float(rc), ctypes.c_float(h),
+                            ctypes.c_float(rc), ctypes.c_float(h), int(kernel),
                             *[_p(a) for a in out], _p(nbr), *[_p(a) for a in ab], _p(cand))
     if st != 0:
         raise ValueError("oracle interact: bad arguments")
     return Interactions(*out, nbr, *ab, int(cand[0]))
 
 
-def brute(x, y, z, rc: float, h: float):
+def brute(x, y, z, rc: float, h: float, kernel: int = GAUSSIAN):
     """O(N^2) evaluation of the definition of Sec. 2 in input order.
     Returns (S, Vx, Vy, Vz, nbr)."""
     x, y, z = _f32(x), _f32(y), _f32(z)
     n = len(x)
     out = [np.zeros(n, np.float64) for _ in range(4)]
     nbr = np.zeros(n, np.uint32)
-    st = lib().pio_brute(_p(x), _p(y), _p(z), n, ctypes.c_float(rc), ctypes.c_float(h),
+    st = lib().pio_brute(_p(x), _p(y), _p(z), n, ctypes.c_float(rc), ctypes.c_float(h), int(kernel),
                          *[_p(a) for a in out], _p(nbr))
     if st != 0:
         raise ValueError("oracle brute: bad arguments")

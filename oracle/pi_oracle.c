@@ -22,9 +22,14 @@
  *     (Max(0, .) / Min(limit, .)), i.e. the box is not periodic.
  *
  * Readings where the paper is silent (each is also listed in the design doc):
- *   - K is the Gaussian exp(-r^2/h^2); outputs S_i = sum K and
+ *   - K is the Gaussian exp(-r^2/h^2) by default; outputs S_i = sum K and
  *     V_i = sum (p_j - p_i) K (the paper's Lennard-Jones constants are not
- *     fixed by its text).
+ *     fixed by its text).  The other kernels, for the comparisons of
+ *     Sec. 7.1-7.2: Lennard-Jones 4 E0 ((sigma/r)^12 - (sigma/r)^6) with
+ *     E0 = 1, sigma = h and r^2 softened to r^2 + sigma^2/100 (Sec. 7.1 says
+ *     a softening is used without giving it); the low-FLOP kernel K = 1;
+ *     the high-FLOP kernel, whose value is the Lennard-Jones one (its extra
+ *     work changes nothing in the result).
  *   - Grid: n_d = max(1, floor((hi_d - lo_d) / r_c)) in FP64, so the cell
  *     width is >= r_c.
  *   - Cell index, in FP32: c_d = clamp(floor((x_d - lo_d) * inv_w_d), 0,
@@ -185,6 +190,36 @@ static int within_cutoff(float dx, float dy, float dz, float rc2)
     return r2 < rc2;
 }
 
+#define PIO_GAUSSIAN 0
+#define PIO_LJ 1
+#define PIO_LOWFLOP 2
+#define PIO_HIGHFLOP 3
+
+/* K for a pair at squared distance r2 (FP64).  *mag is the size the error of
+ * an FP32 evaluation scales with: |K| for the Gaussian and the constant, and
+ * for Lennard-Jones the sum of the magnitudes of its two terms, 4 (s^6 + s^3),
+ * because 4 (s^6 - s^3) cancels near its zero crossing. */
+static double kernel_value(int kernel, double r2, double h, double* mag)
+{
+    if (kernel == PIO_LJ || kernel == PIO_HIGHFLOP) {
+        double sig2 = h * h;
+        double s = sig2 / (r2 + sig2 / 100.0);
+        double s3 = s * s * s;
+        double s6 = s3 * s3;
+        *mag = 4.0 * (s6 + s3);
+        return 4.0 * (s6 - s3);
+    }
+    if (kernel == PIO_LOWFLOP) {
+        *mag = 1.0;
+        return 1.0;
+    }
+    {
+        double K = exp(-r2 / (h * h));
+        *mag = K;
+        return K;
+    }
+}
+
 /* For every particle k in sorted order: neighbour count, S = sum K,
  * V = sum (p_j - p_k) K over j != k in the clipped 27-cell stencil with the
  * FP32 predicate, all sums in FP64 (exact differences of the FP32 positions).
@@ -192,7 +227,7 @@ static int within_cutoff(float dx, float dy, float dz, float rc2)
  * tolerance) and the number of candidate pairs looked at (j != k in the
  * stencil).  Any of the optional outputs may be NULL. */
 int pio_interact(const float* sx, const float* sy, const float* sz, int64_t n,
-                 const uint32_t* offsets, const int32_t dims[3], float rc, float h,
+                 const uint32_t* offsets, const int32_t dims[3], float rc, float h, int kernel,
                  double* S, double* Vx, double* Vy, double* Vz, uint32_t* nbr,
                  double* absS, double* absVx, double* absVy, double* absVz,
                  uint64_t* candidates)
@@ -202,7 +237,6 @@ int pio_interact(const float* sx, const float* sy, const float* sz, int64_t n,
     const int64_t C = nx * ny * nz;
     if ((int64_t)offsets[C] != n) return PIO_BAD_ARG;
     const float rc2 = rc * rc;  /* FP32 product, round to nearest */
-    const double h2 = (double)h * (double)h;
     uint64_t total_candidates = 0;
 
 #ifdef _OPENMP
@@ -231,16 +265,17 @@ int pio_interact(const float* sx, const float* sy, const float* sz, int64_t n,
                             double ddy = (double)sy[j] - (double)yk;
                             double ddz = (double)sz[j] - (double)zk;
                             double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            double K = exp(-r2 / h2);
+                            double mag;
+                            double K = kernel_value(kernel, r2, (double)h, &mag);
                             cnt += 1;
                             s += K;
                             vx += ddx * K;
                             vy += ddy * K;
                             vz += ddz * K;
-                            as += fabs(K);
-                            avx += fabs(ddx * K);
-                            avy += fabs(ddy * K);
-                            avz += fabs(ddz * K);
+                            as += mag;
+                            avx += fabs(ddx) * mag;
+                            avy += fabs(ddy) * mag;
+                            avz += fabs(ddz) * mag;
                         }
                     }
                 }
@@ -263,11 +298,10 @@ int pio_interact(const float* sx, const float* sy, const float* sz, int64_t n,
 /* O(N^2) brute force over the input order with the same FP32 predicate and
  * FP64 sums: the problem definition of Sec. 2 with no grid at all. */
 int pio_brute(const float* x, const float* y, const float* z, int64_t n, float rc, float h,
-              double* S, double* Vx, double* Vy, double* Vz, uint32_t* nbr)
+              int kernel, double* S, double* Vx, double* Vy, double* Vz, uint32_t* nbr)
 {
     if (!(rc > 0.0f) || !(h > 0.0f)) return PIO_BAD_ARG;
     const float rc2 = rc * rc;
-    const double h2 = (double)h * (double)h;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -281,7 +315,8 @@ int pio_brute(const float* x, const float* y, const float* z, int64_t n, float r
             double ddx = (double)x[j] - (double)x[i];
             double ddy = (double)y[j] - (double)y[i];
             double ddz = (double)z[j] - (double)z[i];
-            double K = exp(-(ddx * ddx + ddy * ddy + ddz * ddz) / h2);
+            double mag;
+            double K = kernel_value(kernel, ddx * ddx + ddy * ddy + ddz * ddz, (double)h, &mag);
             cnt += 1;
             s += K;
             vx += ddx * K;

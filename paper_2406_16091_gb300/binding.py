@@ -30,6 +30,11 @@ PI_OPT_ALGO = 1
 PI_OPT_PRECISION = 2
 PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
+PI_OPT_KERNEL = 5
+PI_KERNEL_GAUSSIAN = 0
+PI_KERNEL_LJ = 1
+PI_KERNEL_LOWFLOP = 2
+PI_KERNEL_HIGHFLOP = 3
 PI_ALGO_TILED = 0
 PI_ALGO_PPNL = 1
 PI_PREC_FP32 = 0
@@ -66,6 +71,11 @@ def load():
     i32, i64, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_float
     sig = {
         "pi_create": ([ctypes.POINTER(PiBox), f32, i64, ctypes.POINTER(P)], i32),
+        "pi_batch_create": ([i32, ctypes.POINTER(PiBox), P, P, ctypes.POINTER(P)], i32),
+        "pi_batch_bin": ([P, P, P, P, P, P], i32),
+        "pi_batch_interact": ([P, P, P, P, P, P, P, i32, P], i32),
+        "pi_batch_info": ([P, P, P, P], i32),
+        "pi_batch_grid": ([P, i32, P], i32),
         "pi_destroy": ([P], i32),
         "pi_bin": ([P, P, P, P, i64, P], i32),
         "pi_interact": ([P, f32, P, P, P, P, P, i32, P], i32),
@@ -128,6 +138,48 @@ def pi_create(lo, hi, r_c: float, n_max: int):
     out = ctypes.c_void_p()
     _check(load().pi_create(ctypes.byref(box), float(r_c), int(n_max), ctypes.byref(out)), "pi_create")
     return out.value
+
+
+def pi_batch_create(boxes, r_c, n_max):
+    """boxes: list of (lo, hi); r_c, n_max: one entry per system."""
+    S = len(boxes)
+    arr = (PiBox * S)(*[PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi)) for lo, hi in boxes])
+    rc = (ctypes.c_float * S)(*[float(v) for v in r_c])
+    nm = (ctypes.c_int64 * S)(*[int(v) for v in n_max])
+    out = ctypes.c_void_p()
+    _check(load().pi_batch_create(S, arr, ctypes.cast(rc, ctypes.c_void_p),
+                                  ctypes.cast(nm, ctypes.c_void_p), ctypes.byref(out)),
+           "pi_batch_create")
+    return out.value
+
+
+def pi_batch_bin(ctx, x, y, z, n, stream=None) -> None:
+    """n: per-system particle counts (host)."""
+    arr = (ctypes.c_int64 * len(n))(*[int(v) for v in n])
+    _check(load().pi_batch_bin(ctx, _ptr(x), _ptr(y), _ptr(z), ctypes.cast(arr, ctypes.c_void_p),
+                               _stream(stream)), "pi_batch_bin")
+
+
+def pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTED,
+                      stream=None) -> None:
+    """h: per-system kernel lengths (host)."""
+    arr = (ctypes.c_float * len(h))(*[float(v) for v in h])
+    _check(load().pi_batch_interact(ctx, ctypes.cast(arr, ctypes.c_void_p), _ptr(S), _ptr(Vx),
+                                    _ptr(Vy), _ptr(Vz), _ptr(nbr), int(out_order), _stream(stream)),
+           "pi_batch_interact")
+
+
+def pi_batch_info(ctx):
+    """(num_systems, total_cells, total_n_max)."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().pi_batch_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "pi_batch_info")
+    return a.value, b.value, c.value
+
+
+def pi_batch_grid(ctx, system: int):
+    dims = (ctypes.c_int32 * 3)()
+    _check(load().pi_batch_grid(ctx, int(system), ctypes.cast(dims, ctypes.c_void_p)), "pi_batch_grid")
+    return tuple(dims)
 
 
 def pi_destroy(ctx) -> None:

@@ -3,35 +3,50 @@
 // Argument checks, the device arena of a context, the launch sequence of a
 // step and the mapping of device error bits to pi_status.  No compute
 // happens here: every step of the path is one of the kernels in pi_bin.cu
-// and pi_interact.cu.
+// and pi_interact.cu.  A context holds one or more independent systems; the
+// single-system calls are the one-system case of the batch calls.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "pi.h"
 #include "pi_internal.cuh"
 
 using pi::Ctrl;
 using pi::Grid;
+using pi::SysDesc;
 
 struct pi_ctx {
-    pi_box box;
-    float rc;
-    int64_t n_max;
-    Grid g;
-    int64_t C;
+    int S;
+    std::vector<pi_box> boxes;
+    std::vector<float> rc;
+    std::vector<int64_t> n_max;  // per system
+    std::vector<SysDesc> sys;     // host copy of the per-system constants
+    std::vector<uint32_t> cbase;  // [S+1]
+    std::vector<uint32_t> rbase;  // [S+1]
+    int64_t C;                    // cells of all systems
+    int64_t n_max_total;
+    uint32_t rows;                // X-rows of all systems
     int device;
     int num_sms;
+    int tiled_per_sm[2];          // resident CTAs of the tiled kernel (plain, Kahan)
 
     // device arena and its parts
     void* arena;
     Ctrl* ctrl;
     uint32_t* counts;
     uint32_t* xbins;
+    uint32_t* pbase;
     uint32_t* offsets;
     unsigned long long* scan_status;
+    SysDesc* d_sys;
+    uint32_t* d_cbase;
+    uint32_t* d_rbase;
+    float* d_kscale;
     uint32_t* cell;
     uint32_t* rank;
     uint32_t* perm_u;
@@ -53,16 +68,18 @@ struct pi_ctx {
     float* io_Vz;
     uint32_t* io_nbr;
 
-    int64_t n;         // particles of the last pi_bin
-    int binned;        // a pi_bin has been enqueued since the last failure
-    uint32_t epoch;    // scan launch epoch
-    uint64_t launches; // kernels launched
-    uint32_t tiled_seq; // launches of the tiled interaction kernel
+    int64_t n;                      // particles of the last pi_bin (all systems)
+    std::vector<uint32_t> pbase_h;  // [S+1] particle bases of the last pi_bin
+    std::vector<float> kscale_h;    // per-system kernel scale last written to d_kscale
+    int binned;                     // a pi_bin has been enqueued since the last failure
+    uint32_t epoch;                 // scan launch epoch
+    uint64_t launches;              // kernels launched
+    uint32_t tiled_seq;             // launches of the tiled interaction kernel
     int algo;
     int precision;
+    int kernel;
     uint64_t wait_limit_ns;
     int withhold_scan;
-    float slack;
 };
 
 namespace {
@@ -117,6 +134,48 @@ struct Carver {
     }
 };
 
+// Grid and margins of one system (Sec. 3: cell width >= r_c).
+pi_status make_system(const pi_box& box, float r_c, SysDesc& d, int64_t& cells)
+{
+    if (!(r_c > 0.0f) || std::isinf(r_c)) return PI_ERR_INVALID_ARG;
+    std::memset(&d, 0, sizeof d);
+    cells = 1;
+    float max_abs = 0.f, min_w = FLT_MAX;
+    for (int k = 0; k < 3; ++k) {
+        const double lo = box.lo[k], hi = box.hi[k];
+        if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return PI_ERR_INVALID_ARG;
+        double n = std::floor((hi - lo) / (double)r_c);
+        if (n < 1.0) n = 1.0;
+        if (n > 2147483647.0) return PI_ERR_INVALID_ARG;
+        d.g.lo[k] = box.lo[k];
+        d.g.hi[k] = box.hi[k];
+        d.g.n[k] = (int32_t)n;
+        d.g.inv_w[k] = (float)(n / (hi - lo));
+        d.cell_w[k] = (float)((hi - lo) / n);
+        cells *= (int64_t)n;
+        if (cells >= ((int64_t)1 << 31) - 1) return PI_ERR_INVALID_ARG;
+        max_abs = std::fmax(max_abs, std::fmax(std::fabs(box.lo[k]), std::fabs(box.hi[k])));
+        min_w = std::fmin(min_w, (float)((hi - lo) / n));
+    }
+    d.rc2 = r_c * r_c;  // FP32 product, round to nearest
+    // margin of the conservative x-windows: cell assignment and face
+    // positions are exact only up to a few ulp of the coordinates
+    d.slack = 1e-5f * min_w + 16.0f * FLT_EPSILON * max_abs;
+    return PI_OK;
+}
+
+// Scale t of the interaction kernel for length h.
+float kernel_scale(int kernel, float h)
+{
+    const double hd = (double)h;
+    switch (kernel) {
+        case PI_KERNEL_LJ:
+        case PI_KERNEL_HIGHFLOP: return h * h;  // sigma^2 in FP32
+        case PI_KERNEL_LOWFLOP: return 0.f;
+        default: return (float)(-1.4426950408889634 / (hd * hd));  // -log2(e) / h^2
+    }
+}
+
 }  // namespace
 
 namespace pi {
@@ -146,75 +205,93 @@ const char* pi_status_str(pi_status s)
 
 const char* pi_last_error(void) { return g_last_error; }
 
-pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
+pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float* r_c,
+                          const int64_t* n_max, pi_ctx** out)
 {
-    if (!box || !out) return PI_ERR_INVALID_ARG;
+    if (!out) return PI_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!(r_c > 0.0f) || std::isinf(r_c)) return PI_ERR_INVALID_ARG;
-    if (n_max < 0 || n_max >= (int64_t)2147483647 - 64) return PI_ERR_INVALID_ARG;
-    Grid g{};
-    int64_t C = 1;
-    float max_abs = 0.f, min_w = FLT_MAX;
-    for (int d = 0; d < 3; ++d) {
-        const double lo = box->lo[d], hi = box->hi[d];
-        if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return PI_ERR_INVALID_ARG;
-        double n = std::floor((hi - lo) / (double)r_c);
-        if (n < 1.0) n = 1.0;
-        if (n > 2147483647.0) return PI_ERR_INVALID_ARG;
-        g.lo[d] = box->lo[d];
-        g.hi[d] = box->hi[d];
-        g.n[d] = (int32_t)n;
-        g.inv_w[d] = (float)(n / (hi - lo));
-        C *= (int64_t)n;
-        if (C >= ((int64_t)1 << 31) - 1) return PI_ERR_INVALID_ARG;
-        max_abs = std::fmax(max_abs, std::fmax(std::fabs(box->lo[d]), std::fabs(box->hi[d])));
-        min_w = std::fmin(min_w, (float)((hi - lo) / n));
-    }
-
+    if (num_systems < 1 || num_systems > pi::MAX_SYSTEMS || !boxes || !r_c || !n_max)
+        return PI_ERR_INVALID_ARG;
+    const int S = num_systems;
     pi_ctx* c = new (std::nothrow) pi_ctx();
     if (!c) return PI_ERR_NOMEM;
-    c->box = *box;
-    c->rc = r_c;
-    c->n_max = n_max;
-    c->g = g;
+    c->S = S;
+    c->boxes.assign(boxes, boxes + S);
+    c->rc.assign(r_c, r_c + S);
+    c->n_max.assign(n_max, n_max + S);
+    c->sys.resize(S);
+    c->cbase.assign(S + 1, 0);
+    c->rbase.assign(S + 1, 0);
+    c->pbase_h.assign(S + 1, 0);
+    c->kscale_h.assign(S, std::nanf(""));
+    int64_t C = 0, N = 0, R = 0;
+    for (int s = 0; s < S; ++s) {
+        int64_t cells = 0;
+        pi_status st = make_system(boxes[s], r_c[s], c->sys[s], cells);
+        if (st == PI_OK && n_max[s] < 0) st = PI_ERR_INVALID_ARG;
+        if (st != PI_OK) {
+            delete c;
+            return st;
+        }
+        c->sys[s].cell_base = (uint32_t)C;
+        c->sys[s].row_base = (uint32_t)R;
+        c->cbase[s] = (uint32_t)C;
+        c->rbase[s] = (uint32_t)R;
+        C += cells;
+        R += (int64_t)c->sys[s].g.n[1] * c->sys[s].g.n[2];
+        N += n_max[s];
+        if (C >= ((int64_t)1 << 31) - 1 || N >= (int64_t)2147483647 - 64) {
+            delete c;
+            return PI_ERR_INVALID_ARG;
+        }
+    }
+    c->cbase[S] = (uint32_t)C;
+    c->rbase[S] = (uint32_t)R;
     c->C = C;
+    c->n_max_total = N;
+    c->rows = (uint32_t)R;
     c->algo = PI_ALGO_TILED;
     c->precision = PI_PREC_FP32;
+    c->kernel = PI_KERNEL_GAUSSIAN;
     c->wait_limit_ns = 1000000000ull;
-    c->slack = 1e-5f * min_w + 16.0f * FLT_EPSILON * max_abs;
-    c->epoch = 0;
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = pi::tiled_occupancy(false, &c->tiled_per_sm[0]);
+    if (e == cudaSuccess) e = pi::tiled_occupancy(true, &c->tiled_per_sm[1]);
     if (e != cudaSuccess) {
-        pi_status st = cuda_fail(e, "pi_create: device query");
+        pi_status st = cuda_fail(e, "pi_batch_create: device query");
         delete c;
         return st;
     }
 
-    const size_t nm = (size_t)n_max;
+    const size_t nm = (size_t)N;
     const size_t tiles = ((size_t)C + 1 + pi::SCAN_TILE - 1) / pi::SCAN_TILE;
     Carver k;
     const size_t o_ctrl = k.take<Ctrl>(1);
     const size_t o_counts = k.take<uint32_t>((size_t)C + 4);
-    const size_t o_xbins = k.take<uint32_t>((size_t)C + 4);
-    const size_t zero_end = k.off;  // ctrl, counts and xbins are cleared by every pi_bin
+    const size_t o_xbins = k.take<uint32_t>((size_t)C + 4);  // ctrl .. xbins: cleared by every pi_bin
+    const size_t o_pbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_offsets = k.take<uint32_t>((size_t)C + 1 + 16);
     const size_t o_status = k.take<unsigned long long>(tiles);
+    const size_t o_sys = k.take<SysDesc>((size_t)S);
+    const size_t o_cbase = k.take<uint32_t>((size_t)S + 1);
+    const size_t o_rbase = k.take<uint32_t>((size_t)S + 1);
+    const size_t o_kscale = k.take<float>((size_t)S);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
     const size_t o_permu = k.take<uint32_t>(nm + 4);
     const size_t o_posu = k.take<float4>(nm + 4);
     const size_t o_perm = k.take<uint32_t>(nm + 4);
-    const size_t o_sx = k.take<float>(nm + pi::SORTED_PAD);
-    const size_t o_sy = k.take<float>(nm + pi::SORTED_PAD);
-    const size_t o_sz = k.take<float>(nm + pi::SORTED_PAD);
+    const size_t o_sx = k.take<float>(nm + 4);
+    const size_t o_sy = k.take<float>(nm + 4);
+    const size_t o_sz = k.take<float>(nm + 4);
     const size_t o_P = k.take<float4>(nm + 4);
     const size_t total = align_up(k.off, 256);
 
     e = cudaMalloc(&c->arena, total);
     if (e != cudaSuccess) {
-        pi_status st = cuda_fail(e, "pi_create: cudaMalloc");
+        pi_status st = cuda_fail(e, "pi_batch_create: cudaMalloc");
         delete c;
         return st;
     }
@@ -222,8 +299,13 @@ pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
     c->ctrl = (Ctrl*)(base + o_ctrl);
     c->counts = (uint32_t*)(base + o_counts);
     c->xbins = (uint32_t*)(base + o_xbins);
+    c->pbase = (uint32_t*)(base + o_pbase);
     c->offsets = (uint32_t*)(base + o_offsets);
     c->scan_status = (unsigned long long*)(base + o_status);
+    c->d_sys = (SysDesc*)(base + o_sys);
+    c->d_cbase = (uint32_t*)(base + o_cbase);
+    c->d_rbase = (uint32_t*)(base + o_rbase);
+    c->d_kscale = (float*)(base + o_kscale);
     c->cell = (uint32_t*)(base + o_cell);
     c->rank = (uint32_t*)(base + o_rank);
     c->perm_u = (uint32_t*)(base + o_permu);
@@ -233,18 +315,30 @@ pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
     c->sy = (float*)(base + o_sy);
     c->sz = (float*)(base + o_sz);
     c->P = (float4*)(base + o_P);
-    (void)zero_end;
-    // everything starts at zero: an empty grid, no error, stale-free scan descriptors
+    // everything starts at zero: an empty grid, no error, stale-free scan
+    // descriptors; then the per-system constants
     e = cudaMemset(c->arena, 0, total);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_sys, c->sys.data(), sizeof(SysDesc) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_cbase, c->cbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_rbase, c->rbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        pi_status st = cuda_fail(e, "pi_create: clear");
+        pi_status st = cuda_fail(e, "pi_batch_create: initialise");
         cudaFree(c->arena);
         delete c;
         return st;
     }
     *out = c;
     return PI_OK;
+}
+
+pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out)
+{
+    if (!box || !out) return PI_ERR_INVALID_ARG;
+    return pi_batch_create(1, box, &r_c, &n_max, out);
 }
 
 pi_status pi_destroy(pi_ctx* ctx)
@@ -260,12 +354,24 @@ pi_status pi_destroy(pi_ctx* ctx)
     return PI_OK;
 }
 
-pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3])
+pi_status pi_batch_info(const pi_ctx* ctx, int32_t* num_systems, int64_t* total_cells,
+                        int64_t* total_n_max)
 {
-    if (!ctx || !dims) return PI_ERR_INVALID_ARG;
-    for (int d = 0; d < 3; ++d) dims[d] = ctx->g.n[d];
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (num_systems) *num_systems = ctx->S;
+    if (total_cells) *total_cells = ctx->C;
+    if (total_n_max) *total_n_max = ctx->n_max_total;
     return PI_OK;
 }
+
+pi_status pi_batch_grid(const pi_ctx* ctx, int32_t system, int32_t dims[3])
+{
+    if (!ctx || !dims || system < 0 || system >= ctx->S) return PI_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d) dims[d] = ctx->sys[system].g.n[d];
+    return PI_OK;
+}
+
+pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3]) { return pi_batch_grid(ctx, 0, dims); }
 
 pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t** offsets,
                     const uint32_t** perm, const float** sx, const float** sy, const float** sz)
@@ -321,6 +427,11 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
             if (value != 0 && value != 1) return PI_ERR_INVALID_ARG;
             ctx->withhold_scan = (int)value;
             return PI_OK;
+        case PI_OPT_KERNEL:
+            if (value < PI_KERNEL_GAUSSIAN || value > PI_KERNEL_HIGHFLOP) return PI_ERR_INVALID_ARG;
+            ctx->kernel = (int)value;
+            std::fill(ctx->kscale_h.begin(), ctx->kscale_h.end(), std::nanf(""));
+            return PI_OK;
     }
     return PI_ERR_INVALID_ARG;
 }
@@ -332,28 +443,37 @@ pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count)
     return PI_OK;
 }
 
-pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
-                 pi_stream stream)
+pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float* z,
+                       const int64_t* n, pi_stream stream)
 {
-    if (!ctx) return PI_ERR_INVALID_ARG;
-    if (n < 0) return PI_ERR_INVALID_ARG;
-    if (n > ctx->n_max) return PI_ERR_CAPACITY;
-    if (n > 0 && (!x || !y || !z)) return PI_ERR_INVALID_ARG;
+    if (!ctx || !n) return PI_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int s = 0; s < ctx->S; ++s) {
+        if (n[s] < 0) return PI_ERR_INVALID_ARG;
+        if (n[s] > ctx->n_max[s]) return PI_ERR_CAPACITY;
+        total += n[s];
+    }
+    if (total > 0 && (!x || !y || !z)) return PI_ERR_INVALID_ARG;
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_bin: set device");
     cudaStream_t s = (cudaStream_t)stream;
     ctx->binned = 0;
     ctx->tiled_seq = 0;  // k_zero clears both row-counter slots
     ctx->epoch = (ctx->epoch % 0x3ffffffeu) + 1u;  // 30-bit, never 0
-    const uint32_t nn = (uint32_t)n;
+    ctx->pbase_h[0] = 0;
+    for (int k = 0; k < ctx->S; ++k) ctx->pbase_h[k + 1] = ctx->pbase_h[k] + (uint32_t)n[k];
+    const uint32_t nn = (uint32_t)total;
     const uint32_t C = (uint32_t)ctx->C;
+    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_rbase, ctx->S};
 
-    // control block, counts and xbins are one contiguous zeroed prefix of the arena
+    // control block, counts and xbins are one contiguous zeroed prefix of the
+    // arena; the same launch writes this step's particle bases
     const size_t zero_words = ((char*)(ctx->xbins + C) - (char*)ctx->ctrl + 3) / 4;
-    PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, zero_words, s));
+    PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, zero_words, ctx->pbase, ctx->pbase_h.data(),
+                           ctx->S + 1, s));
     ctx->launches += 1;
     if (nn > 0) {
-        PI_TRY(pi::launch_hist(x, y, z, nn, ctx->g, ctx->counts, ctx->cell, ctx->rank, ctx->ctrl,
+        PI_TRY(pi::launch_hist(x, y, z, nn, sy, ctx->counts, ctx->cell, ctx->rank, ctx->ctrl,
                                ctx->num_sms, s));
         ctx->launches += 1;
     }
@@ -363,41 +483,70 @@ pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, in
     if (nn > 0) {
         PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, ctx->offsets, ctx->perm_u,
                                   ctx->pos_u, ctx->ctrl, ctx->num_sms, s));
-        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->pos_u, nn, ctx->g, ctx->offsets, ctx->perm,
-                                    ctx->sx, ctx->sy, ctx->sz, ctx->P, ctx->xbins, ctx->ctrl,
-                                    ctx->num_sms, s));
+        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->pos_u, nn, sy, ctx->offsets, ctx->perm, ctx->sx,
+                                    ctx->sy, ctx->sz, ctx->P, ctx->xbins, ctx->ctrl, ctx->num_sms,
+                                    s));
         ctx->launches += 2;
     }
-    ctx->n = n;
+    ctx->n = total;
     ctx->binned = 1;
     return PI_OK;
 }
 
-pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
-                      uint32_t* nbr, int out_order, pi_stream stream)
+pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
+                 pi_stream stream)
 {
     if (!ctx) return PI_ERR_INVALID_ARG;
-    if (!(h > 0.0f) || std::isinf(h)) return PI_ERR_INVALID_ARG;
+    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
+    return pi_batch_bin(ctx, x, y, z, &n, stream);
+}
+
+pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
+                            uint32_t* nbr, int out_order, pi_stream stream)
+{
+    if (!ctx || !h) return PI_ERR_INVALID_ARG;
+    for (int s = 0; s < ctx->S; ++s)
+        if (!(h[s] > 0.0f) || std::isinf(h[s])) return PI_ERR_INVALID_ARG;
     if (out_order != PI_ORDER_SORTED && out_order != PI_ORDER_ORIGINAL) return PI_ERR_INVALID_ARG;
     if (!ctx->binned) return PI_ERR_NOT_BINNED;
     if (ctx->n > 0 && (!S || !Vx || !Vy || !Vz)) return PI_ERR_INVALID_ARG;
     if (ctx->n == 0) return PI_OK;
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_interact: set device");
+    cudaStream_t st = (cudaStream_t)stream;
 
     pi::InteractArgs a{};
+    a.sy = pi::Systems{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_rbase, ctx->S};
     a.P = ctx->P;
     a.xbins = ctx->xbins;
     a.sx = ctx->sx;
-    a.sy = ctx->sy;
+    a.sy_pos = ctx->sy;
     a.sz = ctx->sz;
     a.offsets = ctx->offsets;
     a.perm = ctx->perm;
     a.n = (uint32_t)ctx->n;
-    a.g = ctx->g;
-    a.rc2 = ctx->rc * ctx->rc;  // FP32 product, round to nearest
-    const double hd = (double)h;
-    a.kscale = (float)(-1.4426950408889634 / (hd * hd));  // -log2(e) / h^2
+    a.rows = ctx->rows;
+    a.kernel = ctx->kernel;
+    a.one = 1.0f;
+    a.zero = 0.0f;
+    if (ctx->S == 1) {
+        a.kscale = nullptr;
+        a.kscale0 = kernel_scale(ctx->kernel, h[0]);
+    } else {
+        // write the per-system scales only when they changed
+        bool same = true;
+        std::vector<float> t(ctx->S);
+        for (int s = 0; s < ctx->S; ++s) {
+            t[s] = kernel_scale(ctx->kernel, h[s]);
+            same = same && t[s] == ctx->kscale_h[s];
+        }
+        if (!same) {
+            PI_TRY(pi::launch_set_kscale(ctx->d_kscale, t.data(), ctx->S, st));
+            ctx->launches += 1;
+            ctx->kscale_h = t;
+        }
+        a.kscale = ctx->d_kscale;
+    }
     a.S = S;
     a.Vx = Vx;
     a.Vy = Vy;
@@ -405,23 +554,29 @@ pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, floa
     a.nbr = nbr;
     a.original_order = out_order == PI_ORDER_ORIGINAL;
     a.ctrl = ctx->ctrl;
-    a.slack = ctx->slack;
     a.wait_limit_ns = ctx->wait_limit_ns;
     a.seq = ctx->tiled_seq;
-    for (int d = 0; d < 3; ++d)
-        a.cell_w[d] = (float)(((double)ctx->box.hi[d] - (double)ctx->box.lo[d]) / (double)ctx->g.n[d]);
     int launched = 0;
     cudaError_t e;
     const bool kahan = ctx->precision == PI_PREC_KAHAN;
-    if (ctx->algo == PI_ALGO_PPNL)
-        e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, (cudaStream_t)stream, &launched);
-    else {
-        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, (cudaStream_t)stream, &launched);
+    if (ctx->algo == PI_ALGO_PPNL) {
+        e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, st, &launched);
+    } else {
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], st,
+                                      &launched);
         ctx->tiled_seq += 1;
     }
     ctx->launches += (uint64_t)launched;
     if (e != cudaSuccess) return cuda_fail(e, "pi_interact: launch");
     return PI_OK;
+}
+
+pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
+                      uint32_t* nbr, int out_order, pi_stream stream)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
+    return pi_batch_interact(ctx, &h, S, Vx, Vy, Vz, nbr, out_order, stream);
 }
 
 pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)
@@ -444,13 +599,14 @@ pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float
                       int out_order, pi_stream stream)
 {
     if (!ctx) return PI_ERR_INVALID_ARG;
+    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
     if (n < 0) return PI_ERR_INVALID_ARG;
-    if (n > ctx->n_max) return PI_ERR_CAPACITY;
+    if (n > ctx->n_max[0]) return PI_ERR_CAPACITY;
     if (n > 0 && (!hx || !hy || !hz || !hS || !hVx || !hVy || !hVz)) return PI_ERR_INVALID_ARG;
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_run_host: set device");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t nm = (size_t)ctx->n_max + 4;
+    const size_t nm = (size_t)ctx->n_max_total + 4;
     if (!ctx->io) {
         PI_TRY(cudaMalloc(&ctx->io, nm * 8 * sizeof(float)));
         float* f = (float*)ctx->io;

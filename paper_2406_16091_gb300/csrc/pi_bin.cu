@@ -31,22 +31,26 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-__global__ void k_zero(uint32_t* __restrict__ p, size_t n_words)
+template <int NB>
+__global__ void k_zero(ZeroArgs<NB> z)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
-    uint4* p4 = reinterpret_cast<uint4*>(p);
-    size_t n4 = n_words / 4;
+    uint4* p4 = reinterpret_cast<uint4*>(z.p);
+    size_t n4 = z.n_words / 4;
     for (size_t k = i; k < n4; k += stride) p4[k] = make_uint4(0, 0, 0, 0);
-    for (size_t k = n4 * 4 + i; k < n_words; k += stride) p[k] = 0;
+    for (size_t k = n4 * 4 + i; k < z.n_words; k += stride) z.p[k] = 0;
+    for (size_t k = i; k < (size_t)z.nb; k += stride) z.pbase[k] = z.vals[k];
 }
 
 // a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
 // float4 per component when the arrays are 16-byte aligned.  The loop bound
-// is warp-uniform so that every lane takes part in the match/shuffle.
+// is warp-uniform so that every lane takes part in the match/shuffle.  The
+// system of each particle comes from the particle bases; its cell is offset
+// by the system's first cell.
 __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               const float* __restrict__ y,
-                                              const float* __restrict__ z, uint32_t n, Grid g,
+                                              const float* __restrict__ z, uint32_t n, Systems sy,
                                               uint32_t* __restrict__ counts,
                                               uint32_t* __restrict__ cell_out,
                                               uint32_t* __restrict__ rank_out,
@@ -81,14 +85,18 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                 pz[j] = valid[j] ? z[i] : 0.f;
             }
         }
+        int s = (sy.S == 1 || grp >= groups) ? 0 : find_system(sy.pbase, sy.S, i0);
         // all four matches, then all four atomics, then the shuffles: the
         // atomics of one lane are in flight together instead of one by one
         uint32_t cell[4], rank[4], key[4];
         unsigned peers[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+            if (sy.S > 1 && valid[j])
+                while (s + 1 < sy.S && i0 + j >= __ldg(sy.pbase + s + 1)) ++s;
+            const SysDesc& d = sy.sys[s];
             bool ok = true;
-            cell[j] = cell_of(px[j], py[j], pz[j], g, ok);
+            cell[j] = cell_of(px[j], py[j], pz[j], d.g, ok) + d.cell_base;
             all_ok &= ok | !valid[j];
             key[j] = valid[j] ? cell[j] : 0xffffffffu;
             peers[j] = __match_any_sync(FULL, key[j]);
@@ -311,24 +319,27 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //     than 255 members, bytes 0..2 then 0 (every sub-bin starts at the cell).
 __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ perm_u,
                                                    const float4* __restrict__ pos_u, uint32_t n,
-                                                   Grid g, const uint32_t* __restrict__ offsets,
+                                                   Systems sy, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
-                                                   float* __restrict__ sx, float* __restrict__ sy,
+                                                   float* __restrict__ sx, float* __restrict__ sy_out,
                                                    float* __restrict__ sz, float4* __restrict__ P,
                                                    uint32_t* __restrict__ xbins,
                                                    Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
     bool bad = false;
-    const float inv4 = g.inv_w[0] * 4.0f;
+    const uint32_t C = __ldg(sy.cbase + sy.S);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t i = perm_u[k];
         const float4 pk = pos_u[k];
         const uint32_t c = __float_as_uint(pk.w);
-        if (i >= n || c >= (uint32_t)g.n[0] * (uint32_t)g.n[1] * (uint32_t)g.n[2]) { bad = true; continue; }
+        if (i >= n || c >= C) { bad = true; continue; }
         const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
         if (k < s0 || k >= s1) { bad = true; continue; }
-        const int cx4 = 4 * (int)(c % (uint32_t)g.n[0]);
+        const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
+        const Grid& g = sy.sys[sid].g;
+        const float inv4 = g.inv_w[0] * 4.0f;
+        const int cx4 = 4 * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
         uint32_t r = 0, xr = 0, b1 = 0, b2 = 0, b3 = 0;
         for (uint32_t q = s0; q < s1; ++q) {
             const uint32_t j = perm_u[q];
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ 
         const uint32_t dst = s0 + r;
         perm[dst] = i;
         sx[dst] = pk.x;
-        sy[dst] = pk.y;
+        sy_out[dst] = pk.y;
         sz[dst] = pk.z;
         P[s0 + xr] = make_float4(pk.x, pk.y, pk.z, __uint_as_float(dst));
         if (xr == 0) xbins[c] = (s1 - s0 > 255u) ? (1u << 24) : (b1 | (b2 << 8) | (b3 << 16));
@@ -363,21 +374,36 @@ inline int grid_for(uint64_t work, int threads, int num_sms, int per_sm)
 
 }  // namespace
 
-cudaError_t launch_zero(uint32_t* p, size_t n_words, cudaStream_t s)
+template <int NB>
+cudaError_t launch_zero_nb(uint32_t* p, size_t n_words, uint32_t* pbase, const uint32_t* vals, int nb,
+                           cudaStream_t s)
 {
+    ZeroArgs<NB> z;
+    z.p = p;
+    z.n_words = n_words;
+    z.pbase = pbase;
+    z.nb = nb;
+    for (int k = 0; k < nb; ++k) z.vals[k] = vals[k];
     int blocks = (int)((n_words / 4 + 255) / 256);
     blocks = blocks < 1 ? 1 : (blocks > 1184 ? 1184 : blocks);
-    k_zero<<<blocks, 256, 0, s>>>(p, n_words);
+    k_zero<NB><<<blocks, 256, 0, s>>>(z);
     return cudaGetLastError();
 }
 
-cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n, const Grid& g,
-                        uint32_t* counts, uint32_t* cell, uint32_t* rank, Ctrl* ctrl, int num_sms,
+cudaError_t launch_zero(uint32_t* p, size_t n_words, uint32_t* pbase, const uint32_t* vals, int nb,
                         cudaStream_t s)
+{
+    if (nb <= 8) return launch_zero_nb<8>(p, n_words, pbase, vals, nb, s);
+    return launch_zero_nb<MAX_SYSTEMS + 1>(p, n_words, pbase, vals, nb, s);
+}
+
+cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n,
+                        const Systems& sy, uint32_t* counts, uint32_t* cell, uint32_t* rank,
+                        Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + 3) / 4;
-    k_hist<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(x, y, z, n, g, counts, cell, rank,
+    k_hist<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(x, y, z, n, sy, counts, cell, rank,
                                                              ctrl, vec);
     return cudaGetLastError();
 }
@@ -401,13 +427,37 @@ cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n, const Grid& g,
-                             const uint32_t* offsets, uint32_t* perm, float* sx, float* sy,
-                             float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl, int num_sms,
-                             cudaStream_t s)
+cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
+                             const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
+                             float* sy_out, float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl,
+                             int num_sms, cudaStream_t s)
 {
-    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, pos_u, n, g, offsets, perm, sx,
-                                                             sy, sz, P, xbins, ctrl);
+    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, pos_u, n, sy, offsets, perm, sx,
+                                                             sy_out, sz, P, xbins, ctrl);
+    return cudaGetLastError();
+}
+
+namespace {
+struct KscaleArgs {
+    float* dst;
+    int S;
+    float vals[MAX_SYSTEMS];
+};
+
+__global__ void k_set_kscale(KscaleArgs k)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.S; i += gridDim.x * blockDim.x)
+        k.dst[i] = k.vals[i];
+}
+}  // namespace
+
+cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s)
+{
+    KscaleArgs k;
+    k.dst = kscale;
+    k.S = S;
+    for (int i = 0; i < S; ++i) k.vals[i] = vals[i];
+    k_set_kscale<<<(S + 255) / 256, 256, 0, s>>>(k);
     return cudaGetLastError();
 }
 

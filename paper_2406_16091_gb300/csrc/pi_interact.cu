@@ -1,10 +1,20 @@
 // pi_interact.cu -- interaction kernels (arXiv 2406.16091, Sec. 2-5).
 //
 // For every particle i: n_i = #{j != i : r2_ij < rc2}, S_i = sum K_ij and
-// V_i = sum (p_j - p_i) K_ij with K = exp(-r^2/h^2) = 2^(r2 * kscale),
-// kscale = -log2(e)/h^2.  The pair test is the frozen FP32 form
+// V_i = sum (p_j - p_i) K_ij.  The pair test is the frozen FP32 form
 // r2 = fma(dz, dz, fma(dy, dy, dx*dx)) < fl32(r_c^2) with d = p_j - p_i in
-// FP32, so neighbour counts are exact.  K uses the ex2.approx instruction.
+// FP32, so neighbour counts are exact.  K is one of
+//   Gaussian       exp(-r^2/h^2) = 2^(r2 t), t = -log2(e)/h^2 (ex2.approx)
+//   Lennard-Jones  4 (s^6 - s^3), s = sigma^2 / (r^2 + sigma^2/100),
+//                  sigma = h (the Sec. 7.1 potential with E0 = 1 and a
+//                  softening of sigma/10)
+//   low-FLOP       1 (Sec. 7.2's cheap synthetic kernel: S counts, V sums
+//                  the offsets)
+//   high-FLOP      Lennard-Jones followed by 75 fused multiply-adds by an
+//                  opaque 1 and 0 (Sec. 7.2's expensive synthetic kernel:
+//                  the value is unchanged, the work is 150 FLOP more)
+// Every kernel works on several independent systems at once: particle,
+// cell and X-row indices are global over the concatenated systems.
 //
 // Kernels:
 //   k_interact_ppnl   Alg. 1 (Par-Part-NoLoop): one thread per particle,
@@ -64,20 +74,50 @@ struct KahanAcc {
     __device__ __forceinline__ float value() const { return v; }
 };
 
-template <class Acc>
+// Value of the interaction kernel for one pair inside the cutoff; t is the
+// system's scale (Gaussian: -log2(e)/h^2; Lennard-Jones: sigma^2).
+template <int KERNEL>
+__device__ __forceinline__ float kernel_value(float r2, float t, float one, float zero)
+{
+    if constexpr (KERNEL == KERNEL_GAUSSIAN) {
+        return ex2_approx(__fmul_rn(r2, t));
+    } else if constexpr (KERNEL == KERNEL_LOWFLOP) {
+        return 1.0f;
+    } else {
+        const float rs2 = __fmaf_rn(0.01f, t, r2);
+        const float sr = __fmul_rn(t, __frcp_rn(rs2));
+        const float s3 = __fmul_rn(__fmul_rn(sr, sr), sr);
+        float K = __fmul_rn(4.0f, __fsub_rn(__fmul_rn(s3, s3), s3));
+        if constexpr (KERNEL == KERNEL_HIGHFLOP) {
+#pragma unroll
+            for (int i = 0; i < 75; ++i) K = __fmaf_rn(K, one, zero);
+        }
+        return K;
+    }
+}
+
+// Scale of the kernel and the opaque constants of the high-FLOP kernel.
+struct KParams {
+    float t, one, zero;
+};
+
+// Kernels whose value at r = 0 is far larger than their typical sum: the
+// tiled kernel excludes the self pair by identity for them instead of adding
+// K(0) and taking it off again.
+template <int KERNEL>
+__host__ __device__ constexpr bool self_by_identity()
+{
+    return KERNEL == KERNEL_LJ || KERNEL == KERNEL_HIGHFLOP;
+}
+
+// Per-target accumulators of one interaction kernel.
+template <class Acc, int KERNEL>
 struct Sums {
     Acc s, vx, vy, vz;
     uint32_t n = 0;
 
-    // One candidate without a branch: K is computed for every candidate and
-    // zeroed when the pair test fails (the tiled kernel's inner loop, where
-    // a divergent branch per candidate costs more than the exp2).
-    __device__ __forceinline__ void pair_nb(float dx, float dy, float dz, float rc2, float kscale)
+    __device__ __forceinline__ void add(float dx, float dy, float dz, float K, bool in)
     {
-        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        const bool in = r2 < rc2;
-        const float e = ex2_approx(__fmul_rn(r2, kscale));
-        const float K = in ? e : 0.f;
         s.add(K);
         vx.addmul(dx, K);
         vy.addmul(dy, K);
@@ -85,24 +125,29 @@ struct Sums {
         n += in ? 1u : 0u;
     }
 
-    // One candidate source at FP32 offset (dx, dy, dz) from the target.
-    __device__ __forceinline__ void pair(float dx, float dy, float dz, float rc2, float kscale)
+    // One candidate without a branch: K is computed for every candidate and
+    // zeroed when the pair test fails (the tiled kernel's inner loop, where
+    // a divergent branch per candidate costs more than the kernel value).
+    __device__ __forceinline__ void pair_nb(float dx, float dy, float dz, float rc2, const KParams& kp,
+                                            bool self = false)
     {
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 < rc2) {
-            const float K = ex2_approx(__fmul_rn(r2, kscale));
-            s.add(K);
-            vx.addmul(dx, K);
-            vy.addmul(dy, K);
-            vz.addmul(dz, K);
-            n += 1;
-        }
+        const bool in = (r2 < rc2) && !self;
+        const float e = kernel_value<KERNEL>(r2, kp.t, kp.one, kp.zero);
+        add(dx, dy, dz, in ? e : 0.f, in);
+    }
+
+    // One candidate source at FP32 offset (dx, dy, dz) from the target.
+    __device__ __forceinline__ void pair(float dx, float dy, float dz, float rc2, const KParams& kp)
+    {
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        if (r2 < rc2) add(dx, dy, dz, kernel_value<KERNEL>(r2, kp.t, kp.one, kp.zero), true);
     }
 };
 
-template <class Acc>
-__device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot, const Sums<Acc>& r,
-                                          float s_bias, uint32_t n_bias)
+template <class Acc, int KERNEL>
+__device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot,
+                                          const Sums<Acc, KERNEL>& r, float s_bias, uint32_t n_bias)
 {
     const uint32_t o = a.original_order ? a.perm[slot] : slot;
     a.S[o] = r.s.value() - s_bias;
@@ -114,27 +159,30 @@ __device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot, 
 
 // ---- Alg. 1: Par-Part-NoLoop ------------------------------------------------
 
-template <class Acc>
+template <class Acc, int KERNEL>
 __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 {
     if (load_error(a.ctrl)) return;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n) return;
-    const float xt = a.sx[k], yt = a.sy[k], zt = a.sz[k];
-    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-    const int cx = axis_cell(xt, a.g.lo[0], a.g.inv_w[0], nx);
-    const int cy = axis_cell(yt, a.g.lo[1], a.g.inv_w[1], ny);
-    const int cz = axis_cell(zt, a.g.lo[2], a.g.inv_w[2], nz);
-    Sums<Acc> r;
+    const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.pbase, a.sy.S, k);
+    const SysDesc& d = a.sy.sys[sid];
+    const Grid& g = d.g;
+    const float xt = a.sx[k], yt = a.sy_pos[k], zt = a.sz[k];
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int cx = axis_cell(xt, g.lo[0], g.inv_w[0], nx);
+    const int cy = axis_cell(yt, g.lo[1], g.inv_w[1], ny);
+    const int cz = axis_cell(zt, g.lo[2], g.inv_w[2], nz);
+    Sums<Acc, KERNEL> r;
+    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
     for (int bz = max(cz - 1, 0); bz <= min(cz + 1, nz - 1); ++bz)
         for (int by = max(cy - 1, 0); by <= min(cy + 1, ny - 1); ++by) {
-            const uint32_t row = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
+            const uint32_t row = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
             const uint32_t j0 = a.offsets[row + max(cx - 1, 0)];
             const uint32_t j1 = a.offsets[row + min(cx + 1, nx - 1) + 1];
             for (uint32_t j = j0; j < j1; ++j) {
                 if (j == k) continue;
-                r.pair(__fsub_rn(a.sx[j], xt), __fsub_rn(a.sy[j], yt), __fsub_rn(a.sz[j], zt), a.rc2,
-                       a.kscale);
+                r.pair(__fsub_rn(a.sx[j], xt), __fsub_rn(a.sy_pos[j], yt), __fsub_rn(a.sz[j], zt), d.rc2, kp);
             }
         }
     store_out(a, k, r, 0.f, 0u);
@@ -171,8 +219,11 @@ struct Smem {
         uint32_t cs[9][MAXLX + 4];
     } tbl;
     Plan plan;
+    SysDesc d;      // the system of the current X-row
+    float t;        // its kernel scale
     int coarse[9];  // row holds a cell without sub-bin starts: end lookups use cell bounds
-    uint32_t row;
+    uint32_t row;   // current X-row, local to its system
+    int has_row;
     int failed;
     uint64_t bar;
 };
@@ -231,10 +282,11 @@ __device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t phase, 
 // largest x1 such that the chunk has at most TT targets and its 9 source
 // rows hold at most CAP particles, plus each row's range.  A single cell
 // whose rows exceed CAP is read from global memory (mode 1).
-__device__ void plan_chunk(const InteractArgs& a, Plan& p, int x0, int cy, int cz, unsigned lane)
+__device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int x0, int cy, int cz,
+                           unsigned lane)
 {
-    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-    const uint32_t rb0 = (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
+    const int nx = d.g.n[0], ny = d.g.n[1], nz = d.g.n[2];
+    const uint32_t rb0 = d.cell_base + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
     const int xa = max(x0 - 1, 0);
     const int xmax = min(nx, x0 + MAXLX);
     uint32_t rb[9], rstart[9];
@@ -243,7 +295,7 @@ __device__ void plan_chunk(const InteractArgs& a, Plan& p, int x0, int cy, int c
     for (int r = 0; r < 9; ++r) {
         const int by = cy + r % 3 - 1, bz = cz + r / 3 - 1;
         rok[r] = by >= 0 && by < ny && bz >= 0 && bz < nz;
-        rb[r] = rok[r] ? (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) : 0u;
+        rb[r] = rok[r] ? d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) : 0u;
         rstart[r] = rok[r] ? a.offsets[rb[r] + xa] : 0u;
     }
     const uint32_t tgt0 = a.offsets[rb0 + x0];
@@ -332,47 +384,49 @@ struct Faces {
     float y_lo, y_hi, z_lo, z_hi;
 };
 
-__device__ __forceinline__ Faces faces_of(const InteractArgs& a, float yt, float zt, int cy, int cz)
+__device__ __forceinline__ Faces faces_of(const SysDesc& d, float yt, float zt, int cy, int cz)
 {
-    const float wy = a.cell_w[1], wz = a.cell_w[2];
+    const float wy = d.cell_w[1], wz = d.cell_w[2];
     Faces f;
-    f.y_lo = fmaxf(yt - fmaf((float)cy, wy, a.g.lo[1]) - a.slack, 0.f);
-    f.y_hi = fmaxf(fmaf((float)(cy + 1), wy, a.g.lo[1]) - yt - a.slack, 0.f);
-    f.z_lo = fmaxf(zt - fmaf((float)cz, wz, a.g.lo[2]) - a.slack, 0.f);
-    f.z_hi = fmaxf(fmaf((float)(cz + 1), wz, a.g.lo[2]) - zt - a.slack, 0.f);
+    f.y_lo = fmaxf(yt - fmaf((float)cy, wy, d.g.lo[1]) - d.slack, 0.f);
+    f.y_hi = fmaxf(fmaf((float)(cy + 1), wy, d.g.lo[1]) - yt - d.slack, 0.f);
+    f.z_lo = fmaxf(zt - fmaf((float)cz, wz, d.g.lo[2]) - d.slack, 0.f);
+    f.z_hi = fmaxf(fmaf((float)(cz + 1), wz, d.g.lo[2]) - zt - d.slack, 0.f);
     return f;
 }
 
 // Half-width of the x-window of row rr, or a negative value if the row is
 // out of reach.  Conservative: rc^2 is inflated by 2e-5 and the slack added.
-__device__ __forceinline__ float row_halfwidth(const InteractArgs& a, const Faces& f, int rr)
+__device__ __forceinline__ float row_halfwidth(const SysDesc& d, const Faces& f, int rr)
 {
     const int dy = rr % 3 - 1, dz = rr / 3 - 1;
     const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
     const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
-    const float rcm2 = a.rc2 * 1.00002f;
+    const float rcm2 = d.rc2 * 1.00002f;
     const float t = rcm2 - fmaf(ey, ey, ez * ez);
     if (!(t > 0.f)) return -1.f;
     const float tt = fmaxf(t, 1e-30f);
-    return tt * rsqrtf(tt) + a.slack;
+    return tt * rsqrtf(tt) + d.slack;
 }
 
 // Global-memory path (mode 1) for one target: per row, binary search of the
 // window start inside the cell of x - w, scan until x > x + w.
-template <class Acc>
+template <class Acc, int KERNEL>
 __device__ __forceinline__ void target_sums_global(const InteractArgs& a, const Smem& sm, float xt,
-                                                   float yt, float zt, int cy, int cz, Sums<Acc>& r)
+                                                   float yt, float zt, uint32_t slot, int cy, int cz,
+                                                   const KParams& kp, Sums<Acc, KERNEL>& r)
 {
     const Plan& p = sm.plan;
-    const Faces f = faces_of(a, yt, zt, cy, cz);
+    const SysDesc& d = sm.d;
+    const Faces f = faces_of(d, yt, zt, cy, cz);
 #pragma unroll 1
     for (int rr = 0; rr < 9; ++rr) {
         const int len = p.rlen[rr];
         if (len == 0) continue;
-        const float w = row_halfwidth(a, f, rr);
+        const float w = row_halfwidth(d, f, rr);
         if (w < 0.f) continue;
         const float xlo = xt - w, xhi = xt + w;
-        int k = axis_cell(xlo, a.g.lo[0], a.g.inv_w[0], a.g.n[0]) - p.xa;
+        int k = axis_cell(xlo, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa;
         k = min(max(k, 0), p.xb - p.xa);
         const float4* row = a.P + p.gbeg[rr];
         int lo = (int)sm.tbl.cs[rr][k], hi = (int)sm.tbl.cs[rr][k + 1];
@@ -384,14 +438,15 @@ __device__ __forceinline__ void target_sums_global(const InteractArgs& a, const 
         for (int j = lo; j < len; ++j) {
             const float4 q = row[j];
             if (q.x > xhi) break;
-            r.pair(__fsub_rn(q.x, xt), __fsub_rn(q.y, yt), __fsub_rn(q.z, zt), a.rc2, a.kscale);
+            if (self_by_identity<KERNEL>() && __float_as_uint(q.w) == slot) continue;
+            r.pair(__fsub_rn(q.x, xt), __fsub_rn(q.y, yt), __fsub_rn(q.z, zt), d.rc2, kp);
         }
     }
 }
 
-// Two candidates at once with packed FP32 (f32x2) arithmetic: every element
-// is rounded exactly as the scalar operation would be, so the pair test and
-// the sums are those of Sums::pair_nb.
+// Two Gaussian candidates at once with packed FP32 (f32x2) arithmetic:
+// every element is rounded exactly as the scalar operation would be, so the
+// pair test and the sums are those of Sums::pair_nb.
 struct PackedSums {
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
@@ -418,26 +473,29 @@ struct PackedSums {
 // Sums of one target over the staged rows (mode 0).  Per row: the x-window
 // from the row's lookup table, trimmed to [x - w, x + w] exactly; every
 // source in it is a candidate, taken two at a time.
-template <class Acc>
-__device__ __forceinline__ void target_sums_staged(const InteractArgs& a, const Smem& sm, float xt,
-                                                   float yt, float zt, int cy, int cz, int ncell,
-                                                   float inv4, Sums<Acc>& r)
+template <class Acc, int KERNEL>
+__device__ __forceinline__ void target_sums_staged(const Smem& sm, float xt, float yt, float zt,
+                                                   uint32_t slot, int cy, int cz, int ncell,
+                                                   float inv4, const KParams& kp,
+                                                   Sums<Acc, KERNEL>& r)
 {
+    constexpr bool by_id = self_by_identity<KERNEL>();
     const Plan& p = sm.plan;
-    const Faces f = faces_of(a, yt, zt, cy, cz);
+    const SysDesc& d = sm.d;
+    const Faces f = faces_of(d, yt, zt, cy, cz);
     const int nb = ncell * BPC, base = BPC * p.xa;
-    constexpr bool packed = std::is_same<Acc, PlainAcc>::value;
+    constexpr bool packed = std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
     PackedSums ps;
     const float2 mx = make_float2(-xt, -xt), my = make_float2(-yt, -yt), mz = make_float2(-zt, -zt),
-                 ks = make_float2(a.kscale, a.kscale);
+                 ks = make_float2(kp.t, kp.t);
 #pragma unroll 1
     for (int rr = 0; rr < 9; ++rr) {
         if (p.rlen[rr] == 0) continue;
-        const float w = row_halfwidth(a, f, rr);
+        const float w = row_halfwidth(d, f, rr);
         if (w < 0.f) continue;
         const float xlo = xt - w, xhi = xt + w;
-        int j = sm.tbl.bin[rr][xbin(xlo, a.g.lo[0], inv4, base, nb)];
-        int bh = xbin(xhi, a.g.lo[0], inv4, base, nb) + 1;
+        int j = sm.tbl.bin[rr][xbin(xlo, d.g.lo[0], inv4, base, nb)];
+        int bh = xbin(xhi, d.g.lo[0], inv4, base, nb) + 1;
         if (sm.coarse[rr]) bh = (bh + BPC - 1) / BPC * BPC;
         int je = sm.tbl.bin[rr][bh];
         while (j < je && sm.buf[j].x < xlo) ++j;
@@ -447,18 +505,21 @@ __device__ __forceinline__ void target_sums_staged(const InteractArgs& a, const 
             for (; j + 1 < je; j += 2) {
                 const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
                 ps.pair2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z), mx,
-                         my, mz, a.rc2, ks);
+                         my, mz, d.rc2, ks);
             }
         } else {
             for (; j + 1 < je; j += 2) {
                 const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
-                r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), a.rc2, a.kscale);
-                r.pair_nb(__fsub_rn(s1.x, xt), __fsub_rn(s1.y, yt), __fsub_rn(s1.z, zt), a.rc2, a.kscale);
+                r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), d.rc2, kp,
+                          by_id && __float_as_uint(s0.w) == slot);
+                r.pair_nb(__fsub_rn(s1.x, xt), __fsub_rn(s1.y, yt), __fsub_rn(s1.z, zt), d.rc2, kp,
+                          by_id && __float_as_uint(s1.w) == slot);
             }
         }
         if (j < je) {
             const float4 s0 = sm.buf[j];
-            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), a.rc2, a.kscale);
+            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), d.rc2, kp,
+                      by_id && __float_as_uint(s0.w) == slot);
         }
     }
     if (packed) {
@@ -470,19 +531,18 @@ __device__ __forceinline__ void target_sums_staged(const InteractArgs& a, const 
     }
 }
 
-template <class Acc>
-__global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
+template <class Acc, int KERNEL>
+__global__ void __launch_bounds__(TT, 7) k_interact_tiled(InteractArgs a)
 {
     __shared__ Smem sm;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
-    const uint32_t rows = (uint32_t)ny * (uint32_t)nz;
-    const float inv4 = a.g.inv_w[0] * (float)BPC;
-    // K(0) of this hardware path: the self pair adds exactly this to S
-    const float k0 = ex2_approx(0.f);
+    // The self pair (r = 0) adds exactly kernel_value(0) to S and 1 to n;
+    // both are taken off at the end instead of testing identities per pair
+    // (except for the kernels of self_by_identity).
+    const float k0_scale_free = KERNEL == KERNEL_GAUSSIAN ? ex2_approx(0.f) : 0.f;
 
     if (tid == 0) {
         sm.failed = 0;
@@ -493,17 +553,37 @@ __global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
     uint32_t phase = 0;
 
     for (;;) {
-        if (tid == 0) sm.row = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
+        if (tid == 0) {
+            const uint32_t grow = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
+            sm.has_row = grow < a.rows;
+            if (grow < a.rows) {
+                const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.rbase, a.sy.S, grow);
+                sm.d = a.sy.sys[sid];
+                sm.t = a.kscale ? a.kscale[sid] : a.kscale0;
+                sm.row = grow - sm.d.row_base;
+            }
+        }
         __syncthreads();
+        if (!sm.has_row || sm.failed) break;
         const uint32_t row = sm.row;
-        if (row >= rows || sm.failed) break;
+        const SysDesc& d = sm.d;
+        const int nx = d.g.n[0], ny = d.g.n[1];
+        const float inv4 = d.g.inv_w[0] * (float)BPC;
         const int cy = (int)(row % (uint32_t)ny), cz = (int)(row / (uint32_t)ny);
-        const uint32_t rb0 = (uint32_t)nx * row;
+        const uint32_t rb0 = d.cell_base + (uint32_t)nx * row;
+        // the self pair's contribution (0 where it is excluded by identity)
+        float kself = k0_scale_free;
+        uint32_t nself = 1u;
+        if constexpr (KERNEL == KERNEL_LOWFLOP) kself = 1.0f;
+        if constexpr (self_by_identity<KERNEL>()) {
+            kself = 0.f;
+            nself = 0u;
+        }
 
         for (int x0 = 0; x0 < nx;) {
             if (warp == 0) {
                 if (lane < 9) sm.coarse[lane] = 0;
-                plan_chunk(a, sm.plan, x0, cy, cz, lane);
+                plan_chunk(a, d, sm.plan, x0, cy, cz, lane);
                 __syncwarp();
                 if (lane == 0 && sm.plan.mode == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -524,7 +604,8 @@ __global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
                 const int rr = e / (ncell + 1), k = e % (ncell + 1);
                 if (p.rlen[rr] == 0) continue;
                 const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
-                const uint32_t cidx = (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xa + k;
+                const uint32_t cidx =
+                    d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xa + k;
                 const uint32_t g = a.offsets[cidx];
                 if (mode == 0) {
                     const int start = p.sbeg[rr] + (int)(g - p.gbeg[rr]);
@@ -560,11 +641,16 @@ __global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
                 for (int q0 = 0; q0 < ntarget; q0 += TT) {
                     const int q = q0 + (int)tid;
                     if (q >= ntarget) continue;
-                    Sums<Acc> r;
+                    Sums<Acc, KERNEL> r;
+                    const KParams kp{sm.t, a.one, a.zero};
                     const float4 me = mode == 0 ? sm.buf[t0 + q] : a.P[tb + q];
-                    if (mode == 0) target_sums_staged<Acc>(a, sm, me.x, me.y, me.z, cy, cz, ncell, inv4, r);
-                    else target_sums_global<Acc>(a, sm, me.x, me.y, me.z, cy, cz, r);
-                    store_out(a, __float_as_uint(me.w), r, k0, 1u);
+                    const uint32_t slot = __float_as_uint(me.w);
+                    if (mode == 0)
+                        target_sums_staged<Acc, KERNEL>(sm, me.x, me.y, me.z, slot, cy, cz, ncell, inv4,
+                                                        kp, r);
+                    else
+                        target_sums_global<Acc, KERNEL>(a, sm, me.x, me.y, me.z, slot, cy, cz, kp, r);
+                    store_out(a, slot, r, kself, nself);
                 }
             }
             __syncthreads();
@@ -573,38 +659,60 @@ __global__ void __launch_bounds__(TT, 8) k_interact_tiled(InteractArgs a)
     }
 }
 
+template <class Acc>
+cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((a.n + 127) / 128);
+    switch (a.kernel) {
+        case KERNEL_LJ: k_interact_ppnl<Acc, KERNEL_LJ><<<blocks, 128, 0, s>>>(a); break;
+        case KERNEL_LOWFLOP: k_interact_ppnl<Acc, KERNEL_LOWFLOP><<<blocks, 128, 0, s>>>(a); break;
+        case KERNEL_HIGHFLOP: k_interact_ppnl<Acc, KERNEL_HIGHFLOP><<<blocks, 128, 0, s>>>(a); break;
+        default: k_interact_ppnl<Acc, KERNEL_GAUSSIAN><<<blocks, 128, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class Acc>
+cudaError_t launch_tiled_acc(const InteractArgs& a, unsigned grid, cudaStream_t s)
+{
+    switch (a.kernel) {
+        case KERNEL_LJ: k_interact_tiled<Acc, KERNEL_LJ><<<grid, TT, 0, s>>>(a); break;
+        case KERNEL_LOWFLOP: k_interact_tiled<Acc, KERNEL_LOWFLOP><<<grid, TT, 0, s>>>(a); break;
+        case KERNEL_HIGHFLOP: k_interact_tiled<Acc, KERNEL_HIGHFLOP><<<grid, TT, 0, s>>>(a); break;
+        default: k_interact_tiled<Acc, KERNEL_GAUSSIAN><<<grid, TT, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
                                  int* launches)
 {
     (void)num_sms;
-    const unsigned blocks = (unsigned)((a.n + 127) / 128);
-    if (kahan) k_interact_ppnl<KahanAcc><<<blocks, 128, 0, s>>>(a);
-    else k_interact_ppnl<PlainAcc><<<blocks, 128, 0, s>>>(a);
     *launches += 1;
-    return cudaGetLastError();
+    return kahan ? launch_ppnl_acc<KahanAcc>(a, s) : launch_ppnl_acc<PlainAcc>(a, s);
 }
 
-cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
-                                  int* launches)
+cudaError_t tiled_occupancy(bool kahan, int* per_sm)
 {
-    const uint32_t rows = (uint32_t)a.g.n[1] * (uint32_t)a.g.n[2];
-    int per_sm = 0;
-    cudaError_t oe;
-    if (kahan)
-        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<KahanAcc>, TT, 0);
-    else
-        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact_tiled<PlainAcc>, TT, 0);
-    if (oe != cudaSuccess) return oe;
-    if (per_sm < 1) per_sm = 1;
-    uint64_t grid = (uint64_t)num_sms * per_sm;
-    if (grid > rows) grid = rows;
+    // every kernel variant has the same shared memory; the Gaussian one
+    // stands for the register count
+    return kahan ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       per_sm, k_interact_tiled<KahanAcc, KERNEL_GAUSSIAN>, TT, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       per_sm, k_interact_tiled<PlainAcc, KERNEL_GAUSSIAN>, TT, 0);
+}
+
+cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, int per_sm,
+                                  cudaStream_t s, int* launches)
+{
+    uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm < 1 ? 1 : per_sm);
+    if (grid > a.rows) grid = a.rows;
     if (grid < 1) grid = 1;
-    if (kahan) k_interact_tiled<KahanAcc><<<(unsigned)grid, TT, 0, s>>>(a);
-    else k_interact_tiled<PlainAcc><<<(unsigned)grid, TT, 0, s>>>(a);
     *launches += 1;
-    return cudaGetLastError();
+    return kahan ? launch_tiled_acc<KahanAcc>(a, (unsigned)grid, s)
+                 : launch_tiled_acc<PlainAcc>(a, (unsigned)grid, s);
 }
 
 }  // namespace pi

@@ -1,11 +1,19 @@
 // pi_internal.cuh -- definitions shared by the libpi translation units.
 //
-// Layout of the device state of one context (one cudaMalloc arena):
-//   Ctrl            control words (scan ticket, error bits, M_C)
-//   counts[C]       particles per cell
-//   xbins[C]        per cell, where its 4 x-sub-bins start in P (k_xorder)
+// A context holds S >= 1 independent systems (pi_create makes S = 1).  Their
+// particles, cells and X-rows are concatenated in system order, so one
+// launch of each kernel covers every system; per-system geometry lives in a
+// device array of SysDesc, and the first particle / cell / X-row of each
+// system in three base arrays (S + 1 entries each).
+//
+// Layout of the device state (one cudaMalloc arena):
+//   Ctrl            control words (scan ticket, error bits, M_C, row counters)
+//   counts[C]       particles per cell (C = cells of all systems)
+//   xbins[C]        per cell, where its 4 x-sub-bins start in P (k_stabilise)
+//   pbase[S+1]      first particle of each system in the current step
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
+//   sys[S], cbase[S+1], rbase[S+1], kscale[S]   per-system constants
 //   cell[n_max]     cell of each input particle            (binning scratch)
 //   rank[n_max]     provisional slot inside its cell        (binning scratch)
 //   perm_u[n_max]   unstable slot -> input index            (binning scratch)
@@ -31,7 +39,7 @@ enum : uint32_t {
 struct Ctrl {
     uint32_t ticket;        // next scan tile to hand out
     uint32_t error;         // ERR_* bits, sticky until the next pi_bin
-    uint32_t max_per_cell;  // M_C of the last pi_bin
+    uint32_t max_per_cell;  // M_C of the last pi_bin (over all systems)
     uint32_t n;             // particle count of the last pi_bin
     uint32_t work[2];       // next X-row handed out by the tiled interaction;
                             // launch number q uses work[q & 1] and clears the other
@@ -46,13 +54,43 @@ struct Grid {
     int32_t n[3];
 };
 
+// One system's constants.
+struct SysDesc {
+    Grid g;
+    float cell_w[3];  // (hi - lo) / n, computed in FP64
+    float rc2;        // fl32(r_c * r_c)
+    float slack;      // absolute margin of the conservative x-windows
+    uint32_t cell_base;
+    uint32_t row_base;
+};
+
+constexpr int MAX_SYSTEMS = 2048;
+
+// The systems as kernels see them.
+struct Systems {
+    const SysDesc* sys;     // [S]
+    const uint32_t* pbase;  // [S+1] first particle (= first sorted slot) of each system
+    const uint32_t* cbase;  // [S+1] first cell
+    const uint32_t* rbase;  // [S+1] first X-row
+    int S;
+};
+
+// Largest s with base[s] <= v (base[0] = 0, nondecreasing).
+__device__ __forceinline__ int find_system(const uint32_t* base, int S, uint32_t v)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Scan tiling (a3): 256 threads x 16 counts per tile.
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
-
-// Padding (in elements) after the sorted position arrays.
-constexpr int SORTED_PAD = 16;
 
 // Cell index of a position (Sec. 2: "compute its cell index using its
 // physical position").  FP32, round-to-nearest subtract and multiply, floor,
@@ -88,34 +126,56 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Parameters of k_zero: clear [p, p + n_words), then write the S + 1
+// particle bases of this step.
+template <int NB>
+struct ZeroArgs {
+    uint32_t* p;
+    size_t n_words;
+    uint32_t* pbase;
+    int nb;  // entries of vals used (S + 1)
+    uint32_t vals[NB];
+};
+
 // Launch wrappers (each returns the cudaGetLastError of its launch).
-cudaError_t launch_zero(uint32_t* p, size_t n_words, cudaStream_t s);
-cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n, const Grid& g,
-                        uint32_t* counts, uint32_t* cell, uint32_t* rank, Ctrl* ctrl, int num_sms,
+cudaError_t launch_zero(uint32_t* p, size_t n_words, uint32_t* pbase, const uint32_t* vals, int nb,
                         cudaStream_t s);
+cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n,
+                        const Systems& sy, uint32_t* counts, uint32_t* cell, uint32_t* rank,
+                        Ctrl* ctrl, int num_sms, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
                         uint64_t wait_limit_ns, int withhold_first, cudaStream_t s);
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
                            const float* y, const float* z, uint32_t n, const uint32_t* offsets,
                            uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s);
-cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n, const Grid& g,
-                             const uint32_t* offsets, uint32_t* perm, float* sx, float* sy,
-                             float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl, int num_sms,
-                             cudaStream_t s);
+cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
+                             const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
+                             float* sy_out, float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl,
+                             int num_sms, cudaStream_t s);
+
+// Per-system scale of the interaction kernel, written from launch parameters
+// (vals[s] for s < S) into kscale.
+cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s);
+
+// Interaction kernels (PI_KERNEL_* of include/pi.h).
+enum : int { KERNEL_GAUSSIAN = 0, KERNEL_LJ = 1, KERNEL_LOWFLOP = 2, KERNEL_HIGHFLOP = 3 };
 
 struct InteractArgs {
+    Systems sy;
     const float4* P;        // x-ordered copy: (x, y, z, stable slot as bits)
-    const uint32_t* xbins;  // per cell: starts of its 4 x-sub-bins (see k_xorder)
+    const uint32_t* xbins;  // per cell: starts of its 4 x-sub-bins (see k_stabilise)
     const float* sx;
-    const float* sy;
+    const float* sy_pos;
     const float* sz;
     const uint32_t* offsets;
     const uint32_t* perm;
-    uint32_t n;
-    Grid g;
-    float rc2;     // fl32(r_c * r_c)
-    float kscale;  // fl32(-log2(e) / h^2): K = 2^(r2 * kscale)
+    uint32_t n;             // particles of all systems
+    uint32_t rows;          // X-rows of all systems
+    const float* kscale;    // [S]: Gaussian K = 2^(r2 * kscale[s]); Lennard-Jones sigma^2
+    float kscale0;          // the scale when S == 1 (kscale may then be null)
+    int kernel;             // KERNEL_*
+    float one, zero;        // 1 and 0, opaque to the compiler (high-FLOP kernel)
     float* S;
     float* Vx;
     float* Vy;
@@ -123,16 +183,16 @@ struct InteractArgs {
     uint32_t* nbr;
     int original_order;
     Ctrl* ctrl;
-    float slack;            // absolute margin for the conservative windows
     uint64_t wait_limit_ns; // bound of every device-side wait
     uint32_t seq;           // launch number of the tiled kernel (row counter slot)
-    float cell_w[3];        // cell widths (hi - lo) / n, computed in FP64
 };
 
 // Each adds the number of kernels it launched to *launches.
 cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
                                  int* launches);
-cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms,
+cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, int per_sm,
                                   cudaStream_t s, int* launches);
+// Resident CTAs per SM of the tiled kernel (queried once per context).
+cudaError_t tiled_occupancy(bool kahan, int* per_sm);
 
 }  // namespace pi

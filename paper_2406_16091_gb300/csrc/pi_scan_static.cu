@@ -69,7 +69,7 @@ extern "C" pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, u
     // and the descriptors this call uses (a cleared descriptor reads as "not
     // ready", so one fixed epoch suffices)
     const size_t words = (sizeof(pi::Ctrl) + tiles * sizeof(unsigned long long)) / 4;
-    if (pi::launch_zero((uint32_t*)base, words, s) != cudaSuccess) return PI_ERR_CUDA;
+    if (pi::launch_zero((uint32_t*)base, words, nullptr, nullptr, 0, s) != cudaSuccess) return PI_ERR_CUDA;
     if (pi::launch_scan(counts, (uint32_t)C, offsets, status, ctrl, 1u, 1000000000ull, 0, s) !=
         cudaSuccess)
         return PI_ERR_CUDA;

@@ -1,0 +1,127 @@
+"""GPU parity for the other interaction kernels (Sec. 7.1-7.2) and for
+batches of independent systems run in one launch per kernel."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_16091_gb300 import binding as B
+from paper_2406_16091_gb300 import workloads as W
+
+from gpu_harness import TOL, check_binning, check_interaction, oracle_run, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = [(B.PI_KERNEL_LJ, oracle.LJ), (B.PI_KERNEL_LOWFLOP, oracle.LOWFLOP),
+           (B.PI_KERNEL_HIGHFLOP, oracle.HIGHFLOP), (B.PI_KERNEL_GAUSSIAN, oracle.GAUSSIAN)]
+
+
+@pytest.mark.parametrize("algo", [B.PI_ALGO_TILED, B.PI_ALGO_PPNL])
+@pytest.mark.parametrize("kern", KERNELS)
+@pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
+def test_kernel_parity(algo, kern, precision):
+    gk, ok = kern
+    w = W.scaled(W.SMALL, 20000)
+    x, y, z = w.positions()
+    b, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h, ok)
+    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, algo=algo, precision=precision, kernel=gk)
+    check_binning(g, b)
+    check_interaction(g, r)
+
+
+def _systems(seed=5):
+    """Uneven systems: different sizes, boxes, cutoffs, layouts, an empty one."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(12):
+        n = int(np.exp(rng.uniform(np.log(300), np.log(30000))))
+        if k == 3:
+            n = 0
+        if k == 4:
+            n = 1
+        cells = int(rng.integers(3, 24))
+        lo = tuple(float(v) for v in rng.uniform(-2, 2, 3).astype(np.float32))
+        ext = float(rng.uniform(0.5, 2.0))
+        hi = tuple(float(np.float32(v + ext)) for v in lo)
+        rc = W.rc_for_cells(cells, ext) * 0.999
+        if k % 4 == 1 and n > 10:
+            x, y, z = W.clustered(n, 100 + k)
+            x = (np.float32(lo[0]) + np.float32(ext) * x).astype(np.float32)
+            y = (np.float32(lo[1]) + np.float32(ext) * y).astype(np.float32)
+            z = (np.float32(lo[2]) + np.float32(ext) * z).astype(np.float32)
+            x = np.minimum(x, np.nextafter(np.float32(hi[0]), np.float32(lo[0])))
+            y = np.minimum(y, np.nextafter(np.float32(hi[1]), np.float32(lo[1])))
+            z = np.minimum(z, np.nextafter(np.float32(hi[2]), np.float32(lo[2])))
+        else:
+            x, y, z = W.uniform(n, 100 + k, lo, hi)
+        out.append(dict(n=n, lo=lo, hi=hi, rc=rc, h=rc / 2, x=x, y=y, z=z))
+    return out
+
+
+@pytest.mark.parametrize("algo", [B.PI_ALGO_TILED, B.PI_ALGO_PPNL])
+@pytest.mark.parametrize("order", [B.PI_ORDER_SORTED, B.PI_ORDER_ORIGINAL])
+def test_batch_matches_each_system_alone(algo, order):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    systems = _systems()
+    ns = [s["n"] for s in systems]
+    N = sum(ns)
+    ctx = B.pi_batch_create([(s["lo"], s["hi"]) for s in systems], [s["rc"] for s in systems],
+                            [n + 5 for n in ns])
+    try:
+        B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
+        S_, C, _ = B.pi_batch_info(ctx)
+        assert S_ == len(systems)
+        cat = lambda k: torch.from_numpy(np.concatenate([s[k] for s in systems]).astype(np.float32)).to(dev)
+        st = torch.cuda.current_stream()
+        tx, ty, tz = cat("x"), cat("y"), cat("z")
+        out = [torch.full((N,), float("nan"), device=dev) for _ in range(4)]
+        nb = torch.full((N,), -1, dtype=torch.int32, device=dev)
+        B.pi_batch_bin(ctx, tx, ty, tz, ns, st)
+        B.pi_batch_interact(ctx, [s["h"] for s in systems], *out, nb, order, st)
+        counts = torch.empty(C, dtype=torch.int32, device=dev)
+        offsets = torch.empty(C + 1, dtype=torch.int32, device=dev)
+        perm = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+        B.pi_copy_binned(ctx, counts, offsets, perm, None, None, None, st)
+        status, mpc = B.pi_sync_status(ctx, st, raise_on_error=False)
+        assert status == B.PI_OK
+        counts = counts.cpu().numpy().view(np.uint32)
+        offsets = offsets.cpu().numpy().view(np.uint32)
+        perm = perm.cpu().numpy().view(np.uint32)[:N]
+        outs = [o.cpu().numpy() for o in out]
+        nbr = nb.cpu().numpy().view(np.uint32)
+        p0 = c0 = 0
+        best_mpc = 0
+        for k, s in enumerate(systems):
+            b, r = oracle_run(s["x"], s["y"], s["z"], s["lo"], s["hi"], s["rc"], s["h"])
+            dims = B.pi_batch_grid(ctx, k)
+            assert tuple(dims) == tuple(b.dims)
+            c1 = c0 + int(np.prod(dims))
+            n = s["n"]
+            assert np.array_equal(counts[c0:c1], b.counts)
+            assert np.array_equal(offsets[c0:c1 + 1] - p0, b.offsets)
+            assert np.array_equal(perm[p0:p0 + n] - p0, b.perm)
+            best_mpc = max(best_mpc, b.max_per_cell)
+            if n:
+                sl = slice(p0, p0 + n)
+                g = {"S": outs[0][sl], "Vx": outs[1][sl], "Vy": outs[2][sl], "Vz": outs[3][sl],
+                     "nbr": nbr[sl]}
+                check_interaction(g, r, perm=b.perm if order == B.PI_ORDER_ORIGINAL else None)
+            p0 += n
+            c0 = c1
+        assert c0 == C and mpc == best_mpc
+    finally:
+        B.pi_destroy(ctx)
+
+
+def test_batch_rejects_bad_counts():
+    torch = pytest.importorskip("torch")
+    ctx = B.pi_batch_create([((0, 0, 0), (1, 1, 1))] * 2, [0.1, 0.2], [10, 10])
+    try:
+        buf = torch.zeros(32, device="cuda")
+        with pytest.raises(B.PiError) as e:
+            B.pi_batch_bin(ctx, buf, buf, buf, [5, 11])
+        assert e.value.status == B.PI_ERR_CAPACITY
+        with pytest.raises(B.PiError):
+            B.pi_bin(ctx, buf, buf, buf, 3)  # single-system call on a batch
+    finally:
+        B.pi_destroy(ctx)

@@ -212,3 +212,47 @@ def test_paper_candidates_per_particle(golden_dir):
             assert per == n - 1 == v
         elif n >= 5000:
             assert abs(per / v - 1) < 0.02, (d, m, per, v)
+
+
+@pytest.mark.parametrize("kernel", [oracle.LJ, oracle.LOWFLOP, oracle.HIGHFLOP])
+def test_other_kernels_equal_brute_force(kernel):
+    n, lo, hi, rc = 2000, (0, 0, 0), (1, 1, 1), 0.1
+    x, y, z = W.uniform(n, 31, lo, hi)
+    b = oracle.bin_particles(x, y, z, lo, hi, rc)
+    r = oracle.interact(b, rc, rc / 2, kernel)
+    u = lambda a: oracle.unpermute(a, b.perm)
+    bS, bVx, bVy, bVz, bnb = oracle.brute(x, y, z, rc, rc / 2, kernel)
+    assert np.array_equal(u(r.nbr), bnb)
+    assert np.allclose(u(r.S), bS, rtol=1e-12, atol=1e-12 * np.abs(bS).max())
+    assert np.allclose(u(r.Vx), bVx, rtol=1e-12, atol=1e-12 * np.abs(bVx).max())
+
+
+def test_lennard_jones_well_depth():
+    """Sec. 7.1's potential with E0 = 1: at s^3 = 1/2 (s = sigma^2 /
+    (r^2 + sigma^2/100)) it reaches its minimum, -E0 = -1."""
+    sigma = float(np.float32(0.05))  # the oracle takes h as FP32
+    r2 = sigma * sigma * (2.0 ** (1.0 / 3.0) - 0.01)
+    r = math.sqrt(r2)
+    x = np.array([0.3, 0.3 + r], np.float32)
+    d = float(x[1]) - float(x[0])
+    s = sigma * sigma / (d * d + sigma * sigma / 100)
+    b = oracle.bin_particles(x, [0.5, 0.5], [0.5, 0.5], (0, 0, 0), (1, 1, 1), 0.2)
+    res = oracle.interact(b, 0.2, sigma, oracle.LJ)
+    assert res.S[0] == pytest.approx(4 * (s ** 6 - s ** 3), rel=1e-12)
+    assert res.S[0] == pytest.approx(-1.0, abs=1e-6)
+    # far outside the well the potential is repulsive near r = 0 and tends to 0
+    assert res.absS[0] == pytest.approx(4 * (s ** 6 + s ** 3), rel=1e-12)
+
+
+def test_lowflop_kernel_counts():
+    """K = 1: S equals the neighbour count and V the summed offsets."""
+    w = W.scaled(W.SMALL, 3000)
+    x, y, z = w.positions()
+    b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
+    r1 = oracle.interact(b, w.rc, w.h, oracle.LOWFLOP)
+    r2 = oracle.interact(b, w.rc, 1e30, oracle.GAUSSIAN)
+    assert np.array_equal(r1.S, r1.nbr.astype(np.float64))
+    assert np.allclose(r1.Vx, r2.Vx, rtol=1e-12, atol=1e-15)
+    rh = oracle.interact(b, w.rc, w.h, oracle.HIGHFLOP)
+    rl = oracle.interact(b, w.rc, w.h, oracle.LJ)
+    assert np.array_equal(rh.S, rl.S)
