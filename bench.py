@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--flush-mb", type=int, default=512)
+    p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
+                   default="none", help="run one of the extra studies instead of the main line")
+    p.add_argument("--jobs", type=int, default=400, help="serving study: number of jobs")
     return p.parse_args()
 
 
@@ -406,9 +409,267 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+
+# ---------------------------------------------------------------- studies
+#
+# Extra measurements, one JSON line each ("study": name).  They are not the
+# benchmark line the contract above defines; they cover the other workloads:
+# the precision study (clustered workload, FP32 vs Kahan vs the FP64 oracle),
+# the batched workload (many uneven systems in one launch vs one launch set
+# per system), the serving workload (Poisson arrivals) and a sweep of
+# occupancy, interaction kernel and algorithm.
+
+
+def _torch_setup():
+    import torch
+
+    from paper_2406_16091_gb300 import binding as B
+    from paper_2406_16091_gb300 import build as pibuild
+
+    torch.cuda.set_device(0)
+    pibuild.build()
+    B.load()
+    return torch, B
+
+
+def _time_events(torch, fn, reps, flush=None):
+    """Median and mean milliseconds of fn() over reps runs (CUDA events on the
+    current stream), with an optional L2 flush before each run."""
+    s = torch.cuda.current_stream()
+    ts = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), statistics.fmean(ts)
+
+
+def study_precision(args):
+    """Clustered workload: the sums of plain FP32 and of Kahan-compensated
+    FP32 accumulation against the FP64 oracle, error stated per output, plus
+    the FP64 GPU totals of V (which vanish up to rounding)."""
+    import oracle
+
+    torch, B = _torch_setup()
+    w = W.WORKLOADS["clustered"]
+    x, y, z = w.positions()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
+    r = oracle.interact(b, w.rc, w.h)
+    t_oracle = time.perf_counter() - t0
+    ctx = B.pi_create(w.lo, w.hi, w.rc, w.n)
+    s = torch.cuda.current_stream()
+    tx, ty, tz = (torch.from_numpy(a).to(dev) for a in (x, y, z))
+    out = [torch.empty(w.n, device=dev) for _ in range(4)]
+    nb = torch.empty(w.n, dtype=torch.int32, device=dev)
+    tot = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = {"study": "precision", "workload": "clustered: " + w.note, "n": w.n,
+           "pairs": int(r.nbr.sum()), "oracle_seconds": t_oracle, "oracle_threads": oracle.num_threads()}
+    B.pi_bin(ctx, tx, ty, tz, w.n, s)
+    for name, prec in (("fp32", B.PI_PREC_FP32), ("kahan", B.PI_PREC_KAHAN)):
+        B.pi_set_option(ctx, B.PI_OPT_PRECISION, prec)
+        B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+        B.pi_sync_status(ctx, s)
+        ms, _ = _time_events(torch, lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s), 10)
+        entry = {"interact_ms": ms,
+                 "nbr_exact": bool(np.array_equal(nb.cpu().numpy().view(np.uint32), r.nbr))}
+        for k, (o, ref, ab) in enumerate(zip(out, (r.S, r.Vx, r.Vy, r.Vz),
+                                             (r.absS, r.absVx, r.absVy, r.absVz))):
+            g = o.cpu().numpy().astype(np.float64)
+            nz = ab > 0
+            rel = np.abs(g[nz] - ref[nz]) / ab[nz]
+            key = ("S", "Vx", "Vy", "Vz")[k]
+            entry[key] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+                          "p99_rel": float(np.percentile(rel, 99)),
+                          "max_abs": float(np.abs(g - ref).max())}
+            if k > 0:
+                B.pi_total_f64(ctx, o, tot, s)
+                entry[key]["gpu_fp64_total"] = float(tot.cpu()[0])
+                entry[key]["total_over_sum_abs"] = abs(float(tot.cpu()[0])) / float(ab.sum())
+        res[name] = entry
+    B.pi_destroy(ctx)
+    print(json.dumps(res), flush=True)
+
+
+def study_batched(args):
+    """The batched workload: 256 uneven systems in one context (one launch per
+    kernel, graph-captured, tile shape autotuned) against one context and one
+    launch set per system, at the same accuracy (bitwise-equal outputs)."""
+    torch, B = _torch_setup()
+    dev = torch.device("cuda", 0)
+    systems = W.batched_systems()
+    ns = [sy.n for sy in systems]
+    N = sum(ns)
+    pos = [sy.positions() for sy in systems]
+    cat = lambda k: torch.from_numpy(np.concatenate([p[k] for p in pos])).to(dev)
+    tx, ty, tz = cat(0), cat(1), cat(2)
+    hs = [sy.h for sy in systems]
+    s = torch.cuda.current_stream()
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, device=dev)
+    # --- batched
+    ctx = B.pi_batch_create([(sy.lo, sy.hi) for sy in systems], [sy.rc for sy in systems], ns)
+    out = [torch.empty(N, device=dev) for _ in range(4)]
+    nb = torch.empty(N, dtype=torch.int32, device=dev)
+    B.pi_batch_bin(ctx, tx, ty, tz, ns, s)
+    tile, tile_ms = B.pi_autotune(ctx, hs, *out, nb, B.PI_ORDER_SORTED, 5, s)
+
+    def step_batch():
+        B.pi_batch_bin(ctx, tx, ty, tz, ns, s)
+        B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, s)
+
+    for _ in range(3):
+        step_batch()
+    pairs = int(nb.to(torch.int64).sum().item())
+    ms_batch, _ = _time_events(torch, step_batch, 20, flush)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(s)
+    with torch.cuda.stream(cs):
+        step_batch_cs = lambda: (B.pi_batch_bin(ctx, tx, ty, tz, ns, cs),
+                                 B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, cs))
+        step_batch_cs()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=cs):
+            step_batch_cs()
+    s.wait_stream(cs)
+    ms_graph, _ = _time_events(torch, g.replay, 20, flush)
+    B.pi_sync_status(ctx, s)
+    batch_out = [o.clone() for o in out] + [nb.clone()]
+    # --- one context per system, launched one after the other
+    ctxs = [B.pi_create(sy.lo, sy.hi, sy.rc, sy.n) for sy in systems]
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    views = lambda t, k: t[int(offs[k]):int(offs[k + 1])]
+
+    def step_plain(stream=s):
+        for k, c in enumerate(ctxs):
+            B.pi_bin(c, views(tx, k), views(ty, k), views(tz, k), ns[k], stream)
+            B.pi_interact(c, hs[k], *[views(o, k) for o in out], views(nb, k), B.PI_ORDER_SORTED, stream)
+
+    for _ in range(3):
+        step_plain()
+    ms_plain, _ = _time_events(torch, step_plain, 10, flush)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cs):
+        step_plain(cs)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g2, stream=cs):
+            step_plain(cs)
+    s.wait_stream(cs)
+    ms_plain_graph, _ = _time_events(torch, g2.replay, 10, flush)
+    torch.cuda.synchronize()
+    same = all(torch.equal(a.view(torch.int32), b.view(torch.int32))
+               for a, b in zip(batch_out, [o for o in out] + [nb]))
+    for c in ctxs:
+        B.pi_destroy(c)
+    B.pi_destroy(ctx)
+    res = {"study": "batched", "systems": len(systems), "particles": N, "pairs": pairs,
+           "tile_chosen": tile, "tile_ms": tile_ms,
+           "batched_ms": ms_batch, "batched_graph_ms": ms_graph,
+           "plain_ms": ms_plain, "plain_graph_ms": ms_plain_graph,
+           "batched_graph_pairs_per_s": pairs / (ms_graph * 1e-3),
+           "plain_pairs_per_s": pairs / (ms_plain * 1e-3),
+           "speedup_vs_plain": ms_plain / ms_graph,
+           "speedup_vs_plain_graph": ms_plain_graph / ms_graph,
+           "outputs_bitwise_equal": bool(same),
+           "l2": "flushed before every timed step"}
+    print(json.dumps(res), flush=True)
+
+
+def study_serving(args):
+    """The serving workload: jobs of N log-uniform in [1k, 1M], occupancy in
+    {2, 4, 8, 16}, half uniform and half clustered.  First the capacity (all
+    jobs queued at once), then Poisson arrivals at 50 %, 80 % and 95 % of it."""
+    torch, B = _torch_setup()
+    from paper_2406_16091_gb300.serving import Server, make_job
+
+    specs = W.serving_jobs(args.jobs)
+    t0 = time.perf_counter()
+    jobs = []
+    for k, sp in enumerate(specs):
+        x, y, z = sp.positions()
+        jobs.append(make_job(k, x, y, z, sp.lo, sp.hi, sp.rc, sp.h))
+    t_gen = time.perf_counter() - t0
+    srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=8)
+    res = {"study": "serving", "jobs": len(jobs), "particles": sum(j.n for j in jobs),
+           "generation_s": t_gen}
+    try:
+        # warm-up: every slot once
+        warm = jobs[: min(20, len(jobs))]
+        for j in warm:
+            j.arrival = 0.0
+        srv.run(warm)
+        for j in jobs:
+            j.arrival = 0.0
+        cap = srv.run(jobs)
+        res["capacity"] = cap
+        rng = np.random.default_rng(1005)
+        for frac in (0.5, 0.8, 0.95):
+            rate = frac * cap["jobs_per_s"]
+            t = np.cumsum(rng.exponential(1.0 / rate, len(jobs)))
+            for j, a in zip(jobs, t):
+                j.arrival = float(a)
+            res[f"load_{int(frac * 100)}"] = srv.run(jobs)
+    finally:
+        srv.close()
+    print(json.dumps(res), flush=True)
+
+
+def study_sweep(args):
+    """Interaction throughput over occupancy (1-32 particles per cell), over
+    the interaction kernels of Sec. 7.1-7.2, and the tiled kernel's speedup
+    over Par-Part-NoLoop (Alg. 1) -- the paper's comparison."""
+    torch, B = _torch_setup()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, device=dev)
+    s = torch.cuda.current_stream()
+    rows = []
+    names = ["scale_ppc1", "scale_ppc2", "scale_ppc4", "scale", "scale_ppc16", "scale_ppc32"]
+    kernels = [("gaussian", B.PI_KERNEL_GAUSSIAN), ("lj", B.PI_KERNEL_LJ),
+               ("lowflop", B.PI_KERNEL_LOWFLOP), ("highflop", B.PI_KERNEL_HIGHFLOP)]
+    for name in names:
+        w = W.WORKLOADS[name]
+        x, y, z = w.positions()
+        ctx = B.pi_create(w.lo, w.hi, w.rc, w.n)
+        t = [torch.from_numpy(a).to(dev) for a in (x, y, z)]
+        out = [torch.empty(w.n, device=dev) for _ in range(4)]
+        nb = torch.empty(w.n, dtype=torch.int32, device=dev)
+        B.pi_bin(ctx, *t, w.n, s)
+        B.pi_sync_status(ctx, s)
+        for kname, kern in kernels if name == "scale" else kernels[:1]:
+            B.pi_set_option(ctx, B.PI_OPT_KERNEL, kern)
+            entry = {"workload": name, "kernel": kname}
+            for algo_name, algo in (("tiled", B.PI_ALGO_TILED), ("ppnl", B.PI_ALGO_PPNL)):
+                B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
+                run = lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+                run()
+                ms, _ = _time_events(torch, run, 10, flush)
+                entry[f"{algo_name}_ms"] = ms
+            pairs = int(nb.to(torch.int64).sum().item())
+            entry["pairs"] = pairs
+            entry["tiled_pairs_per_s"] = pairs / (entry["tiled_ms"] * 1e-3)
+            entry["speedup_vs_ppnl"] = entry["ppnl_ms"] / entry["tiled_ms"]
+            rows.append(entry)
+        B.pi_set_option(ctx, B.PI_OPT_KERNEL, B.PI_KERNEL_GAUSSIAN)
+        B.pi_set_option(ctx, B.PI_OPT_ALGO, B.PI_ALGO_TILED)
+        B.pi_sync_status(ctx, s)
+        B.pi_destroy(ctx)
+    print(json.dumps({"study": "sweep", "rows": rows}), flush=True)
+
+
+STUDIES = {"precision": study_precision, "batched": study_batched, "serving": study_serving,
+           "sweep": study_sweep}
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.study != "none":
+        STUDIES[args.study](args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -84,7 +84,11 @@ enum {
      * and pi_sync_status() returns PI_ERR_TIMEOUT.  Default 0. */
     PI_OPT_TEST_WITHHOLD_SCAN = 4,
     /* Interaction kernel K (PI_KERNEL_*), default PI_KERNEL_GAUSSIAN. */
-    PI_OPT_KERNEL = 5
+    PI_OPT_KERNEL = 5,
+    /* Tile shape of the tiled interaction: 0, 1, 2 for 64, 128, 256 targets
+     * (threads) per chunk with 640, 1280, 2560 staged particles; default 1.
+     * pi_autotune sets it from measurements.  Results do not depend on it. */
+    PI_OPT_TILE = 6
 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
 enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
@@ -111,6 +115,16 @@ enum { PI_KERNEL_GAUSSIAN = 0, PI_KERNEL_LJ = 1, PI_KERNEL_LOWFLOP = 2, PI_KERNE
  * Allocates all device buffers once (about 28 B per particle + 8 B per cell).
  * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA. */
 pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out);
+
+/* Re-targets a single-system context to another box and cutoff without
+ * allocating: the grid of (box, r_c) must have at most as many cells as the
+ * grid the context was created with (PI_ERR_CAPACITY otherwise); n_max is
+ * unchanged.  The new constants are written by a launch on `stream`, so work
+ * enqueued on that stream afterwards sees them; the context must be binned
+ * again before pi_interact.  Used to keep device-resident contexts for jobs
+ * of varying shape (serving).  Errors: PI_ERR_INVALID_ARG (also for a batch
+ * context), PI_ERR_CAPACITY, PI_ERR_CUDA. */
+pi_status pi_reconfigure(pi_ctx* ctx, const pi_box* box, float r_c, pi_stream stream);
 
 /* Frees the context and its device buffers (synchronises the device first).
  * NULL is accepted. */
@@ -190,6 +204,20 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
 pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                             uint32_t* nbr, int out_order, pi_stream stream);
 
+/* Autotuner of the tiled interaction's tile shape (PI_OPT_TILE) for the
+ * data of the last pi_bin / pi_batch_bin: runs the interaction (arguments as
+ * pi_batch_interact, h one entry per system) once untimed and `reps` times
+ * timed (1 <= reps <= 100) for each shape, keeps the shape with the
+ * smallest median time for later calls, and returns it in *chosen and the
+ * medians in ms[3] (milliseconds; either pointer may be NULL).  The shape
+ * changes only the speed: the outputs are the same for every shape (each
+ * target's terms are summed in the same order).  Synchronises `stream`.  The
+ * output arrays hold the last run's results.
+ * Errors: those of pi_batch_interact, PI_ERR_INVALID_ARG, PI_ERR_CUDA. */
+pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
+                      uint32_t* nbr, int out_order, int reps, int32_t* chosen, float* ms,
+                      pi_stream stream);
+
 /* Number of systems, total cells and total particle capacity (host outputs,
  * any may be NULL). */
 pi_status pi_batch_info(const pi_ctx* ctx, int32_t* num_systems, int64_t* total_cells,
@@ -217,6 +245,16 @@ pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t**
  * PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
 pi_status pi_copy_binned(const pi_ctx* ctx, uint32_t* counts, uint32_t* offsets, uint32_t* perm,
                          float* sx, float* sy, float* sz, pi_stream stream);
+
+/* FP64 totals for the invariant check of the interaction's vector sums: each
+ * within-cutoff pair appears once from each side with opposite d_ij, so the
+ * V outputs of a system total zero up to rounding (Sec. 2's pair set is
+ * symmetric).  v: device FP32 array over the particles of the last pi_bin
+ * (any of the outputs of pi_interact, in either order); out: device array of
+ * num_systems doubles, out[s] = sum of v over system s, accumulated in FP64
+ * in a fixed order (the same result on every run).  Asynchronous on stream.
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
+pi_status pi_total_f64(pi_ctx* ctx, const float* v, double* out, pi_stream stream);
 
 /* Synchronises `stream`, then returns the device-side status of the work
  * enqueued so far (PI_ERR_TIMEOUT, PI_ERR_OUT_OF_BOX, PI_ERR_CAPACITY or

@@ -31,6 +31,7 @@ PI_OPT_PRECISION = 2
 PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
+PI_OPT_TILE = 6
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1
 PI_KERNEL_LOWFLOP = 2
@@ -77,12 +78,15 @@ def load():
         "pi_batch_info": ([P, P, P, P], i32),
         "pi_batch_grid": ([P, i32, P], i32),
         "pi_destroy": ([P], i32),
+        "pi_reconfigure": ([P, ctypes.POINTER(PiBox), f32, P], i32),
         "pi_bin": ([P, P, P, P, i64, P], i32),
         "pi_interact": ([P, f32, P, P, P, P, P, i32, P], i32),
         "pi_run_host": ([P, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
         "pi_grid": ([P, P], i32),
         "pi_binned": ([P] + [ctypes.POINTER(P)] * 6, i32),
         "pi_copy_binned": ([P, P, P, P, P, P, P, P], i32),
+        "pi_total_f64": ([P, P, P, P], i32),
+        "pi_autotune": ([P, P, P, P, P, P, P, i32, i32, P, P, P], i32),
         "pi_scan_counts_noalloc": ([P, i64, P, P, P], i32),
         "pi_sync_status": ([P, P, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pi_set_option": ([P, i32, i64], i32),
@@ -182,6 +186,11 @@ def pi_batch_grid(ctx, system: int):
     return tuple(dims)
 
 
+def pi_reconfigure(ctx, lo, hi, r_c: float, stream=None) -> None:
+    box = PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi))
+    _check(load().pi_reconfigure(ctx, ctypes.byref(box), float(r_c), _stream(stream)), "pi_reconfigure")
+
+
 def pi_destroy(ctx) -> None:
     _check(load().pi_destroy(ctx), "pi_destroy")
 
@@ -229,6 +238,25 @@ def pi_scan_counts_noalloc(counts, C: int, offsets, result=None, stream=None) ->
     receives M_C and the device error bits."""
     _check(load().pi_scan_counts_noalloc(_ptr(counts), int(C), _ptr(offsets), _ptr(result),
                                          _stream(stream)), "pi_scan_counts_noalloc")
+
+
+def pi_autotune(ctx, h, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTED, reps: int = 3,
+                stream=None):
+    """Times every tile shape on the binned data, keeps the fastest.
+    Returns (chosen shape, [median ms per shape])."""
+    arr = (ctypes.c_float * len(h))(*[float(v) for v in h])
+    chosen = ctypes.c_int32()
+    ms = (ctypes.c_float * 3)()
+    _check(load().pi_autotune(ctx, ctypes.cast(arr, ctypes.c_void_p), _ptr(S), _ptr(Vx), _ptr(Vy),
+                              _ptr(Vz), _ptr(nbr), int(out_order), int(reps), ctypes.byref(chosen),
+                              ctypes.cast(ms, ctypes.c_void_p), _stream(stream)), "pi_autotune")
+    return chosen.value, list(ms)
+
+
+def pi_total_f64(ctx, v, out, stream=None) -> None:
+    """FP64 total of device array v over each system's particles into out
+    (device float64, one entry per system)."""
+    _check(load().pi_total_f64(ctx, _ptr(v), _ptr(out), _stream(stream)), "pi_total_f64")
 
 
 def pi_sync_status(ctx, stream=None, raise_on_error: bool = True):

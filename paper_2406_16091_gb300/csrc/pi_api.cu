@@ -27,13 +27,14 @@ struct pi_ctx {
     std::vector<int64_t> n_max;  // per system
     std::vector<SysDesc> sys;     // host copy of the per-system constants
     std::vector<uint32_t> cbase;  // [S+1]
-    std::vector<uint32_t> rbase;  // [S+1]
+    std::vector<uint32_t> wbase;  // [S+1]
     int64_t C;                    // cells of all systems
+    int64_t C_alloc;              // cells the arena was sized for
     int64_t n_max_total;
-    uint32_t rows;                // X-rows of all systems
+    uint32_t work;                // work items of the tiled interaction
     int device;
     int num_sms;
-    int tiled_per_sm[2];          // resident CTAs of the tiled kernel (plain, Kahan)
+    int tiled_per_sm[2][pi::NUM_TILES];  // resident CTAs of each tile shape (plain, Kahan)
 
     // device arena and its parts
     void* arena;
@@ -45,8 +46,9 @@ struct pi_ctx {
     unsigned long long* scan_status;
     SysDesc* d_sys;
     uint32_t* d_cbase;
-    uint32_t* d_rbase;
+    uint32_t* d_wbase;
     float* d_kscale;
+    double* d_partial;            // [S * TOTAL_PARTS] scratch of pi_total_f64
     uint32_t* cell;
     uint32_t* rank;
     uint32_t* perm_u;
@@ -78,6 +80,7 @@ struct pi_ctx {
     int algo;
     int precision;
     int kernel;
+    int tile;                       // tile shape of the tiled kernel (0..2)
     uint64_t wait_limit_ns;
     int withhold_scan;
 };
@@ -221,7 +224,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->n_max.assign(n_max, n_max + S);
     c->sys.resize(S);
     c->cbase.assign(S + 1, 0);
-    c->rbase.assign(S + 1, 0);
+    c->wbase.assign(S + 1, 0);
     c->pbase_h.assign(S + 1, 0);
     c->kscale_h.assign(S, std::nanf(""));
     int64_t C = 0, N = 0, R = 0;
@@ -233,32 +236,36 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
             delete c;
             return st;
         }
-        c->sys[s].cell_base = (uint32_t)C;
-        c->sys[s].row_base = (uint32_t)R;
+        SysDesc& d = c->sys[s];
+        d.nseg = (uint32_t)((d.g.n[0] + pi::SEG_CELLS - 1) / pi::SEG_CELLS);
+        d.cell_base = (uint32_t)C;
+        d.work_base = (uint32_t)R;
         c->cbase[s] = (uint32_t)C;
-        c->rbase[s] = (uint32_t)R;
+        c->wbase[s] = (uint32_t)R;
         C += cells;
-        R += (int64_t)c->sys[s].g.n[1] * c->sys[s].g.n[2];
+        R += (int64_t)d.g.n[1] * d.g.n[2] * d.nseg;
         N += n_max[s];
-        if (C >= ((int64_t)1 << 31) - 1 || N >= (int64_t)2147483647 - 64) {
+        if (C >= ((int64_t)1 << 31) - 1 || N >= (int64_t)2147483647 - 64 || R >= ((int64_t)1 << 31)) {
             delete c;
             return PI_ERR_INVALID_ARG;
         }
     }
     c->cbase[S] = (uint32_t)C;
-    c->rbase[S] = (uint32_t)R;
+    c->wbase[S] = (uint32_t)R;
     c->C = C;
+    c->C_alloc = C;
     c->n_max_total = N;
-    c->rows = (uint32_t)R;
+    c->work = (uint32_t)R;
     c->algo = PI_ALGO_TILED;
     c->precision = PI_PREC_FP32;
     c->kernel = PI_KERNEL_GAUSSIAN;
+    c->tile = 1;
     c->wait_limit_ns = 1000000000ull;
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
-    if (e == cudaSuccess) e = pi::tiled_occupancy(false, &c->tiled_per_sm[0]);
-    if (e == cudaSuccess) e = pi::tiled_occupancy(true, &c->tiled_per_sm[1]);
+    if (e == cudaSuccess) e = pi::tiled_occupancy(false, c->tiled_per_sm[0]);
+    if (e == cudaSuccess) e = pi::tiled_occupancy(true, c->tiled_per_sm[1]);
     if (e != cudaSuccess) {
         pi_status st = cuda_fail(e, "pi_batch_create: device query");
         delete c;
@@ -276,8 +283,9 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_status = k.take<unsigned long long>(tiles);
     const size_t o_sys = k.take<SysDesc>((size_t)S);
     const size_t o_cbase = k.take<uint32_t>((size_t)S + 1);
-    const size_t o_rbase = k.take<uint32_t>((size_t)S + 1);
+    const size_t o_wbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_kscale = k.take<float>((size_t)S);
+    const size_t o_partial = k.take<double>((size_t)S * pi::TOTAL_PARTS);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
     const size_t o_permu = k.take<uint32_t>(nm + 4);
@@ -304,8 +312,9 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->scan_status = (unsigned long long*)(base + o_status);
     c->d_sys = (SysDesc*)(base + o_sys);
     c->d_cbase = (uint32_t*)(base + o_cbase);
-    c->d_rbase = (uint32_t*)(base + o_rbase);
+    c->d_wbase = (uint32_t*)(base + o_wbase);
     c->d_kscale = (float*)(base + o_kscale);
+    c->d_partial = (double*)(base + o_partial);
     c->cell = (uint32_t*)(base + o_cell);
     c->rank = (uint32_t*)(base + o_rank);
     c->perm_u = (uint32_t*)(base + o_permu);
@@ -323,7 +332,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_cbase, c->cbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_rbase, c->rbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(c->d_wbase, c->wbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         pi_status st = cuda_fail(e, "pi_batch_create: initialise");
@@ -351,6 +360,36 @@ pi_status pi_destroy(pi_ctx* ctx)
     delete ctx;
     if (e != cudaSuccess) return cuda_fail(e, "pi_destroy: synchronize");
     if (e2 != cudaSuccess) return cuda_fail(e2, "pi_destroy: cudaFree");
+    return PI_OK;
+}
+
+pi_status pi_reconfigure(pi_ctx* ctx, const pi_box* box, float r_c, pi_stream stream)
+{
+    if (!ctx || !box) return PI_ERR_INVALID_ARG;
+    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
+    SysDesc d;
+    int64_t cells = 0;
+    const pi_status st = make_system(*box, r_c, d, cells);
+    if (st != PI_OK) return st;
+    if (cells > ctx->C_alloc) return PI_ERR_CAPACITY;
+    d.nseg = (uint32_t)((d.g.n[0] + pi::SEG_CELLS - 1) / pi::SEG_CELLS);
+    d.cell_base = 0;
+    d.work_base = 0;
+    const int64_t work = (int64_t)d.g.n[1] * d.g.n[2] * d.nseg;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_reconfigure: set device");
+    PI_TRY(pi::launch_set_system(ctx->d_sys, ctx->d_cbase, ctx->d_wbase, d, (uint32_t)cells,
+                                 (uint32_t)work, (cudaStream_t)stream));
+    ctx->launches += 1;
+    ctx->boxes[0] = *box;
+    ctx->rc[0] = r_c;
+    ctx->sys[0] = d;
+    ctx->cbase[1] = (uint32_t)cells;
+    ctx->wbase[1] = (uint32_t)work;
+    ctx->C = cells;
+    ctx->work = (uint32_t)work;
+    ctx->binned = 0;
+    std::fill(ctx->kscale_h.begin(), ctx->kscale_h.end(), std::nanf(""));
     return PI_OK;
 }
 
@@ -427,6 +466,10 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
             if (value != 0 && value != 1) return PI_ERR_INVALID_ARG;
             ctx->withhold_scan = (int)value;
             return PI_OK;
+        case PI_OPT_TILE:
+            if (value < 0 || value >= pi::NUM_TILES) return PI_ERR_INVALID_ARG;
+            ctx->tile = (int)value;
+            return PI_OK;
         case PI_OPT_KERNEL:
             if (value < PI_KERNEL_GAUSSIAN || value > PI_KERNEL_HIGHFLOP) return PI_ERR_INVALID_ARG;
             ctx->kernel = (int)value;
@@ -464,7 +507,7 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
     for (int k = 0; k < ctx->S; ++k) ctx->pbase_h[k + 1] = ctx->pbase_h[k] + (uint32_t)n[k];
     const uint32_t nn = (uint32_t)total;
     const uint32_t C = (uint32_t)ctx->C;
-    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_rbase, ctx->S};
+    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
 
     // control block, counts and xbins are one contiguous zeroed prefix of the
     // arena; the same launch writes this step's particle bases
@@ -516,7 +559,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     cudaStream_t st = (cudaStream_t)stream;
 
     pi::InteractArgs a{};
-    a.sy = pi::Systems{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_rbase, ctx->S};
+    a.sy = pi::Systems{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
     a.P = ctx->P;
     a.xbins = ctx->xbins;
     a.sx = ctx->sx;
@@ -525,7 +568,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     a.offsets = ctx->offsets;
     a.perm = ctx->perm;
     a.n = (uint32_t)ctx->n;
-    a.rows = ctx->rows;
+    a.work = ctx->work;
     a.kernel = ctx->kernel;
     a.one = 1.0f;
     a.zero = 0.0f;
@@ -562,13 +605,66 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     if (ctx->algo == PI_ALGO_PPNL) {
         e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, st, &launched);
     } else {
-        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], st,
-                                      &launched);
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0],
+                                      ctx->tile, st, &launched);
         ctx->tiled_seq += 1;
     }
     ctx->launches += (uint64_t)launched;
     if (e != cudaSuccess) return cuda_fail(e, "pi_interact: launch");
     return PI_OK;
+}
+
+pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
+                      uint32_t* nbr, int out_order, int reps, int32_t* chosen, float* ms,
+                      pi_stream stream)
+{
+    if (!ctx || !h || reps < 1 || reps > 100) return PI_ERR_INVALID_ARG;
+    if (!ctx->binned) return PI_ERR_NOT_BINNED;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_autotune: set device");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int saved_algo = ctx->algo;
+    ctx->algo = PI_ALGO_TILED;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PI_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "pi_autotune: event");
+    }
+    float best = 0.f;
+    int best_tile = ctx->tile;
+    pi_status result = PI_OK;
+    for (int t = 0; t < pi::NUM_TILES && result == PI_OK; ++t) {
+        ctx->tile = t;
+        // one untimed run, then the timed ones; the median counts
+        result = pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr, out_order, stream);
+        std::vector<float> times;
+        for (int r = 0; r < reps && result == PI_OK; ++r) {
+            ce = cudaEventRecord(e0, st);
+            if (ce == cudaSuccess) result = pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr, out_order, stream);
+            if (ce == cudaSuccess && result == PI_OK) ce = cudaEventRecord(e1, st);
+            if (ce == cudaSuccess && result == PI_OK) ce = cudaEventSynchronize(e1);
+            float m = 0.f;
+            if (ce == cudaSuccess && result == PI_OK) ce = cudaEventElapsedTime(&m, e0, e1);
+            if (ce != cudaSuccess && result == PI_OK) result = cuda_fail(ce, "pi_autotune: timing");
+            times.push_back(m);
+        }
+        if (result != PI_OK) break;
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (ms) ms[t] = med;
+        if (t == 0 || med < best) {
+            best = med;
+            best_tile = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->algo = saved_algo;
+    ctx->tile = best_tile;
+    if (chosen) *chosen = best_tile;
+    return result;
 }
 
 pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
@@ -577,6 +673,20 @@ pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, floa
     if (!ctx) return PI_ERR_INVALID_ARG;
     if (ctx->S != 1) return PI_ERR_INVALID_ARG;
     return pi_batch_interact(ctx, &h, S, Vx, Vy, Vz, nbr, out_order, stream);
+}
+
+pi_status pi_total_f64(pi_ctx* ctx, const float* v, double* out, pi_stream stream)
+{
+    if (!ctx || !out) return PI_ERR_INVALID_ARG;
+    if (!ctx->binned) return PI_ERR_NOT_BINNED;
+    if (ctx->n > 0 && !v) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_total_f64: set device");
+    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
+    PI_TRY(pi::launch_total_f64(ctx->n > 0 ? v : ctx->sx, sy, ctx->d_partial, pi::TOTAL_PARTS, out,
+                                (cudaStream_t)stream));
+    ctx->launches += 2;
+    return PI_OK;
 }
 
 pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)

@@ -438,6 +438,16 @@ cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32
 }
 
 namespace {
+__global__ void k_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, SysDesc d, uint32_t cells,
+                             uint32_t work)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sys[0] = d;
+        cbase[1] = cells;
+        wbase[1] = work;
+    }
+}
+
 struct KscaleArgs {
     float* dst;
     int S;
@@ -450,6 +460,13 @@ __global__ void k_set_kscale(KscaleArgs k)
         k.dst[i] = k.vals[i];
 }
 }  // namespace
+
+cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, const SysDesc& d,
+                              uint32_t cells, uint32_t work, cudaStream_t s)
+{
+    k_set_system<<<1, 32, 0, s>>>(sys, cbase, wbase, d, cells, work);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s)
 {

@@ -23,8 +23,9 @@
 //   k_interact_tiled  reads P, the x-ordered copy written by binning: the
 //                     sorted particles with every cell ordered by x, as float4
 //                     (x, y, z, stable slot); every X-row of P is sorted by x
-//                     as a whole.  One CTA per X-row of target
-//                     cells (rows handed out dynamically), in chunks of
+//                     as a whole.  Work items are segments of an X-row of
+//                     target cells, handed out dynamically from one queue
+//                     over all systems, and processed in chunks of
 //                     consecutive cells.  The 9 neighbour rows (y +- 1,
 //                     z +- 1) of a chunk are contiguous ranges of P, each
 //                     staged into shared memory with one cp.async.bulk copy
@@ -101,13 +102,15 @@ struct KParams {
     float t, one, zero;
 };
 
-// Kernels whose value at r = 0 is far larger than their typical sum: the
-// tiled kernel excludes the self pair by identity for them instead of adding
-// K(0) and taking it off again.
-template <int KERNEL>
+// Where the tiled kernel excludes the self pair by identity instead of
+// adding K(0) and taking it off again: kernels whose value at r = 0 is far
+// larger than their typical sum (Lennard-Jones), and the compensated
+// precision mode, where taking K(0) off would cost the accuracy of particles
+// whose sum is small next to K(0).
+template <int KERNEL, class Acc>
 __host__ __device__ constexpr bool self_by_identity()
 {
-    return KERNEL == KERNEL_LJ || KERNEL == KERNEL_HIGHFLOP;
+    return KERNEL == KERNEL_LJ || KERNEL == KERNEL_HIGHFLOP || std::is_same<Acc, KahanAcc>::value;
 }
 
 // Per-target accumulators of one interaction kernel.
@@ -190,8 +193,19 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 
 // ---- tiled interaction ----------------------------------------------------------
 
-constexpr int TT = 128;                     // threads per CTA = targets per chunk
-constexpr int CAP = 1280;                   // staged particles per chunk (20 KB of float4)
+// Tile shapes: threads per CTA (= targets per chunk) and staged particles per
+// chunk.  The autotuner (pi_autotune) picks one per context; every shape
+// gives the same per-target summation order, so the results are identical.
+template <int TT_, int CAP_, int MINB_>
+struct Tile {
+    static constexpr int TT = TT_;
+    static constexpr int CAP = CAP_;
+    static constexpr int MINB = MINB_;  // CTAs per SM the register budget is sized for
+};
+using Tile64 = Tile<64, 640, 16>;
+using Tile128 = Tile<128, 1280, 8>;
+using Tile256 = Tile<256, 2560, 4>;
+
 constexpr int MAXLX = 64;                   // target cells per chunk along X
 constexpr int BPC = 4;                      // x-bins per cell in the staged-row lookup
 constexpr int RBINS = (MAXLX + 2) * BPC + 2;
@@ -210,6 +224,7 @@ struct Plan {
     int total;  // staged particles
 };
 
+template <int CAP>
 struct Smem {
     float4 buf[CAP + 1];  // staged rows; one spare slot keeps a read one past the end inside
     union {
@@ -223,6 +238,7 @@ struct Smem {
     float t;        // its kernel scale
     int coarse[9];  // row holds a cell without sub-bin starts: end lookups use cell bounds
     uint32_t row;   // current X-row, local to its system
+    int xs, xe;     // its cells [xs, xe) handled by this work item
     int has_row;
     int failed;
     uint64_t bar;
@@ -282,74 +298,65 @@ __device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t phase, 
 // largest x1 such that the chunk has at most TT targets and its 9 source
 // rows hold at most CAP particles, plus each row's range.  A single cell
 // whose rows exceed CAP is read from global memory (mode 1).
-__device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int x0, int cy, int cz,
-                           unsigned lane)
+template <int TT, int CAP>
+__device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int x0, int xe, int cy,
+                           int cz, unsigned lane)
 {
     const int nx = d.g.n[0], ny = d.g.n[1], nz = d.g.n[2];
-    const uint32_t rb0 = d.cell_base + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
+    const uint32_t cb = d.cell_base;
+    const uint32_t rb0 = cb + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
     const int xa = max(x0 - 1, 0);
-    const int xmax = min(nx, x0 + MAXLX);
-    uint32_t rb[9], rstart[9];
-    bool rok[9];
+    const int xmax = min(xe, x0 + MAXLX);
+    // first particle of each row's source range (the same for every lane)
+    uint32_t rstart[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         const int by = cy + r % 3 - 1, bz = cz + r / 3 - 1;
-        rok[r] = by >= 0 && by < ny && bz >= 0 && bz < nz;
-        rb[r] = rok[r] ? d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) : 0u;
-        rstart[r] = rok[r] ? a.offsets[rb[r] + xa] : 0u;
+        const bool ok = by >= 0 && by < ny && bz >= 0 && bz < nz;
+        rstart[r] = ok ? a.offsets[cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xa]
+                       : 0u;
     }
     const uint32_t tgt0 = a.offsets[rb0 + x0];
     int best = 0;
     bool first_fits = true;
-    uint32_t best_end[9], first_end[9];
     for (int base = x0 + 1; base <= xmax; base += 32) {
         const int x1 = base + (int)lane;
-        const int xb = min(x1, nx - 1);
         bool valid = false, fits = true;
-        uint32_t rend[9];
         if (x1 <= xmax) {
+            const int xb = min(x1, nx - 1);
             const uint32_t targets = a.offsets[rb0 + x1] - tgt0;
             uint32_t staged = 0;
 #pragma unroll
             for (int r = 0; r < 9; ++r) {
-                rend[r] = rok[r] ? a.offsets[rb[r] + xb + 1] : 0u;
-                staged += rend[r] - rstart[r];
+                const int by = cy + r % 3 - 1, bz = cz + r / 3 - 1;
+                if (by < 0 || by >= ny || bz < 0 || bz >= nz) continue;
+                staged += a.offsets[cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xb + 1] -
+                          rstart[r];
             }
             fits = staged <= (uint32_t)CAP;
             valid = fits && targets <= (uint32_t)TT;
-        } else {
-#pragma unroll
-            for (int r = 0; r < 9; ++r) rend[r] = rstart[r];
         }
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (base == x0 + 1) {
-            first_fits = __shfl_sync(0xffffffffu, fits, 0);
-#pragma unroll
-            for (int r = 0; r < 9; ++r) first_end[r] = __shfl_sync(0xffffffffu, rend[r], 0);
-        }
-        if (vm) {
-            const int L = 31 - __clz(vm);
-            best = base + L;
-#pragma unroll
-            for (int r = 0; r < 9; ++r) best_end[r] = __shfl_sync(0xffffffffu, rend[r], L);
-        }
+        if (base == x0 + 1) first_fits = __shfl_sync(0xffffffffu, fits, 0);
+        if (vm) best = base + 31 - __clz(vm);
         if (vm != 0xffffffffu) break;
     }
     int x1 = best, mode = 0;
     if (best == 0) {
         x1 = x0 + 1;
         mode = first_fits ? 0 : 1;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) best_end[r] = first_end[r];
     }
+    const int xb = min(x1, nx - 1);
     // lane r < 9 owns row r
     uint32_t gb = 0, len = 0;
-#pragma unroll
-    for (int r = 0; r < 9; ++r)
-        if ((int)lane == r) {
-            gb = rstart[r];
-            len = best_end[r] - rstart[r];
+    if (lane < 9) {
+        const int by = cy + (int)lane % 3 - 1, bz = cz + (int)lane / 3 - 1;
+        if (by >= 0 && by < ny && bz >= 0 && bz < nz) {
+            const uint32_t rb = cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
+            gb = a.offsets[rb + xa];
+            len = a.offsets[rb + xb + 1] - gb;
         }
+    }
     uint32_t incl = len;
 #pragma unroll
     for (int o = 1; o < 16; o <<= 1) {
@@ -364,7 +371,7 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
     if (lane == 8) p.total = (int)incl;
     if (lane == 0) {
         p.xa = xa;
-        p.xb = min(x1, nx - 1);
+        p.xb = xb;
         p.x1 = x1;
         p.mode = mode;
     }
@@ -409,41 +416,6 @@ __device__ __forceinline__ float row_halfwidth(const SysDesc& d, const Faces& f,
     return tt * rsqrtf(tt) + d.slack;
 }
 
-// Global-memory path (mode 1) for one target: per row, binary search of the
-// window start inside the cell of x - w, scan until x > x + w.
-template <class Acc, int KERNEL>
-__device__ __forceinline__ void target_sums_global(const InteractArgs& a, const Smem& sm, float xt,
-                                                   float yt, float zt, uint32_t slot, int cy, int cz,
-                                                   const KParams& kp, Sums<Acc, KERNEL>& r)
-{
-    const Plan& p = sm.plan;
-    const SysDesc& d = sm.d;
-    const Faces f = faces_of(d, yt, zt, cy, cz);
-#pragma unroll 1
-    for (int rr = 0; rr < 9; ++rr) {
-        const int len = p.rlen[rr];
-        if (len == 0) continue;
-        const float w = row_halfwidth(d, f, rr);
-        if (w < 0.f) continue;
-        const float xlo = xt - w, xhi = xt + w;
-        int k = axis_cell(xlo, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa;
-        k = min(max(k, 0), p.xb - p.xa);
-        const float4* row = a.P + p.gbeg[rr];
-        int lo = (int)sm.tbl.cs[rr][k], hi = (int)sm.tbl.cs[rr][k + 1];
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (row[mid].x < xlo) lo = mid + 1;
-            else hi = mid;
-        }
-        for (int j = lo; j < len; ++j) {
-            const float4 q = row[j];
-            if (q.x > xhi) break;
-            if (self_by_identity<KERNEL>() && __float_as_uint(q.w) == slot) continue;
-            r.pair(__fsub_rn(q.x, xt), __fsub_rn(q.y, yt), __fsub_rn(q.z, zt), d.rc2, kp);
-        }
-    }
-}
-
 // Two Gaussian candidates at once with packed FP32 (f32x2) arithmetic:
 // every element is rounded exactly as the scalar operation would be, so the
 // pair test and the sums are those of Sums::pair_nb.
@@ -451,15 +423,16 @@ struct PackedSums {
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
 
+    // second = false drops the second candidate (an odd tail reuses the first)
     __device__ __forceinline__ void pair2(float2 px, float2 py, float2 pz, float2 mx, float2 my,
-                                          float2 mz, float rc2, float2 ks)
+                                          float2 mz, float rc2, float2 ks, bool second = true)
     {
         const float2 dx = __fadd2_rn(px, mx);
         const float2 dy = __fadd2_rn(py, my);
         const float2 dz = __fadd2_rn(pz, mz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const float2 t = __fmul2_rn(r2, ks);
-        const bool i0 = r2.x < rc2, i1 = r2.y < rc2;
+        const bool i0 = r2.x < rc2, i1 = (r2.y < rc2) && second;
         const float e0 = ex2_approx(t.x), e1 = ex2_approx(t.y);
         const float2 K = make_float2(i0 ? e0 : 0.f, i1 ? e1 : 0.f);
         s = __fadd2_rn(s, K);
@@ -470,24 +443,101 @@ struct PackedSums {
     }
 };
 
+// The candidates [j, je) of one row window, in order.  The Gaussian FP32
+// path takes them two at a time (packed, even and odd partial sums); the
+// others one at a time.  Shared by the staged and the global-memory paths so
+// that both sum every target's terms in the same order.
+template <class Acc, int KERNEL>
+__device__ __forceinline__ void window_sums(const float4* src, int j, int je, float xt, float yt,
+                                            float zt, uint32_t slot, float rc2, const KParams& kp,
+                                            PackedSums& ps, Sums<Acc, KERNEL>& r)
+{
+    constexpr bool packed = std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
+    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
+    if constexpr (packed) {
+        const float2 mx = make_float2(-xt, -xt), my = make_float2(-yt, -yt), mz = make_float2(-zt, -zt),
+                     ks = make_float2(kp.t, kp.t);
+        for (; j < je; j += 2) {
+            const bool two = j + 1 < je;
+            const float4 s0 = src[j], s1 = src[two ? j + 1 : j];
+            ps.pair2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z), mx, my,
+                     mz, rc2, ks, two);
+        }
+    } else {
+        for (; j < je; ++j) {
+            const float4 s0 = src[j];
+            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), rc2, kp,
+                      by_id && __float_as_uint(s0.w) == slot);
+        }
+    }
+}
+
+template <class Acc, int KERNEL>
+__device__ __forceinline__ void finish_packed(const PackedSums& ps, Sums<Acc, KERNEL>& r)
+{
+    if constexpr (std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN) {
+        r.s.add(ps.s.x + ps.s.y);
+        r.vx.add(ps.vx.x + ps.vx.y);
+        r.vy.add(ps.vy.x + ps.vy.y);
+        r.vz.add(ps.vz.x + ps.vz.y);
+        r.n += (uint32_t)(ps.n.x + ps.n.y);
+    }
+}
+
+// Global-memory path (mode 1) for one target: per row, the window
+// [first x >= x - w, first x > x + w) by binary search inside the cells of
+// x - w and x + w, summed exactly as the staged path does.
+template <class Acc, int KERNEL, class SM>
+__device__ __forceinline__ void target_sums_global(const InteractArgs& a, const SM& sm, float xt,
+                                                   float yt, float zt, uint32_t slot, int cy, int cz,
+                                                   const KParams& kp, Sums<Acc, KERNEL>& r)
+{
+    const Plan& p = sm.plan;
+    const SysDesc& d = sm.d;
+    const Faces f = faces_of(d, yt, zt, cy, cz);
+    PackedSums ps;
+#pragma unroll 1
+    for (int rr = 0; rr < 9; ++rr) {
+        const int len = p.rlen[rr];
+        if (len == 0) continue;
+        const float w = row_halfwidth(d, f, rr);
+        if (w < 0.f) continue;
+        const float xlo = xt - w, xhi = xt + w;
+        const int kmax = p.xb - p.xa;
+        const int k0 = min(max(axis_cell(xlo, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa, 0), kmax);
+        const int k1 = min(max(axis_cell(xhi, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa, 0), kmax);
+        const float4* row = a.P + p.gbeg[rr];
+        int lo = (int)sm.tbl.cs[rr][k0], hi = (int)sm.tbl.cs[rr][k0 + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (row[mid].x < xlo) lo = mid + 1;
+            else hi = mid;
+        }
+        int e0 = max((int)sm.tbl.cs[rr][k1], lo), e1 = (int)sm.tbl.cs[rr][k1 + 1];
+        while (e0 < e1) {
+            const int mid = (e0 + e1) >> 1;
+            if (row[mid].x > xhi) e1 = mid;
+            else e0 = mid + 1;
+        }
+        window_sums<Acc, KERNEL>(row, lo, e0, xt, yt, zt, slot, d.rc2, kp, ps, r);
+    }
+    finish_packed(ps, r);
+}
+
 // Sums of one target over the staged rows (mode 0).  Per row: the x-window
 // from the row's lookup table, trimmed to [x - w, x + w] exactly; every
 // source in it is a candidate, taken two at a time.
-template <class Acc, int KERNEL>
-__device__ __forceinline__ void target_sums_staged(const Smem& sm, float xt, float yt, float zt,
+template <class Acc, int KERNEL, class SM>
+__device__ __forceinline__ void target_sums_staged(const SM& sm, float xt, float yt, float zt,
                                                    uint32_t slot, int cy, int cz, int ncell,
                                                    float inv4, const KParams& kp,
                                                    Sums<Acc, KERNEL>& r)
 {
-    constexpr bool by_id = self_by_identity<KERNEL>();
     const Plan& p = sm.plan;
     const SysDesc& d = sm.d;
     const Faces f = faces_of(d, yt, zt, cy, cz);
     const int nb = ncell * BPC, base = BPC * p.xa;
-    constexpr bool packed = std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
     PackedSums ps;
-    const float2 mx = make_float2(-xt, -xt), my = make_float2(-yt, -yt), mz = make_float2(-zt, -zt),
-                 ks = make_float2(kp.t, kp.t);
 #pragma unroll 1
     for (int rr = 0; rr < 9; ++rr) {
         if (p.rlen[rr] == 0) continue;
@@ -501,40 +551,16 @@ __device__ __forceinline__ void target_sums_staged(const Smem& sm, float xt, flo
         while (j < je && sm.buf[j].x < xlo) ++j;
         while (je > j && sm.buf[je - 1].x > xhi) --je;
         // window [j, je): every source in it is a candidate
-        if (packed) {
-            for (; j + 1 < je; j += 2) {
-                const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
-                ps.pair2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z), mx,
-                         my, mz, d.rc2, ks);
-            }
-        } else {
-            for (; j + 1 < je; j += 2) {
-                const float4 s0 = sm.buf[j], s1 = sm.buf[j + 1];
-                r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), d.rc2, kp,
-                          by_id && __float_as_uint(s0.w) == slot);
-                r.pair_nb(__fsub_rn(s1.x, xt), __fsub_rn(s1.y, yt), __fsub_rn(s1.z, zt), d.rc2, kp,
-                          by_id && __float_as_uint(s1.w) == slot);
-            }
-        }
-        if (j < je) {
-            const float4 s0 = sm.buf[j];
-            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), d.rc2, kp,
-                      by_id && __float_as_uint(s0.w) == slot);
-        }
+        window_sums<Acc, KERNEL>(sm.buf, j, je, xt, yt, zt, slot, d.rc2, kp, ps, r);
     }
-    if (packed) {
-        r.s.add(ps.s.x + ps.s.y);
-        r.vx.add(ps.vx.x + ps.vx.y);
-        r.vy.add(ps.vy.x + ps.vy.y);
-        r.vz.add(ps.vz.x + ps.vz.y);
-        r.n += (uint32_t)(ps.n.x + ps.n.y);
-    }
+    finish_packed(ps, r);
 }
 
-template <class Acc, int KERNEL>
-__global__ void __launch_bounds__(TT, 7) k_interact_tiled(InteractArgs a)
+template <class T, class Acc, int KERNEL>
+__global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs a)
 {
-    __shared__ Smem sm;
+    constexpr int TT = T::TT, CAP = T::CAP;
+    __shared__ Smem<CAP> sm;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
@@ -554,13 +580,17 @@ __global__ void __launch_bounds__(TT, 7) k_interact_tiled(InteractArgs a)
 
     for (;;) {
         if (tid == 0) {
-            const uint32_t grow = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
-            sm.has_row = grow < a.rows;
-            if (grow < a.rows) {
-                const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.rbase, a.sy.S, grow);
+            const uint32_t item = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
+            sm.has_row = item < a.work;
+            if (item < a.work) {
+                const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.wbase, a.sy.S, item);
                 sm.d = a.sy.sys[sid];
                 sm.t = a.kscale ? a.kscale[sid] : a.kscale0;
-                sm.row = grow - sm.d.row_base;
+                const uint32_t local = item - sm.d.work_base;
+                const uint32_t seg = local % sm.d.nseg;
+                sm.row = local / sm.d.nseg;
+                sm.xs = (int)seg * SEG_CELLS;
+                sm.xe = min(sm.d.g.n[0], (int)(seg + 1) * SEG_CELLS);
             }
         }
         __syncthreads();
@@ -575,15 +605,16 @@ __global__ void __launch_bounds__(TT, 7) k_interact_tiled(InteractArgs a)
         float kself = k0_scale_free;
         uint32_t nself = 1u;
         if constexpr (KERNEL == KERNEL_LOWFLOP) kself = 1.0f;
-        if constexpr (self_by_identity<KERNEL>()) {
+        if constexpr (self_by_identity<KERNEL, Acc>()) {
             kself = 0.f;
             nself = 0u;
         }
 
-        for (int x0 = 0; x0 < nx;) {
+        const int xe = sm.xe;
+        for (int x0 = sm.xs; x0 < xe;) {
             if (warp == 0) {
                 if (lane < 9) sm.coarse[lane] = 0;
-                plan_chunk(a, d, sm.plan, x0, cy, cz, lane);
+                plan_chunk<TT, CAP>(a, d, sm.plan, x0, xe, cy, cz, lane);
                 __syncwarp();
                 if (lane == 0 && sm.plan.mode == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -673,15 +704,35 @@ cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
 }
 
 template <class Acc>
-cudaError_t launch_tiled_acc(const InteractArgs& a, unsigned grid, cudaStream_t s)
+cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
+                             cudaStream_t s)
 {
+    // the other kernels are comparators: they run with the middle tile shape
+    if (a.kernel != KERNEL_GAUSSIAN) tile = 1;
+    const int TTs[3] = {Tile64::TT, Tile128::TT, Tile256::TT};
+    uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
+    if (grid > a.work) grid = a.work;
+    if (grid < 1) grid = 1;
+    const unsigned g = (unsigned)grid;
+    const int tt = TTs[tile];
     switch (a.kernel) {
-        case KERNEL_LJ: k_interact_tiled<Acc, KERNEL_LJ><<<grid, TT, 0, s>>>(a); break;
-        case KERNEL_LOWFLOP: k_interact_tiled<Acc, KERNEL_LOWFLOP><<<grid, TT, 0, s>>>(a); break;
-        case KERNEL_HIGHFLOP: k_interact_tiled<Acc, KERNEL_HIGHFLOP><<<grid, TT, 0, s>>>(a); break;
-        default: k_interact_tiled<Acc, KERNEL_GAUSSIAN><<<grid, TT, 0, s>>>(a); break;
+        case KERNEL_LJ: k_interact_tiled<Tile128, Acc, KERNEL_LJ><<<g, tt, 0, s>>>(a); break;
+        case KERNEL_LOWFLOP: k_interact_tiled<Tile128, Acc, KERNEL_LOWFLOP><<<g, tt, 0, s>>>(a); break;
+        case KERNEL_HIGHFLOP: k_interact_tiled<Tile128, Acc, KERNEL_HIGHFLOP><<<g, tt, 0, s>>>(a); break;
+        default:
+            if (tile == 0) k_interact_tiled<Tile64, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
+            else if (tile == 2) k_interact_tiled<Tile256, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
+            else k_interact_tiled<Tile128, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
+            break;
     }
     return cudaGetLastError();
+}
+
+template <class T, class Acc>
+cudaError_t occupancy_of(int* per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_interact_tiled<T, Acc, KERNEL_GAUSSIAN>,
+                                                         T::TT, 0);
 }
 
 }  // namespace
@@ -696,23 +747,23 @@ cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms,
 
 cudaError_t tiled_occupancy(bool kahan, int* per_sm)
 {
-    // every kernel variant has the same shared memory; the Gaussian one
-    // stands for the register count
-    return kahan ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       per_sm, k_interact_tiled<KahanAcc, KERNEL_GAUSSIAN>, TT, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       per_sm, k_interact_tiled<PlainAcc, KERNEL_GAUSSIAN>, TT, 0);
+    cudaError_t e;
+    if (kahan) {
+        if ((e = occupancy_of<Tile64, KahanAcc>(&per_sm[0])) != cudaSuccess) return e;
+        if ((e = occupancy_of<Tile128, KahanAcc>(&per_sm[1])) != cudaSuccess) return e;
+        return occupancy_of<Tile256, KahanAcc>(&per_sm[2]);
+    }
+    if ((e = occupancy_of<Tile64, PlainAcc>(&per_sm[0])) != cudaSuccess) return e;
+    if ((e = occupancy_of<Tile128, PlainAcc>(&per_sm[1])) != cudaSuccess) return e;
+    return occupancy_of<Tile256, PlainAcc>(&per_sm[2]);
 }
 
-cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, int per_sm,
-                                  cudaStream_t s, int* launches)
+cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
+                                  int tile, cudaStream_t s, int* launches)
 {
-    uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm < 1 ? 1 : per_sm);
-    if (grid > a.rows) grid = a.rows;
-    if (grid < 1) grid = 1;
     *launches += 1;
-    return kahan ? launch_tiled_acc<KahanAcc>(a, (unsigned)grid, s)
-                 : launch_tiled_acc<PlainAcc>(a, (unsigned)grid, s);
+    return kahan ? launch_tiled_acc<KahanAcc>(a, tile, per_sm, num_sms, s)
+                 : launch_tiled_acc<PlainAcc>(a, tile, per_sm, num_sms, s);
 }
 
 }  // namespace pi

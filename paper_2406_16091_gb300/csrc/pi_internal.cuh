@@ -13,7 +13,7 @@
 //   pbase[S+1]      first particle of each system in the current step
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
-//   sys[S], cbase[S+1], rbase[S+1], kscale[S]   per-system constants
+//   sys[S], cbase[S+1], wbase[S+1], kscale[S]   per-system constants
 //   cell[n_max]     cell of each input particle            (binning scratch)
 //   rank[n_max]     provisional slot inside its cell        (binning scratch)
 //   perm_u[n_max]   unstable slot -> input index            (binning scratch)
@@ -41,7 +41,7 @@ struct Ctrl {
     uint32_t error;         // ERR_* bits, sticky until the next pi_bin
     uint32_t max_per_cell;  // M_C of the last pi_bin (over all systems)
     uint32_t n;             // particle count of the last pi_bin
-    uint32_t work[2];       // next X-row handed out by the tiled interaction;
+    uint32_t work[2];       // next work item handed out by the tiled interaction;
                             // launch number q uses work[q & 1] and clears the other
     uint32_t pad[58];       // the control block is 256 bytes
 };
@@ -61,8 +61,14 @@ struct SysDesc {
     float rc2;        // fl32(r_c * r_c)
     float slack;      // absolute margin of the conservative x-windows
     uint32_t cell_base;
-    uint32_t row_base;
+    uint32_t work_base;  // first work item of the tiled interaction
+    uint32_t nseg;       // work items per X-row: segments of SEG_CELLS cells
 };
+
+// The tiled interaction's work items are segments of SEG_CELLS consecutive
+// cells of an X-row; rows longer than that are split so that heavy rows do
+// not leave one CTA working alone at the end.
+constexpr int SEG_CELLS = 32;
 
 constexpr int MAX_SYSTEMS = 2048;
 
@@ -71,7 +77,7 @@ struct Systems {
     const SysDesc* sys;     // [S]
     const uint32_t* pbase;  // [S+1] first particle (= first sorted slot) of each system
     const uint32_t* cbase;  // [S+1] first cell
-    const uint32_t* rbase;  // [S+1] first X-row
+    const uint32_t* wbase;  // [S+1] first work item of the tiled interaction
     int S;
 };
 
@@ -154,6 +160,17 @@ cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32
                              float* sy_out, float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl,
                              int num_sms, cudaStream_t s);
 
+// FP64 total of v over the particles of each system (out[S], device), in a
+// fixed order: `parts` partial sums per system in `partial` [S * parts].
+constexpr int TOTAL_PARTS = 32;
+cudaError_t launch_total_f64(const float* v, const Systems& sy, double* partial, int parts,
+                             double* out, cudaStream_t s);
+
+// Writes one system's constants (system 0 of a context) from launch
+// parameters: sys[0] = d, cbase[1] = cells, wbase[1] = work items.
+cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, const SysDesc& d,
+                              uint32_t cells, uint32_t work, cudaStream_t s);
+
 // Per-system scale of the interaction kernel, written from launch parameters
 // (vals[s] for s < S) into kscale.
 cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s);
@@ -171,7 +188,7 @@ struct InteractArgs {
     const uint32_t* offsets;
     const uint32_t* perm;
     uint32_t n;             // particles of all systems
-    uint32_t rows;          // X-rows of all systems
+    uint32_t work;          // work items (X-row segments) of all systems
     const float* kscale;    // [S]: Gaussian K = 2^(r2 * kscale[s]); Lennard-Jones sigma^2
     float kscale0;          // the scale when S == 1 (kscale may then be null)
     int kernel;             // KERNEL_*
@@ -190,9 +207,11 @@ struct InteractArgs {
 // Each adds the number of kernels it launched to *launches.
 cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
                                  int* launches);
-cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, int per_sm,
-                                  cudaStream_t s, int* launches);
-// Resident CTAs per SM of the tiled kernel (queried once per context).
+// tile: 0, 1, 2 = 64, 128, 256 targets per chunk; per_sm[tile] = resident CTAs.
+constexpr int NUM_TILES = 3;
+cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
+                                  int tile, cudaStream_t s, int* launches);
+// Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[3]).
 cudaError_t tiled_occupancy(bool kahan, int* per_sm);
 
 }  // namespace pi

@@ -131,3 +131,50 @@ def scaled(w: Workload, n: int, seed: int | None = None) -> Workload:
     cells per axis are scaled by (n / w.n)^(1/3) (at least 1)."""
     cells = max(1, int(round(w.cells_per_axis() * (n / w.n) ** (1.0 / 3.0))))
     return _wl(f"{w.name}@{n}", n, cells, w.seed if seed is None else seed, w.layout)
+
+
+@dataclass
+class System:
+    """One independent system of a batch or one serving job."""
+    n: int
+    rc: float
+    h: float
+    seed: int
+    layout: str = "uniform"
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+
+    def positions(self):
+        if self.layout == "clustered":
+            return clustered(self.n, self.seed)
+        return uniform(self.n, self.seed, self.lo, self.hi)
+
+
+def _system_for(n: int, ppc: float, seed: int, layout: str = "uniform") -> System:
+    cells = max(3, int(round((n / ppc) ** (1.0 / 3.0))))
+    rc = rc_for_cells(cells)
+    return System(n=n, rc=rc, h=float(np.float32(rc) / np.float32(2.0)), seed=seed, layout=layout)
+
+
+def batched_systems(count: int = 256, seed: int = 1004, n_lo: int = 1024, n_hi: int = 262144,
+                    ppc_lo: float = 2.0, ppc_hi: float = 16.0):
+    """The batched workload: ``count`` independent systems, N log-uniform in
+    [n_lo, n_hi], each uniform in its own unit box with a mean occupancy
+    drawn uniformly in [ppc_lo, ppc_hi] (cells per axis max(3,
+    round(cbrt(N / ppc)))), h = r_c / 2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
+    ppc = rng.uniform(ppc_lo, ppc_hi, count)
+    return [_system_for(int(ns[k]), float(ppc[k]), seed * 1000 + k) for k in range(count)]
+
+
+def serving_jobs(count: int = 10000, seed: int = 1005, n_lo: int = 1024, n_hi: int = 1048576):
+    """The serving workload: ``count`` jobs with N log-uniform in [n_lo, n_hi],
+    mean occupancy in {2, 4, 8, 16}, half uniform and half clustered.  Arrival
+    times are drawn by the caller (Poisson at a chosen rate)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
+    ppc = rng.choice([2.0, 4.0, 8.0, 16.0], count)
+    layout = rng.choice(["uniform", "clustered"], count)
+    return [_system_for(int(ns[k]), float(ppc[k]), seed * 100000 + k, str(layout[k]))
+            for k in range(count)]
