@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--flush-mb", type=int, default=512)
+    p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
+                   help="tile shape of the tiled interaction (auto: pi_autotune during warm-up)")
     p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=400, help="serving study: number of jobs")
@@ -259,6 +261,13 @@ def run_ours(args):
         B.pi_bin(ctx, tx, ty, tz, n, s)
         B.pi_interact(ctx, w.h, S, Vx, Vy, Vz, nb, B.PI_ORDER_SORTED, s)
 
+    tile_ms = None
+    if args.tile == "auto":
+        step()
+        tile, tile_ms = B.pi_autotune(ctx, [w.h], S, Vx, Vy, Vz, nb, B.PI_ORDER_SORTED, 5, s)
+    else:
+        tile = int(args.tile)
+        B.pi_set_option(ctx, B.PI_OPT_TILE, tile)
     for _ in range(max(3, args.warmup)):
         step()
     st, mpc = B.pi_sync_status(ctx, s)
@@ -400,6 +409,7 @@ def run_ours(args):
         "pairs_per_step": pairs, "max_per_cell": mpc2,
         "interact_pairs_per_s": pairs / mean_int, "bin_us": 1e6 * mean_bin,
         "interact_us": 1e6 * mean_int,
+        "tile": tile, "tile_ms": tile_ms,
         "roofline": roofline, "roofline_binning": binning, "peak_source": peak_kind,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "timed_region_wall_s": wall,

@@ -85,9 +85,12 @@ enum {
     PI_OPT_TEST_WITHHOLD_SCAN = 4,
     /* Interaction kernel K (PI_KERNEL_*), default PI_KERNEL_GAUSSIAN. */
     PI_OPT_KERNEL = 5,
-    /* Tile shape of the tiled interaction: 0, 1, 2 for 64, 128, 256 targets
-     * (threads) per chunk with 640, 1280, 2560 staged particles; default 1.
-     * pi_autotune sets it from measurements.  Results do not depend on it. */
+    /* Tile shape of the tiled interaction: 0, 1, 2, 3 for 32, 64, 128, 256
+     * targets (threads) per chunk with 512, 576, 1280, 2432 staged
+     * particles; 4, 5 for the warp-specialised form (one producer warp
+     * stages chunks of up to 1152 particles into 2 or 3 buffers for 4 or 8
+     * consumer warps).  Default 0.  pi_autotune sets it from measurements.
+     * Results do not depend on it. */
     PI_OPT_TILE = 6
 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
@@ -209,7 +212,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
  * pi_batch_interact, h one entry per system) once untimed and `reps` times
  * timed (1 <= reps <= 100) for each shape, keeps the shape with the
  * smallest median time for later calls, and returns it in *chosen and the
- * medians in ms[3] (milliseconds; either pointer may be NULL).  The shape
+ * medians in ms[6] (milliseconds; either pointer may be NULL).  The shape
  * changes only the speed: the outputs are the same for every shape (each
  * target's terms are summed in the same order).  Synchronises `stream`.  The
  * output arrays hold the last run's results.

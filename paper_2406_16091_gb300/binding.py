@@ -32,6 +32,7 @@ PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
+PI_NUM_TILES = 6  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1
 PI_KERNEL_LOWFLOP = 2
@@ -246,7 +247,7 @@ def pi_autotune(ctx, h, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTE
     Returns (chosen shape, [median ms per shape])."""
     arr = (ctypes.c_float * len(h))(*[float(v) for v in h])
     chosen = ctypes.c_int32()
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * PI_NUM_TILES)()
     _check(load().pi_autotune(ctx, ctypes.cast(arr, ctypes.c_void_p), _ptr(S), _ptr(Vx), _ptr(Vy),
                               _ptr(Vz), _ptr(nbr), int(out_order), int(reps), ctypes.byref(chosen),
                               ctypes.cast(ms, ctypes.c_void_p), _stream(stream)), "pi_autotune")

@@ -40,7 +40,7 @@ struct pi_ctx {
     void* arena;
     Ctrl* ctrl;
     uint32_t* counts;
-    uint32_t* xbins;
+    uint2* xbins;
     uint32_t* pbase;
     uint32_t* offsets;
     unsigned long long* scan_status;
@@ -80,7 +80,7 @@ struct pi_ctx {
     int algo;
     int precision;
     int kernel;
-    int tile;                       // tile shape of the tiled kernel (0..2)
+    int tile;                       // tile shape of the tiled kernel (0 .. NUM_TILES - 1)
     uint64_t wait_limit_ns;
     int withhold_scan;
 };
@@ -259,7 +259,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->algo = PI_ALGO_TILED;
     c->precision = PI_PREC_FP32;
     c->kernel = PI_KERNEL_GAUSSIAN;
-    c->tile = 1;
+    c->tile = pi::DEFAULT_TILE;
     c->wait_limit_ns = 1000000000ull;
 
     cudaError_t e = cudaGetDevice(&c->device);
@@ -277,7 +277,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     Carver k;
     const size_t o_ctrl = k.take<Ctrl>(1);
     const size_t o_counts = k.take<uint32_t>((size_t)C + 4);
-    const size_t o_xbins = k.take<uint32_t>((size_t)C + 4);  // ctrl .. xbins: cleared by every pi_bin
+    const size_t o_xbins = k.take<uint2>((size_t)C + 4);  // ctrl .. xbins: cleared by every pi_bin
     const size_t o_pbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_offsets = k.take<uint32_t>((size_t)C + 1 + 16);
     const size_t o_status = k.take<unsigned long long>(tiles);
@@ -306,7 +306,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     char* base = (char*)c->arena;
     c->ctrl = (Ctrl*)(base + o_ctrl);
     c->counts = (uint32_t*)(base + o_counts);
-    c->xbins = (uint32_t*)(base + o_xbins);
+    c->xbins = (uint2*)(base + o_xbins);
     c->pbase = (uint32_t*)(base + o_pbase);
     c->offsets = (uint32_t*)(base + o_offsets);
     c->scan_status = (unsigned long long*)(base + o_status);

@@ -313,17 +313,17 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //     P[s0 + x-rank] = (x, y, z, stable slot).  The cells of an X-row are
 //     contiguous and monotone in x, so every X-row of P is sorted by x as a
 //     whole -- the tiled interaction stages such rows;
-//   - (the member of x-rank 0 only) xbins[c]: bytes 0..2 = members whose
-//     x-sub-bin is < 1, < 2, < 3, sub-bin = floor(4 (x - lo) inv_w) - 4 cx
-//     clamped to [0, 3] (monotone in x); byte 3 = 1 when the cell has more
-//     than 255 members, bytes 0..2 then 0 (every sub-bin starts at the cell).
+//   - (the member of x-rank 0 only) xbins[c]: byte b - 1 (b = 1 .. XSUB - 1)
+//     = members whose x-sub-bin is < b (see XSUB); byte 7 = 1 when the cell
+//     has more than 255 members, bytes 0..6 then 0 (every sub-bin starts at
+//     the cell).
 __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ perm_u,
                                                    const float4* __restrict__ pos_u, uint32_t n,
                                                    Systems sy, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
                                                    float* __restrict__ sx, float* __restrict__ sy_out,
                                                    float* __restrict__ sz, float4* __restrict__ P,
-                                                   uint32_t* __restrict__ xbins,
+                                                   uint2* __restrict__ xbins,
                                                    Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
@@ -338,19 +338,18 @@ __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ 
         if (k < s0 || k >= s1) { bad = true; continue; }
         const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
         const Grid& g = sy.sys[sid].g;
-        const float inv4 = g.inv_w[0] * 4.0f;
-        const int cx4 = 4 * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
-        uint32_t r = 0, xr = 0, b1 = 0, b2 = 0, b3 = 0;
+        const float invs = g.inv_w[0] * (float)XSUB;
+        const int cxs = XSUB * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
+        uint32_t r = 0, xr = 0, lt[XSUB - 1] = {};
         for (uint32_t q = s0; q < s1; ++q) {
             const uint32_t j = perm_u[q];
             const float xq = pos_u[q].x;
             r += (j < i) ? 1u : 0u;
             xr += (xq < pk.x || (xq == pk.x && j < i)) ? 1u : 0u;
             const int sb =
-                min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), inv4)) - cx4, 0), 3);
-            b1 += sb < 1 ? 1u : 0u;
-            b2 += sb < 2 ? 1u : 0u;
-            b3 += sb < 3 ? 1u : 0u;
+                min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
+#pragma unroll
+            for (int b = 1; b < XSUB; ++b) lt[b - 1] += sb < b ? 1u : 0u;
         }
         const uint32_t dst = s0 + r;
         perm[dst] = i;
@@ -358,7 +357,13 @@ __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ 
         sy_out[dst] = pk.y;
         sz[dst] = pk.z;
         P[s0 + xr] = make_float4(pk.x, pk.y, pk.z, __uint_as_float(dst));
-        if (xr == 0) xbins[c] = (s1 - s0 > 255u) ? (1u << 24) : (b1 | (b2 << 8) | (b3 << 16));
+        if (xr == 0) {
+            static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
+            xbins[c] = (s1 - s0 > 255u)
+                           ? make_uint2(0u, 1u << 24)
+                           : make_uint2(lt[0] | (lt[1] << 8) | (lt[2] << 16) | (lt[3] << 24),
+                                        lt[4] | (lt[5] << 8) | (lt[6] << 16));
+        }
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
@@ -429,7 +434,7 @@ cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const flo
 
 cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
                              const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
-                             float* sy_out, float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl,
+                             float* sy_out, float* sz, float4* P, uint2* xbins, Ctrl* ctrl,
                              int num_sms, cudaStream_t s)
 {
     k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, pos_u, n, sy, offsets, perm, sx,

@@ -193,22 +193,29 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 
 // ---- tiled interaction ----------------------------------------------------------
 
-// Tile shapes: threads per CTA (= targets per chunk) and staged particles per
-// chunk.  The autotuner (pi_autotune) picks one per context; every shape
-// gives the same per-target summation order, so the results are identical.
-template <int TT_, int CAP_, int MINB_>
+// Tile shapes: threads per CTA (= targets per chunk), staged particles per
+// chunk, CTAs per SM the register and shared-memory budget is sized for, and
+// target cells per chunk along X.  The autotuner (pi_autotune) picks one per
+// context; every shape gives the same per-target summation order, so the
+// results are identical.
+template <int TT_, int CAP_, int MINB_, int MAXLX_>
 struct Tile {
     static constexpr int TT = TT_;
     static constexpr int CAP = CAP_;
-    static constexpr int MINB = MINB_;  // CTAs per SM the register budget is sized for
+    static constexpr int MINB = MINB_;
+    static constexpr int MAXLX = MAXLX_;
+    // lookup-table entries per row: XSUB per source cell plus the row end,
+    // rounded up so that every row starts 16-byte aligned
+    static constexpr int RB = ((MAXLX + 2) * XSUB + 1 + 7) / 8 * 8;
 };
-using Tile64 = Tile<64, 640, 16>;
-using Tile128 = Tile<128, 1280, 8>;
-using Tile256 = Tile<256, 2560, 4>;
+using Tile32 = Tile<32, 512, 16, 16>;
+using Tile64 = Tile<64, 576, 14, 16>;
+using Tile128 = Tile<128, 1280, 7, SEG_CELLS>;
+using Tile256 = Tile<256, 2432, 4, SEG_CELLS>;
 
-constexpr int MAXLX = 64;                   // target cells per chunk along X
-constexpr int BPC = 4;                      // x-bins per cell in the staged-row lookup
-constexpr int RBINS = (MAXLX + 2) * BPC + 2;
+// Lookup-table entries per row of a chunk read from global memory (mode 1:
+// one target cell, so at most 3 source cells).
+constexpr int RB_GLOBAL = 3 * XSUB + 1;
 
 // One chunk: target cells [x0, x1) of an X-row, source cells [xa, xb] of the
 // 9 neighbour rows (row r has dy = r % 3 - 1, dz = r / 3 - 1).  Row r holds
@@ -224,25 +231,42 @@ struct Plan {
     int total;  // staged particles
 };
 
-template <int CAP>
+template <class T>
 struct Smem {
-    float4 buf[CAP + 1];  // staged rows; one spare slot keeps a read one past the end inside
+    // Staged rows.  buf[CAP] is a sentinel far from every particle: an odd
+    // tail pairs its last candidate with it, and the pair test rejects it.
+    float4 buf[T::CAP + 1];
+    // Per row r and sub-bin b of the chunk's source cells (b = XSUB * cell +
+    // sub-bin, counted from cell xa): index of the first particle of row r
+    // whose sub-bin is >= b; entry XSUB * ncell is the row end.  Staged
+    // indices in mode 0, indices into P in mode 1.
     union {
-        // mode 0: per row, first staged index (absolute) whose x-bin is >= b
-        uint16_t bin[9][RBINS];
-        // mode 1: per row, start of each cell relative to the row
-        uint32_t cs[9][MAXLX + 4];
+        __align__(16) uint16_t staged[9][T::RB];
+        uint32_t global[9][RB_GLOBAL];
     } tbl;
+    // Per target (thread): its non-empty x-windows as byte offsets into buf,
+    // first | end << 16, plus one spare row read after the last window.
+    uint32_t win[10][T::TT];
     Plan plan;
-    SysDesc d;      // the system of the current X-row
-    float t;        // its kernel scale
-    int coarse[9];  // row holds a cell without sub-bin starts: end lookups use cell bounds
-    uint32_t row;   // current X-row, local to its system
-    int xs, xe;     // its cells [xs, xe) handled by this work item
+    SysDesc d;             // the system of the current X-row
+    float t;               // its kernel scale
+    uint32_t coarse_mask;  // bit r: row r holds a cell without sub-bin starts
+    uint32_t row;          // current X-row, local to its system
+    int xs, xe;            // its cells [xs, xe) handled by this work item
     int has_row;
     int failed;
     uint64_t bar;
 };
+
+// MINB CTAs of a shape fit the SM's 228 KB of shared memory (1 KB of which
+// each CTA reserves).
+template <class T>
+constexpr bool fits_sm()
+{
+    return T::MINB * (sizeof(Smem<T>) + 1024) <= 228u * 1024u;
+}
+static_assert(fits_sm<Tile32>() && fits_sm<Tile64>() && fits_sm<Tile128>() && fits_sm<Tile256>(),
+              "tile shapes exceed the shared memory of their CTAs per SM");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -298,7 +322,7 @@ __device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t phase, 
 // largest x1 such that the chunk has at most TT targets and its 9 source
 // rows hold at most CAP particles, plus each row's range.  A single cell
 // whose rows exceed CAP is read from global memory (mode 1).
-template <int TT, int CAP>
+template <class T>
 __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int x0, int xe, int cy,
                            int cz, unsigned lane)
 {
@@ -306,7 +330,7 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
     const uint32_t cb = d.cell_base;
     const uint32_t rb0 = cb + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
     const int xa = max(x0 - 1, 0);
-    const int xmax = min(xe, x0 + MAXLX);
+    const int xmax = min(xe, x0 + T::MAXLX);
     // first particle of each row's source range (the same for every lane)
     uint32_t rstart[9];
 #pragma unroll
@@ -333,8 +357,8 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
                 staged += a.offsets[cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xb + 1] -
                           rstart[r];
             }
-            fits = staged <= (uint32_t)CAP;
-            valid = fits && targets <= (uint32_t)TT;
+            fits = staged <= (uint32_t)T::CAP;
+            valid = fits && targets <= (uint32_t)T::TT;
         }
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
         if (base == x0 + 1) first_fits = __shfl_sync(0xffffffffu, fits, 0);
@@ -377,12 +401,47 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
     }
 }
 
-// x-bin used by the staged-row lookup: monotone in x (FP32 round-to-nearest
-// subtract and multiply, floor), relative to the first source cell xa.
-__device__ __forceinline__ int xbin(float x, float lo, float inv4, int base, int nb)
+// Lookup table of one chunk, built from the offsets and the per-cell
+// sub-bin starts (no staged data needed, so it overlaps the bulk copies).
+// Warps take rows, lanes take cells; rows without particles (or outside the
+// grid) get all-zero entries, i.e. empty windows.
+template <int NW, class E, int RB>
+__device__ __forceinline__ void build_table(const InteractArgs& a, const SysDesc& d, const Plan& p,
+                                            int cy, int cz, int ncell, E (*tbl)[RB],
+                                            uint32_t* coarse_mask, unsigned warp, unsigned lane)
 {
-    const int b = __float2int_rd(__fmul_rn(__fsub_rn(x, lo), inv4)) - base;
-    return min(max(b, 0), nb - 1);
+    const int nx = d.g.n[0], ny = d.g.n[1];
+    for (int rr = (int)warp; rr < 9; rr += NW) {
+        const int len = p.rlen[rr];
+        const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
+        const uint32_t rb = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + p.xa;
+        // mode 0: staged index = sbeg + (P index - gbeg); mode 1: P index
+        const uint32_t shift = sizeof(E) == 2 ? (uint32_t)p.sbeg[rr] - p.gbeg[rr] : 0u;
+        for (int k = (int)lane; k <= ncell; k += 32) {
+            E* e = &tbl[rr][XSUB * k];
+            if (len == 0) {
+                if (k == ncell) e[0] = 0;
+                else
+#pragma unroll
+                    for (int b = 0; b < XSUB; ++b) e[b] = 0;
+                continue;
+            }
+            const uint32_t start = a.offsets[rb + k] + shift;
+            if (k == ncell) {
+                e[0] = (E)start;
+                continue;
+            }
+            const uint2 w = a.xbins[rb + k];
+            if (w.y >> 24) atomicOr(coarse_mask, 1u << rr);
+            e[0] = (E)start;
+#pragma unroll
+            for (int b = 1; b < XSUB; ++b) {
+                const uint32_t word = b <= 4 ? w.x : w.y;
+                const uint32_t cnt = (word >> (8 * ((b - 1) & 3))) & 255u;
+                e[b] = (E)(start + cnt);
+            }
+        }
+    }
 }
 
 // Distances (minus slack, at least 0) from a target to the faces of its own
@@ -402,66 +461,143 @@ __device__ __forceinline__ Faces faces_of(const SysDesc& d, float yt, float zt, 
     return f;
 }
 
-// Half-width of the x-window of row rr, or a negative value if the row is
-// out of reach.  Conservative: rc^2 is inflated by 2e-5 and the slack added.
-__device__ __forceinline__ float row_halfwidth(const SysDesc& d, const Faces& f, int rr)
+// Sub-bin of x counted from the chunk's first source cell, clamped to
+// [lo, hi]: the FP32 expression of k_stabilise, so it is monotone in x and
+// agrees with the sub-bins the table was built from.
+__device__ __forceinline__ int sub_bin(float x, float xlo, float invs, int base, int lo, int hi)
 {
-    const int dy = rr % 3 - 1, dz = rr / 3 - 1;
-    const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
-    const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
+    const int b = __float2int_rd(__fmul_rn(__fsub_rn(x, xlo), invs)) - base;
+    return min(max(b, lo), hi);
+}
+
+// The 9 x-windows of one target: per row r, the sources whose sub-bin lies
+// between those of x - w_r and x + w_r, w_r = sqrt(rc^2 - d_yz^2) (inflated
+// by 2e-5 relative and the slack; negative d_yz^2 headroom = row out of
+// reach, empty window), and inside the target's cells cx - 1 .. cx + 1 (the
+// 27-cell stencil of the cell list, so a window never depends on how far
+// the chunk extends).  Every source of the stencil that the pair test
+// accepts is inside; the rest fail the test.  Windows are [j[r], je[r]) in
+// the table's indices.
+template <class E, int RB>
+__device__ __forceinline__ void target_windows(const E (*tbl)[RB], uint32_t coarse_mask,
+                                               const SysDesc& d, float xt, float yt, float zt, int cy,
+                                               int cz, int base, int (&j)[9], int (&je)[9])
+{
+    const Faces f = faces_of(d, yt, zt, cy, cz);
     const float rcm2 = d.rc2 * 1.00002f;
-    const float t = rcm2 - fmaf(ey, ey, ez * ez);
-    if (!(t > 0.f)) return -1.f;
-    const float tt = fmaxf(t, 1e-30f);
-    return tt * rsqrtf(tt) + d.slack;
+    const float xlo = d.g.lo[0], slack = d.slack, invs = d.g.inv_w[0] * (float)XSUB;
+    const int nx = d.g.n[0];
+    const int cx = axis_cell(xt, xlo, d.g.inv_w[0], nx);
+    const int lo = XSUB * max(cx - 1, 0) - base;
+    const int hi = XSUB * (min(cx + 1, nx - 1) + 1) - base - 1;
+#pragma unroll
+    for (int rr = 0; rr < 9; ++rr) {
+        const int dy = rr % 3 - 1, dz = rr / 3 - 1;
+        const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
+        const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
+        const float t = rcm2 - fmaf(ey, ey, ez * ez);
+        const float tt = fmaxf(t, 1e-30f);
+        const float w = tt * rsqrtf(tt) + slack;
+        const int b0 = sub_bin(xt - w, xlo, invs, base, lo, hi);
+        int b1 = sub_bin(xt + w, xlo, invs, base, lo, hi) + 1;
+        if ((coarse_mask >> rr) & 1u) b1 = (b1 + XSUB - 1) / XSUB * XSUB;
+        const int first = (int)tbl[rr][b0];
+        j[rr] = first;
+        je[rr] = t > 0.f ? (int)tbl[rr][b1] : first;
+    }
+}
+
+// 1.0f if a < b else 0.0f (PTX set with a float destination).
+__device__ __forceinline__ float lt_mask(float a, float b)
+{
+    float m;
+    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
+    return m;
+}
+
+// 1.0f if a < b and c < ce else 0.0f (the second comparison masks an odd
+// tail: the same set instruction, with a predicate combined by AND).
+__device__ __forceinline__ float lt_mask_and(float a, float b, int c, int ce)
+{
+    float m;
+    asm("{\n\t.reg .pred q;\n\t"
+        "setp.lt.s32 q, %3, %4;\n\t"
+        "set.lt.and.f32.f32 %0, %1, %2, q;\n\t}"
+        : "=f"(m)
+        : "f"(a), "f"(b), "r"(c), "r"(ce));
+    return m;
 }
 
 // Two Gaussian candidates at once with packed FP32 (f32x2) arithmetic:
-// every element is rounded exactly as the scalar operation would be, so the
-// pair test and the sums are those of Sums::pair_nb.
+// every element is rounded exactly as the scalar operation would be.  The
+// pair test gives a 1/0 mask m; K = 2^(r2 t) * m and n += m.  2^(r2 t) is in
+// [0, 1] for every finite candidate, so K is exactly the kernel value or +0.
 struct PackedSums {
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
 
-    // second = false drops the second candidate (an odd tail reuses the first)
-    __device__ __forceinline__ void pair2(float2 px, float2 py, float2 pz, float2 mx, float2 my,
-                                          float2 mz, float rc2, float2 ks, bool second = true)
+    // Sources s0 and s1, both real candidates or s1 the sentinel.  The
+    // offsets are formed by scalar subtractions straight into register
+    // pairs, which is cheaper than packing the loaded positions first.
+    __device__ __forceinline__ void pair2u(const float4& s0, const float4& s1, float xt, float yt,
+                                           float zt, float rc2, float2 ks)
     {
-        const float2 dx = __fadd2_rn(px, mx);
-        const float2 dy = __fadd2_rn(py, my);
-        const float2 dz = __fadd2_rn(pz, mz);
+        const float2 dx = make_float2(__fsub_rn(s0.x, xt), __fsub_rn(s1.x, xt));
+        const float2 dy = make_float2(__fsub_rn(s0.y, yt), __fsub_rn(s1.y, yt));
+        const float2 dz = make_float2(__fsub_rn(s0.z, zt), __fsub_rn(s1.z, zt));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const float2 t = __fmul2_rn(r2, ks);
-        const bool i0 = r2.x < rc2, i1 = (r2.y < rc2) && second;
-        const float e0 = ex2_approx(t.x), e1 = ex2_approx(t.y);
-        const float2 K = make_float2(i0 ? e0 : 0.f, i1 ? e1 : 0.f);
+        const float2 m = make_float2(lt_mask(r2.x, rc2), lt_mask(r2.y, rc2));
+        const float2 K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
         s = __fadd2_rn(s, K);
         vx = __ffma2_rn(dx, K, vx);
         vy = __ffma2_rn(dy, K, vy);
         vz = __ffma2_rn(dz, K, vz);
-        n = __fadd2_rn(n, make_float2(i0 ? 1.f : 0.f, i1 ? 1.f : 0.f));
+        n = __fadd2_rn(n, m);
+    }
+
+    // Sources s0 = candidate c and s1 = candidate c + 1 (or c again when
+    // c + 1 == ce, then masked out).  The offsets are formed by
+    // scalar subtractions straight into register pairs, which is cheaper
+    // than packing the loaded positions into pairs first.
+    __device__ __forceinline__ void pair2s(const float4& s0, const float4& s1, float xt, float yt,
+                                           float zt, float rc2, float2 ks, int c1, int ce)
+    {
+        const float2 dx = make_float2(__fsub_rn(s0.x, xt), __fsub_rn(s1.x, xt));
+        const float2 dy = make_float2(__fsub_rn(s0.y, yt), __fsub_rn(s1.y, yt));
+        const float2 dz = make_float2(__fsub_rn(s0.z, zt), __fsub_rn(s1.z, zt));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 t = __fmul2_rn(r2, ks);
+        const float2 m = make_float2(lt_mask(r2.x, rc2), lt_mask_and(r2.y, rc2, c1, ce));
+        const float2 K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
+        s = __fadd2_rn(s, K);
+        vx = __ffma2_rn(dx, K, vx);
+        vy = __ffma2_rn(dy, K, vy);
+        vz = __ffma2_rn(dz, K, vz);
+        n = __fadd2_rn(n, m);
     }
 };
 
-// The candidates [j, je) of one row window, in order.  The Gaussian FP32
-// path takes them two at a time (packed, even and odd partial sums); the
-// others one at a time.  Shared by the staged and the global-memory paths so
-// that both sum every target's terms in the same order.
+template <class Acc, int KERNEL>
+__host__ __device__ constexpr bool packed_path()
+{
+    return std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
+}
+
+// The candidates [j, je) of one window, in order.  The Gaussian FP32 path
+// takes them two at a time (packed, even and odd partial sums); the others
+// one at a time.
 template <class Acc, int KERNEL>
 __device__ __forceinline__ void window_sums(const float4* src, int j, int je, float xt, float yt,
                                             float zt, uint32_t slot, float rc2, const KParams& kp,
                                             PackedSums& ps, Sums<Acc, KERNEL>& r)
 {
-    constexpr bool packed = std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
     constexpr bool by_id = self_by_identity<KERNEL, Acc>();
-    if constexpr (packed) {
-        const float2 mx = make_float2(-xt, -xt), my = make_float2(-yt, -yt), mz = make_float2(-zt, -zt),
-                     ks = make_float2(kp.t, kp.t);
+    if constexpr (packed_path<Acc, KERNEL>()) {
+        const float2 ks = make_float2(kp.t, kp.t);
         for (; j < je; j += 2) {
-            const bool two = j + 1 < je;
-            const float4 s0 = src[j], s1 = src[two ? j + 1 : j];
-            ps.pair2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z), mx, my,
-                     mz, rc2, ks, two);
+            const float4 s0 = src[j], s1 = src[min(j + 1, je - 1)];
+            ps.pair2s(s0, s1, xt, yt, zt, rc2, ks, j + 1, je);
         }
     } else {
         for (; j < je; ++j) {
@@ -475,7 +611,7 @@ __device__ __forceinline__ void window_sums(const float4* src, int j, int je, fl
 template <class Acc, int KERNEL>
 __device__ __forceinline__ void finish_packed(const PackedSums& ps, Sums<Acc, KERNEL>& r)
 {
-    if constexpr (std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN) {
+    if constexpr (packed_path<Acc, KERNEL>()) {
         r.s.add(ps.s.x + ps.s.y);
         r.vx.add(ps.vx.x + ps.vx.y);
         r.vy.add(ps.vy.x + ps.vy.y);
@@ -484,83 +620,94 @@ __device__ __forceinline__ void finish_packed(const PackedSums& ps, Sums<Acc, KE
     }
 }
 
-// Global-memory path (mode 1) for one target: per row, the window
-// [first x >= x - w, first x > x + w) by binary search inside the cells of
-// x - w and x + w, summed exactly as the staged path does.
-template <class Acc, int KERNEL, class SM>
-__device__ __forceinline__ void target_sums_global(const InteractArgs& a, const SM& sm, float xt,
-                                                   float yt, float zt, uint32_t slot, int cy, int cz,
+// Mode 0, one target: its windows over the staged rows go to the thread's
+// column of sm.win (empty ones dropped), then all of them are walked in one
+// loop, so that a lane whose window in one row is short goes on with the
+// next row instead of idling until the warp's longest window of that row
+// ends.  The candidates and their order are those of the per-row loop of
+// mode 1 (window by window, two at a time, odd tails alone), so both modes
+// give the same sums.
+template <int CAP, int RB, int WT, class Acc, int KERNEL>
+__device__ __forceinline__ void target_sums_staged(const float4* buf, const uint16_t (*tbl)[RB],
+                                                   uint32_t coarse_mask, const SysDesc& d,
+                                                   uint32_t (*win)[WT], unsigned tid, float xt, float yt,
+                                                   float zt, uint32_t slot, int cy, int cz, int base,
                                                    const KParams& kp, Sums<Acc, KERNEL>& r)
 {
-    const Plan& p = sm.plan;
-    const SysDesc& d = sm.d;
-    const Faces f = faces_of(d, yt, zt, cy, cz);
+    int j[9], je[9];
+    target_windows(tbl, coarse_mask, d, xt, yt, zt, cy, cz, base, j, je);
+    int nw = 0;
+#pragma unroll
+    for (int rr = 0; rr < 9; ++rr)
+        if (je[rr] > j[rr]) win[nw++][tid] = (uint32_t)j[rr] * 16u | ((uint32_t)je[rr] * 16u << 16);
+    // nw >= 1: the window of the target's own row holds the target
+    const float rc2 = d.rc2;
     PackedSums ps;
-#pragma unroll 1
-    for (int rr = 0; rr < 9; ++rr) {
-        const int len = p.rlen[rr];
-        if (len == 0) continue;
-        const float w = row_halfwidth(d, f, rr);
-        if (w < 0.f) continue;
-        const float xlo = xt - w, xhi = xt + w;
-        const int kmax = p.xb - p.xa;
-        const int k0 = min(max(axis_cell(xlo, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa, 0), kmax);
-        const int k1 = min(max(axis_cell(xhi, d.g.lo[0], d.g.inv_w[0], d.g.n[0]) - p.xa, 0), kmax);
-        const float4* row = a.P + p.gbeg[rr];
-        int lo = (int)sm.tbl.cs[rr][k0], hi = (int)sm.tbl.cs[rr][k0 + 1];
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (row[mid].x < xlo) lo = mid + 1;
-            else hi = mid;
+    if constexpr (packed_path<Acc, KERNEL>()) {
+        const float2 ks = make_float2(kp.t, kp.t);
+        // byte offsets: candidates from buf[0], window words from this
+        // thread's first one
+        const char* cb = reinterpret_cast<const char*>(buf);
+        const char* wb = reinterpret_cast<const char*>(&win[0][tid]);
+        constexpr uint32_t SENT = (uint32_t)CAP * 16u, WSTEP = (uint32_t)WT * 4u;
+        uint32_t wo = 0;
+        const uint32_t woe = (uint32_t)nw * WSTEP;
+        uint32_t w = *reinterpret_cast<const uint32_t*>(wb);
+        uint32_t c = w & 0xffffu, ce = w >> 16;
+        // The window switch is written as selects so that no lane waits for
+        // the others at the end of a window: a lane leaves only after its
+        // last window.  Four candidates per trip, in two packed pairs; slots
+        // past the window's end read the sentinel, so the pairs and their
+        // order are those of the two-at-a-time loop.
+        do {
+            const uint32_t c1 = c + 16u < ce ? c + 16u : SENT;
+            const uint32_t c2 = c + 32u < ce ? c + 32u : SENT;
+            const uint32_t c3 = c + 48u < ce ? c + 48u : SENT;
+            const float4 s0 = *reinterpret_cast<const float4*>(cb + c);
+            const float4 s1 = *reinterpret_cast<const float4*>(cb + c1);
+            const float4 s2 = *reinterpret_cast<const float4*>(cb + c2);
+            const float4 s3 = *reinterpret_cast<const float4*>(cb + c3);
+            ps.pair2u(s0, s1, xt, yt, zt, rc2, ks);
+            ps.pair2u(s2, s3, xt, yt, zt, rc2, ks);
+            c += 64u;
+            const bool sw = c >= ce;
+            wo += sw ? WSTEP : 0u;
+            const uint32_t wn = *reinterpret_cast<const uint32_t*>(wb + wo);
+            c = sw ? (wn & 0xffffu) : c;
+            ce = sw ? (wn >> 16) : ce;
+        } while (wo < woe);
+        finish_packed(ps, r);
+    } else {
+        for (int k = 0; k < nw; ++k) {
+            const uint32_t w = win[k][tid];
+            window_sums<Acc, KERNEL>(buf, (int)((w & 0xffffu) >> 4), (int)(w >> 20), xt, yt, zt, slot, rc2,
+                                     kp, ps, r);
         }
-        int e0 = max((int)sm.tbl.cs[rr][k1], lo), e1 = (int)sm.tbl.cs[rr][k1 + 1];
-        while (e0 < e1) {
-            const int mid = (e0 + e1) >> 1;
-            if (row[mid].x > xhi) e1 = mid;
-            else e0 = mid + 1;
-        }
-        window_sums<Acc, KERNEL>(row, lo, e0, xt, yt, zt, slot, d.rc2, kp, ps, r);
     }
-    finish_packed(ps, r);
 }
 
-// Sums of one target over the staged rows (mode 0).  Per row: the x-window
-// from the row's lookup table, trimmed to [x - w, x + w] exactly; every
-// source in it is a candidate, taken two at a time.
-template <class Acc, int KERNEL, class SM>
-__device__ __forceinline__ void target_sums_staged(const SM& sm, float xt, float yt, float zt,
-                                                   uint32_t slot, int cy, int cz, int ncell,
-                                                   float inv4, const KParams& kp,
-                                                   Sums<Acc, KERNEL>& r)
+// Mode 1, one target: the same windows, read from P in global memory.
+template <class Acc, int KERNEL>
+__device__ __forceinline__ void target_sums_global(const float4* P, const uint32_t (*tbl)[RB_GLOBAL],
+                                                   uint32_t coarse_mask, const SysDesc& d, float xt,
+                                                   float yt, float zt, uint32_t slot, int cy, int cz,
+                                                   int base, const KParams& kp, Sums<Acc, KERNEL>& r)
 {
-    const Plan& p = sm.plan;
-    const SysDesc& d = sm.d;
-    const Faces f = faces_of(d, yt, zt, cy, cz);
-    const int nb = ncell * BPC, base = BPC * p.xa;
+    int j[9], je[9];
+    target_windows(tbl, coarse_mask, d, xt, yt, zt, cy, cz, base, j, je);
     PackedSums ps;
 #pragma unroll 1
-    for (int rr = 0; rr < 9; ++rr) {
-        if (p.rlen[rr] == 0) continue;
-        const float w = row_halfwidth(d, f, rr);
-        if (w < 0.f) continue;
-        const float xlo = xt - w, xhi = xt + w;
-        int j = sm.tbl.bin[rr][xbin(xlo, d.g.lo[0], inv4, base, nb)];
-        int bh = xbin(xhi, d.g.lo[0], inv4, base, nb) + 1;
-        if (sm.coarse[rr]) bh = (bh + BPC - 1) / BPC * BPC;
-        int je = sm.tbl.bin[rr][bh];
-        while (j < je && sm.buf[j].x < xlo) ++j;
-        while (je > j && sm.buf[je - 1].x > xhi) --je;
-        // window [j, je): every source in it is a candidate
-        window_sums<Acc, KERNEL>(sm.buf, j, je, xt, yt, zt, slot, d.rc2, kp, ps, r);
-    }
+    for (int rr = 0; rr < 9; ++rr)
+        window_sums<Acc, KERNEL>(P, j[rr], je[rr], xt, yt, zt, slot, d.rc2, kp, ps, r);
     finish_packed(ps, r);
 }
 
 template <class T, class Acc, int KERNEL>
 __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs a)
 {
-    constexpr int TT = T::TT, CAP = T::CAP;
-    __shared__ Smem<CAP> sm;
+    constexpr int TT = T::TT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
 
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
@@ -572,6 +719,7 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
 
     if (tid == 0) {
         sm.failed = 0;
+        sm.buf[T::CAP] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
         bar_init(&sm.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -598,7 +746,6 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
         const uint32_t row = sm.row;
         const SysDesc& d = sm.d;
         const int nx = d.g.n[0], ny = d.g.n[1];
-        const float inv4 = d.g.inv_w[0] * (float)BPC;
         const int cy = (int)(row % (uint32_t)ny), cz = (int)(row / (uint32_t)ny);
         const uint32_t rb0 = d.cell_base + (uint32_t)nx * row;
         // the self pair's contribution (0 where it is excluded by identity)
@@ -613,8 +760,8 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
         const int xe = sm.xe;
         for (int x0 = sm.xs; x0 < xe;) {
             if (warp == 0) {
-                if (lane < 9) sm.coarse[lane] = 0;
-                plan_chunk<TT, CAP>(a, d, sm.plan, x0, xe, cy, cz, lane);
+                if (lane == 0) sm.coarse_mask = 0u;
+                plan_chunk<T>(a, d, sm.plan, x0, xe, cy, cz, lane);
                 __syncwarp();
                 if (lane == 0 && sm.plan.mode == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -627,33 +774,13 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             }
             __syncthreads();
             const Plan& p = sm.plan;
-            const int x1 = p.x1, mode = p.mode, xa = p.xa;
-            const int ncell = p.xb - xa + 1;
-            // Row lookup tables, built from the offsets and the per-cell
-            // sub-bin starts while the bulk copies are in flight.
-            for (int e = tid; e < 9 * (ncell + 1); e += TT) {
-                const int rr = e / (ncell + 1), k = e % (ncell + 1);
-                if (p.rlen[rr] == 0) continue;
-                const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
-                const uint32_t cidx =
-                    d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xa + k;
-                const uint32_t g = a.offsets[cidx];
-                if (mode == 0) {
-                    const int start = p.sbeg[rr] + (int)(g - p.gbeg[rr]);
-                    if (k == ncell) {
-                        sm.tbl.bin[rr][BPC * ncell] = (uint16_t)start;
-                    } else {
-                        const uint32_t w = a.xbins[cidx];
-                        if (w >> 24) sm.coarse[rr] = 1;
-                        sm.tbl.bin[rr][BPC * k] = (uint16_t)start;
-                        sm.tbl.bin[rr][BPC * k + 1] = (uint16_t)(start + (int)(w & 255u));
-                        sm.tbl.bin[rr][BPC * k + 2] = (uint16_t)(start + (int)((w >> 8) & 255u));
-                        sm.tbl.bin[rr][BPC * k + 3] = (uint16_t)(start + (int)((w >> 16) & 255u));
-                    }
-                } else {
-                    sm.tbl.cs[rr][k] = g - p.gbeg[rr];
-                }
-            }
+            const int x1 = p.x1, mode = p.mode;
+            const int ncell = p.xb - p.xa + 1;
+            // lookup tables, built while the bulk copies are in flight
+            if (mode == 0)
+                build_table<T::TT / 32>(a, d, p, cy, cz, ncell, sm.tbl.staged, &sm.coarse_mask, warp, lane);
+            else
+                build_table<T::TT / 32>(a, d, p, cy, cz, ncell, sm.tbl.global, &sm.coarse_mask, warp, lane);
             if (mode == 0) {
                 if (!bar_wait_bounded(&sm.bar, phase, a.wait_limit_ns)) {
                     sm.failed = 1;
@@ -668,6 +795,7 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             const int ntarget = (int)(te - tb);
             // staged index of the first target (the centre row is row 4)
             const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
+            const int base = XSUB * p.xa;
             if (!sm.failed) {
                 for (int q0 = 0; q0 < ntarget; q0 += TT) {
                     const int q = q0 + (int)tid;
@@ -677,10 +805,12 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
                     const float4 me = mode == 0 ? sm.buf[t0 + q] : a.P[tb + q];
                     const uint32_t slot = __float_as_uint(me.w);
                     if (mode == 0)
-                        target_sums_staged<Acc, KERNEL>(sm, me.x, me.y, me.z, slot, cy, cz, ncell, inv4,
-                                                        kp, r);
+                        target_sums_staged<T::CAP, T::RB, T::TT, Acc, KERNEL>(
+                            sm.buf, sm.tbl.staged, sm.coarse_mask, sm.d, sm.win, tid, me.x, me.y, me.z, slot,
+                            cy, cz, base, kp, r);
                     else
-                        target_sums_global<Acc, KERNEL>(a, sm, me.x, me.y, me.z, slot, cy, cz, kp, r);
+                        target_sums_global<Acc, KERNEL>(a.P, sm.tbl.global, sm.coarse_mask, sm.d, me.x, me.y,
+                                                        me.z, slot, cy, cz, base, kp, r);
                     store_out(a, slot, r, kself, nself);
                 }
             }
@@ -688,6 +818,261 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             x0 = x1;
         }
     }
+}
+
+// ---- warp-specialised tiled interaction -----------------------------------------
+//
+// The same chunks, windows and per-target sums as k_interact_tiled, but the
+// chunk set-up no longer stalls the CTA: one producer warp plans a chunk,
+// issues its bulk copies and builds its lookup table into one of NS stage
+// buffers while W consumer warps work on the chunks already staged.  The
+// consumers take 32-target groups of a chunk from a counter, so a warp that
+// is done with its groups goes on with the next chunk instead of waiting for
+// the slowest warp.  Hand-over is by mbarriers: `full` (the producer's 32
+// lanes arrive after writing the stage, plus the bytes of the bulk copies)
+// and `empty` (every consumer lane arrives when its warp has left the
+// chunk).  Every wait is bounded.
+
+template <int W_, int CAP_, int NS_, int MAXLX_, int MINB_, int GMAX_>
+struct WsTile {
+    static constexpr int W = W_;              // consumer warps
+    static constexpr int CAP = CAP_;          // staged particles per stage
+    static constexpr int NS = NS_;            // stages
+    static constexpr int MAXLX = MAXLX_;      // target cells per chunk along X
+    static constexpr int MINB = MINB_;        // CTAs per SM the budget is sized for
+    static constexpr int TT = 32 * GMAX_;     // most targets per chunk (planner limit)
+    static constexpr int THREADS = 32 * (W + 1);
+    static constexpr int RB = ((MAXLX + 2) * XSUB + 1 + 7) / 8 * 8;
+};
+using Ws4 = WsTile<4, 1152, 2, SEG_CELLS, 4, 8>;
+using Ws8 = WsTile<8, 1152, 3, SEG_CELLS, 2, 8>;
+
+template <class T>
+struct WsStage {
+    float4 buf[T::CAP + 1];  // staged rows; buf[CAP] is the sentinel
+    union {
+        __align__(16) uint16_t staged[9][T::RB];
+        uint32_t global[9][RB_GLOBAL];
+    } tbl;
+    Plan plan;
+    SysDesc d;
+    float t;               // kernel scale of the chunk's system
+    uint32_t coarse_mask;  // bit r: row r holds a cell without sub-bin starts
+    int cy, cz;            // the chunk's X-row
+    uint32_t tb;           // P index of its first target
+    int ntarget, ngroups;
+    int next_group;        // next 32-target group handed to a consumer warp
+    int done;              // set instead of a chunk when the work is over
+    uint64_t full, empty;
+};
+
+template <class T>
+struct WsSmem {
+    WsStage<T> st[T::NS];
+    uint32_t win[10][32 * T::W];  // per consumer thread: its windows (see target_sums_staged)
+    int failed;
+};
+
+template <class T>
+constexpr bool ws_fits_sm()
+{
+    return T::MINB * (sizeof(WsSmem<T>) + 1024) <= 228u * 1024u;
+}
+static_assert(ws_fits_sm<Ws4>() && ws_fits_sm<Ws8>(),
+              "warp-specialised shapes exceed the shared memory of their CTAs per SM");
+
+__device__ __forceinline__ void bar_expect_tx_only(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait of a whole warp; the outcome is the same on every lane (a
+// lane whose wait ran out makes the warp give up), so that the warp stays
+// converged for the shuffles that follow.
+template <class T>
+__device__ __forceinline__ bool ws_wait(WsSmem<T>& sm, uint64_t* bar, uint32_t parity, uint64_t limit,
+                                        Ctrl* ctrl)
+{
+    const bool got = bar_wait_bounded(bar, parity, limit);
+    if (__all_sync(0xffffffffu, got)) return true;
+    if ((threadIdx.x & 31u) == 0) {
+        *((volatile int*)&sm.failed) = 1;
+        atomicOr(&ctrl->error, ERR_TIMEOUT);
+    }
+    return false;
+}
+
+template <class T>
+__device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
+{
+    constexpr int NS = T::NS;
+    // per stage: its last use handed over, and whether that use had bulk
+    // copies (those of earlier uses have landed: the consumers waited for
+    // them before releasing the stage)
+    int last_use[NS];
+    bool copies[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        last_use[s] = -1;
+        copies[s] = false;
+    }
+    uint32_t v = 0;  // chunks handed over so far
+    bool ok = true;
+    while (ok) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&a.ctrl->work[a.seq & 1u], 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.work) break;
+        const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.wbase, a.sy.S, item);
+        const SysDesc d = a.sy.sys[sid];
+        const float t = a.kscale ? a.kscale[sid] : a.kscale0;
+        const uint32_t local = item - d.work_base;
+        const uint32_t seg = local % d.nseg, row = local / d.nseg;
+        const int nx = d.g.n[0], ny = d.g.n[1];
+        const int cy = (int)(row % (uint32_t)ny), cz = (int)(row / (uint32_t)ny);
+        const uint32_t rb0 = d.cell_base + (uint32_t)nx * row;
+        const int xs = (int)seg * SEG_CELLS, xe = min(nx, (int)(seg + 1) * SEG_CELLS);
+        for (int x0 = xs; x0 < xe;) {
+            const int s = (int)(v % NS);
+            const uint32_t u = v / NS;
+            WsStage<T>& st = sm.st[s];
+            if (u > 0 && !ws_wait(sm, &st.empty, (u - 1u) & 1u, a.wait_limit_ns, a.ctrl)) {
+                ok = false;
+                break;
+            }
+            if (lane == 0) st.coarse_mask = 0u;
+            __syncwarp();
+            plan_chunk<T>(a, d, st.plan, x0, xe, cy, cz, lane);
+            __syncwarp();
+            const Plan& p = st.plan;
+            const int x1 = p.x1, mode = p.mode, ncell = p.xb - p.xa + 1;
+            if (lane == 0 && mode == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect_tx_only(&st.full, (uint32_t)p.total * 16u);
+                for (int rr = 0; rr < 9; ++rr)
+                    if (p.rlen[rr] > 0)
+                        bulk_g2s(&st.buf[p.sbeg[rr]], a.P + p.gbeg[rr], (uint32_t)p.rlen[rr] * 16u, &st.full);
+            }
+            last_use[s] = (int)u;
+            copies[s] = mode == 0;
+            if (mode == 0) {
+                build_table<1>(a, d, p, cy, cz, ncell, st.tbl.staged, &st.coarse_mask, 0u, lane);
+            } else {
+                build_table<1>(a, d, p, cy, cz, ncell, st.tbl.global, &st.coarse_mask, 0u, lane);
+            }
+            if (lane == 0) {
+                const uint32_t tb = a.offsets[rb0 + x0];
+                const int nt = (int)(a.offsets[rb0 + x1] - tb);
+                st.d = d;
+                st.t = t;
+                st.cy = cy;
+                st.cz = cz;
+                st.tb = tb;
+                st.ntarget = nt;
+                st.ngroups = (nt + 31) / 32;
+                st.next_group = 0;
+                st.done = 0;
+            }
+            bar_arrive(&st.full);  // every lane: its table entries are written
+            ++v;
+            x0 = x1;
+        }
+    }
+    if (ok) {
+        const int s = (int)(v % NS);
+        const uint32_t u = v / NS;
+        WsStage<T>& st = sm.st[s];
+        if (u == 0 || ws_wait(sm, &st.empty, (u - 1u) & 1u, a.wait_limit_ns, a.ctrl)) {
+            if (lane == 0) st.done = 1;
+            bar_arrive(&st.full);
+            return;  // the consumers wait for every handed-over stage before they leave
+        }
+    }
+    // after a failure, let this CTA's bulk copies in flight land first
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (copies[s]) bar_wait_bounded(&sm.st[s].full, (uint32_t)last_use[s] & 1u, a.wait_limit_ns);
+}
+
+template <class T, class Acc, int KERNEL>
+__device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, unsigned lane, float kself,
+                            uint32_t nself)
+{
+    constexpr int NS = T::NS;
+    for (uint32_t v = 0;; ++v) {
+        const int s = (int)(v % NS);
+        const uint32_t u = v / NS;
+        WsStage<T>& st = sm.st[s];
+        if (!ws_wait(sm, &st.full, u & 1u, a.wait_limit_ns, a.ctrl)) return;
+        if (st.done) return;
+        const Plan& p = st.plan;
+        const int mode = p.mode, base = XSUB * p.xa, cy = st.cy, cz = st.cz, nt = st.ntarget,
+                  ng = st.ngroups;
+        const uint32_t tb = st.tb;
+        const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
+        const KParams kp{st.t, a.one, a.zero};
+        for (;;) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&st.next_group, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= ng) break;
+            const int q = 32 * g + (int)lane;
+            if (q < nt) {
+                Sums<Acc, KERNEL> r;
+                const float4 me = mode == 0 ? st.buf[t0 + q] : a.P[tb + q];
+                const uint32_t slot = __float_as_uint(me.w);
+                if (mode == 0)
+                    target_sums_staged<T::CAP, T::RB, 32 * T::W, Acc, KERNEL>(
+                        st.buf, st.tbl.staged, st.coarse_mask, st.d, sm.win, tid, me.x, me.y, me.z, slot, cy,
+                        cz, base, kp, r);
+                else
+                    target_sums_global<Acc, KERNEL>(a.P, st.tbl.global, st.coarse_mask, st.d, me.x, me.y,
+                                                    me.z, slot, cy, cz, base, kp, r);
+                store_out(a, slot, r, kself, nself);
+            }
+        }
+        __syncwarp();
+        bar_arrive(&st.empty);
+        if (__any_sync(0xffffffffu, *((volatile int*)&sm.failed) != 0)) return;
+    }
+}
+
+template <class T, class Acc, int KERNEL>
+__global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WsSmem<T>& sm = *reinterpret_cast<WsSmem<T>*>(smem_raw);
+    const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) {
+        if (blockIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
+        sm.failed = load_error(a.ctrl) != 0u;
+        for (int s = 0; s < T::NS; ++s) {
+            sm.st[s].buf[T::CAP] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
+            bar_init(&sm.st[s].full, 32);
+            bar_init(&sm.st[s].empty, 32 * T::W);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (sm.failed) return;
+    // the self pair's contribution (0 where it is excluded by identity)
+    float kself = KERNEL == KERNEL_GAUSSIAN ? ex2_approx(0.f) : 0.f;
+    uint32_t nself = 1u;
+    if constexpr (KERNEL == KERNEL_LOWFLOP) kself = 1.0f;
+    if constexpr (self_by_identity<KERNEL, Acc>()) {
+        kself = 0.f;
+        nself = 0u;
+    }
+    if (warp == (unsigned)T::W)
+        ws_producer<T>(a, sm, lane);
+    else
+        ws_consumer<T, Acc, KERNEL>(a, sm, tid, lane, kself, nself);
 }
 
 template <class Acc>
@@ -703,36 +1088,66 @@ cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class T, class Acc, int KERNEL>
+void launch_tiled_one(const InteractArgs& a, unsigned grid, cudaStream_t s)
+{
+    k_interact_tiled<T, Acc, KERNEL><<<grid, T::TT, sizeof(Smem<T>), s>>>(a);
+}
+
+template <class T, class Acc, int KERNEL>
+void launch_ws_one(const InteractArgs& a, unsigned grid, cudaStream_t s)
+{
+    k_interact_ws<T, Acc, KERNEL><<<grid, T::THREADS, sizeof(WsSmem<T>), s>>>(a);
+}
+
 template <class Acc>
 cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
                              cudaStream_t s)
 {
-    // the other kernels are comparators: they run with the middle tile shape
-    if (a.kernel != KERNEL_GAUSSIAN) tile = 1;
-    const int TTs[3] = {Tile64::TT, Tile128::TT, Tile256::TT};
+    // the other kernels are comparators: they run with one tile shape
+    if (a.kernel != KERNEL_GAUSSIAN) tile = DEFAULT_TILE;
     uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
-    const int tt = TTs[tile];
+    using TD = Tile32;
+    static_assert(DEFAULT_TILE == 0, "the comparator kernels use the default shape");
     switch (a.kernel) {
-        case KERNEL_LJ: k_interact_tiled<Tile128, Acc, KERNEL_LJ><<<g, tt, 0, s>>>(a); break;
-        case KERNEL_LOWFLOP: k_interact_tiled<Tile128, Acc, KERNEL_LOWFLOP><<<g, tt, 0, s>>>(a); break;
-        case KERNEL_HIGHFLOP: k_interact_tiled<Tile128, Acc, KERNEL_HIGHFLOP><<<g, tt, 0, s>>>(a); break;
+        case KERNEL_LJ: launch_tiled_one<TD, Acc, KERNEL_LJ>(a, g, s); break;
+        case KERNEL_LOWFLOP: launch_tiled_one<TD, Acc, KERNEL_LOWFLOP>(a, g, s); break;
+        case KERNEL_HIGHFLOP: launch_tiled_one<TD, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
         default:
-            if (tile == 0) k_interact_tiled<Tile64, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
-            else if (tile == 2) k_interact_tiled<Tile256, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
-            else k_interact_tiled<Tile128, Acc, KERNEL_GAUSSIAN><<<g, tt, 0, s>>>(a);
+            switch (tile) {
+                case 0: launch_tiled_one<Tile32, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 1: launch_tiled_one<Tile64, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 3: launch_tiled_one<Tile256, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 4: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 5: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                default: launch_tiled_one<Tile128, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+            }
             break;
     }
     return cudaGetLastError();
 }
 
+// Allows the shape's dynamic shared memory (above the 48 KB default for the
+// largest shape) and returns its resident CTAs per SM.
+template <class T, class Acc>
+cudaError_t ws_occupancy_of(int* per_sm)
+{
+    auto fn = k_interact_ws<T, Acc, KERNEL_GAUSSIAN>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WsSmem<T>));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T::THREADS, sizeof(WsSmem<T>));
+}
+
 template <class T, class Acc>
 cudaError_t occupancy_of(int* per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_interact_tiled<T, Acc, KERNEL_GAUSSIAN>,
-                                                         T::TT, 0);
+    auto fn = k_interact_tiled<T, Acc, KERNEL_GAUSSIAN>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<T>));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T::TT, sizeof(Smem<T>));
 }
 
 }  // namespace
@@ -745,17 +1160,22 @@ cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms,
     return kahan ? launch_ppnl_acc<KahanAcc>(a, s) : launch_ppnl_acc<PlainAcc>(a, s);
 }
 
-cudaError_t tiled_occupancy(bool kahan, int* per_sm)
+template <class Acc>
+cudaError_t tiled_occupancy_acc(int* per_sm)
 {
     cudaError_t e;
-    if (kahan) {
-        if ((e = occupancy_of<Tile64, KahanAcc>(&per_sm[0])) != cudaSuccess) return e;
-        if ((e = occupancy_of<Tile128, KahanAcc>(&per_sm[1])) != cudaSuccess) return e;
-        return occupancy_of<Tile256, KahanAcc>(&per_sm[2]);
-    }
-    if ((e = occupancy_of<Tile64, PlainAcc>(&per_sm[0])) != cudaSuccess) return e;
-    if ((e = occupancy_of<Tile128, PlainAcc>(&per_sm[1])) != cudaSuccess) return e;
-    return occupancy_of<Tile256, PlainAcc>(&per_sm[2]);
+    if ((e = occupancy_of<Tile32, Acc>(&per_sm[0])) != cudaSuccess) return e;
+    if ((e = occupancy_of<Tile64, Acc>(&per_sm[1])) != cudaSuccess) return e;
+    if ((e = occupancy_of<Tile128, Acc>(&per_sm[2])) != cudaSuccess) return e;
+    if ((e = occupancy_of<Tile256, Acc>(&per_sm[3])) != cudaSuccess) return e;
+    if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[4])) != cudaSuccess) return e;
+    return ws_occupancy_of<Ws8, Acc>(&per_sm[5]);
+}
+
+cudaError_t tiled_occupancy(bool kahan, int* per_sm)
+{
+    static_assert(NUM_TILES == 6, "one occupancy entry per tile shape");
+    return kahan ? tiled_occupancy_acc<KahanAcc>(per_sm) : tiled_occupancy_acc<PlainAcc>(per_sm);
 }
 
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,

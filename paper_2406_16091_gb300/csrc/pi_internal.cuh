@@ -9,7 +9,7 @@
 // Layout of the device state (one cudaMalloc arena):
 //   Ctrl            control words (scan ticket, error bits, M_C, row counters)
 //   counts[C]       particles per cell (C = cells of all systems)
-//   xbins[C]        per cell, where its 4 x-sub-bins start in P (k_stabilise)
+//   xbins[C]        per cell, where its XSUB x-sub-bins start in P (k_stabilise)
 //   pbase[S+1]      first particle of each system in the current step
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
@@ -98,6 +98,12 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
+// x-sub-bins per cell.  A particle of cell cx lies in sub-bin
+// clamp(floor((x - lo) * XSUB * inv_w) - XSUB * cx, 0, XSUB - 1), which is
+// monotone in x along an X-row; k_stabilise stores where each sub-bin of a
+// cell starts, and the tiled interaction uses them to find x-windows.
+constexpr int XSUB = 8;
+
 // Cell index of a position (Sec. 2: "compute its cell index using its
 // physical position").  FP32, round-to-nearest subtract and multiply, floor,
 // clamp; X fastest so that an X-row of cells is contiguous after sorting.
@@ -157,7 +163,7 @@ cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const flo
                            uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s);
 cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
                              const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
-                             float* sy_out, float* sz, float4* P, uint32_t* xbins, Ctrl* ctrl,
+                             float* sy_out, float* sz, float4* P, uint2* xbins, Ctrl* ctrl,
                              int num_sms, cudaStream_t s);
 
 // FP64 total of v over the particles of each system (out[S], device), in a
@@ -181,7 +187,7 @@ enum : int { KERNEL_GAUSSIAN = 0, KERNEL_LJ = 1, KERNEL_LOWFLOP = 2, KERNEL_HIGH
 struct InteractArgs {
     Systems sy;
     const float4* P;        // x-ordered copy: (x, y, z, stable slot as bits)
-    const uint32_t* xbins;  // per cell: starts of its 4 x-sub-bins (see k_stabilise)
+    const uint2* xbins;     // per cell: starts of its XSUB x-sub-bins (see k_stabilise)
     const float* sx;
     const float* sy_pos;
     const float* sz;
@@ -207,11 +213,14 @@ struct InteractArgs {
 // Each adds the number of kernels it launched to *launches.
 cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
                                  int* launches);
-// tile: 0, 1, 2 = 64, 128, 256 targets per chunk; per_sm[tile] = resident CTAs.
-constexpr int NUM_TILES = 3;
+// tile: 0, 1, 2, 3 = 32, 64, 128, 256 targets per chunk (one thread each);
+// 4, 5 = warp-specialised, 4 or 8 consumer warps; per_sm[tile] = resident
+// CTAs.
+constexpr int NUM_TILES = 6;
+constexpr int DEFAULT_TILE = 0;
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
                                   int tile, cudaStream_t s, int* launches);
-// Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[3]).
+// Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[NUM_TILES]).
 cudaError_t tiled_occupancy(bool kahan, int* per_sm);
 
 }  // namespace pi

@@ -18,6 +18,11 @@ from gpu_harness import check_binning, check_interaction, oracle_run, run_gpu
 pytestmark = pytest.mark.gpu
 
 ALGOS = [B.PI_ALGO_TILED, B.PI_ALGO_PPNL]
+# (algorithm, tile shape): the one-thread-per-target shapes of 32 and 128
+# targets, both warp-specialised shapes, and Alg. 1
+VARIANTS = [(B.PI_ALGO_TILED, 0), (B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 4), (B.PI_ALGO_TILED, 5),
+            (B.PI_ALGO_PPNL, None)]
+VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "ppnl"]
 
 
 def _case(w):
@@ -35,11 +40,12 @@ SMALL_CASES = {
 
 
 @pytest.mark.parametrize("name", list(SMALL_CASES))
-@pytest.mark.parametrize("algo", ALGOS)
-def test_small_workloads(name, algo):
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
+def test_small_workloads(name, variant):
     x, y, z, lo, hi, rc, h = _case(SMALL_CASES[name])
     b, r = oracle_run(x, y, z, lo, hi, rc, h)
-    g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo)
+    algo, tile = variant
+    g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile)
     check_binning(g, b)
     check_interaction(g, r)
 
@@ -49,8 +55,8 @@ def test_tiny_and_ragged_sizes(n):
     x, y, z = W.uniform(n, 100 + n)
     rc = 0.2
     b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2)
-    for algo in ALGOS:
-        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo, n_max=n + 7)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo, tile=tile, n_max=n + 7)
         check_binning(g, b)
         if n:
             check_interaction(g, r)
@@ -61,8 +67,8 @@ def test_non_cubic_box_with_offset():
     x, y, z = W.uniform(30000, 77, lo, hi)
     rc = 0.031
     b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2)
-    for algo in ALGOS:
-        g = run_gpu(x, y, z, lo, hi, rc, rc / 2, algo=algo)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, lo, hi, rc, rc / 2, algo=algo, tile=tile)
         check_binning(g, b)
         check_interaction(g, r)
 
@@ -74,9 +80,10 @@ def test_long_rows_longer_than_a_chunk():
     rc = 0.01
     b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2)
     assert b.dims[0] == 300
-    g = run_gpu(x, y, z, lo, hi, rc, rc / 2)
-    check_binning(g, b)
-    check_interaction(g, r)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, lo, hi, rc, rc / 2, algo=algo, tile=tile)
+        check_binning(g, b)
+        check_interaction(g, r)
 
 
 def test_dense_cell_overflows_shared_memory():
@@ -89,8 +96,8 @@ def test_dense_cell_overflows_shared_memory():
     rc = 1.0 / 64
     b, r = oracle_run(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), rc, rc / 2)
     assert b.max_per_cell > 300
-    for algo in ALGOS:
-        g = run_gpu(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo)
+    for algo, tile in VARIANTS:
+        g = run_gpu(p[:, 0], p[:, 1], p[:, 2], (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo, tile=tile)
         check_binning(g, b)
         check_interaction(g, r)
 
@@ -105,14 +112,14 @@ def test_lattice_on_cell_faces():
     rc = 1.0 / m
     b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2)
     assert r.nbr.max() == 0
-    for algo in ALGOS:
-        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, rc / 2, algo=algo, tile=tile)
         check_binning(g, b)
         check_interaction(g, r)
     rc2 = 1.5 / m
     b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc2, rc2 / 2)
-    for algo in ALGOS:
-        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc2, rc2 / 2, algo=algo)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc2, rc2 / 2, algo=algo, tile=tile)
         check_binning(g, b)
         check_interaction(g, r)
 
@@ -121,8 +128,8 @@ def test_coincident_particles():
     x = np.full(50, 0.3, np.float32)
     y = np.full(50, 0.6, np.float32)
     b, r = oracle_run(x, y, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05)
-    for algo in ALGOS:
-        g = run_gpu(x, y, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05, algo=algo)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, x, (0, 0, 0), (1, 1, 1), 0.1, 0.05, algo=algo, tile=tile)
         check_binning(g, b)
         check_interaction(g, r)
         assert np.all(g["S"] == 49.0)
@@ -131,8 +138,8 @@ def test_coincident_particles():
 def test_original_order_output():
     x, y, z, lo, hi, rc, h = _case(W.scaled(W.SMALL, 10000))
     b, r = oracle_run(x, y, z, lo, hi, rc, h)
-    for algo in ALGOS:
-        g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, order=B.PI_ORDER_ORIGINAL)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile, order=B.PI_ORDER_ORIGINAL)
         check_interaction(g, r, perm=b.perm)
 
 
@@ -141,17 +148,17 @@ def test_kahan_precision_mode():
     plain FP32 sums on a 32-per-cell workload."""
     x, y, z, lo, hi, rc, h = _case(W.scaled(W.SCALE_VARIANTS[32], 40000))
     b, r = oracle_run(x, y, z, lo, hi, rc, h)
-    for algo in ALGOS:
-        plain = check_interaction(run_gpu(x, y, z, lo, hi, rc, h, algo=algo), r)
+    for algo, tile in VARIANTS:
+        plain = check_interaction(run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile), r)
         kahan = check_interaction(
-            run_gpu(x, y, z, lo, hi, rc, h, algo=algo, precision=B.PI_PREC_KAHAN), r)
+            run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile, precision=B.PI_PREC_KAHAN), r)
         assert kahan["S"] <= plain["S"] * 1.01 + 1e-9
 
 
 def test_repeat_is_deterministic():
     x, y, z, lo, hi, rc, h = _case(W.scaled(W.CLUSTERED, 50000))
-    a = run_gpu(x, y, z, lo, hi, rc, h, repeat=1)
-    c = run_gpu(x, y, z, lo, hi, rc, h, repeat=3)
+    a = run_gpu(x, y, z, lo, hi, rc, h, repeat=1, tile=4)
+    c = run_gpu(x, y, z, lo, hi, rc, h, repeat=3, tile=4)
     for k in ("counts", "offsets", "perm", "sx", "nbr", "S", "Vx", "Vy", "Vz"):
         assert np.array_equal(a[k].view(np.uint32), c[k].view(np.uint32)), k
 
