@@ -261,11 +261,14 @@ def run_ours(args):
         B.pi_bin(ctx, tx, ty, tz, n, s)
         B.pi_interact(ctx, w.h, S, Vx, Vy, Vz, nb, B.PI_ORDER_SORTED, s)
 
-    tile_ms = None
-    if args.tile == "auto":
+    tile_ms, tile = None, None
+    if args.algo == "tiled" and args.tile == "auto":
+        # the autotuner may also pick Alg. 1 (PPNL); the line reports the choice
         step()
         tile, tile_ms = B.pi_autotune(ctx, [w.h], S, Vx, Vy, Vz, nb, B.PI_ORDER_SORTED, 5, s)
-    else:
+        if tile == B.PI_AUTOTUNE_PPNL:
+            args.algo = "ppnl"
+    elif args.algo == "tiled":
         tile = int(args.tile)
         B.pi_set_option(ctx, B.PI_OPT_TILE, tile)
     for _ in range(max(3, args.warmup)):
@@ -654,15 +657,22 @@ def study_sweep(args):
         for kname, kern in kernels if name == "scale" else kernels[:1]:
             B.pi_set_option(ctx, B.PI_OPT_KERNEL, kern)
             entry = {"workload": name, "kernel": kname}
+            run = lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
             for algo_name, algo in (("tiled", B.PI_ALGO_TILED), ("ppnl", B.PI_ALGO_PPNL)):
                 B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
-                run = lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+                B.pi_set_option(ctx, B.PI_OPT_TILE, 4)
                 run()
                 ms, _ = _time_events(torch, run, 10, flush)
                 entry[f"{algo_name}_ms"] = ms
+            # what the autotuner picks for this occupancy and kernel
+            chosen, cand_ms = B.pi_autotune(ctx, [w.h], *out, nb, B.PI_ORDER_SORTED, 3, s)
+            entry["autotuned"] = "ppnl" if chosen == B.PI_AUTOTUNE_PPNL else f"tile{chosen}"
+            entry["autotuned_ms"], _ = _time_events(torch, run, 10, flush)
+            entry["candidate_ms"] = cand_ms
             pairs = int(nb.to(torch.int64).sum().item())
             entry["pairs"] = pairs
             entry["tiled_pairs_per_s"] = pairs / (entry["tiled_ms"] * 1e-3)
+            entry["autotuned_pairs_per_s"] = pairs / (entry["autotuned_ms"] * 1e-3)
             entry["speedup_vs_ppnl"] = entry["ppnl_ms"] / entry["tiled_ms"]
             rows.append(entry)
         B.pi_set_option(ctx, B.PI_OPT_KERNEL, B.PI_KERNEL_GAUSSIAN)

@@ -89,7 +89,7 @@ enum {
      * targets (threads) per chunk with 512, 576, 1280, 2432 staged
      * particles; 4, 5 for the warp-specialised form (one producer warp
      * stages chunks of up to 1152 particles into 2 or 3 buffers for 4 or 8
-     * consumer warps).  Default 0.  pi_autotune sets it from measurements.
+     * consumer warps).  Default 4.  pi_autotune sets it from measurements.
      * Results do not depend on it. */
     PI_OPT_TILE = 6
 };
@@ -207,16 +207,19 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
 pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                             uint32_t* nbr, int out_order, pi_stream stream);
 
-/* Autotuner of the tiled interaction's tile shape (PI_OPT_TILE) for the
- * data of the last pi_bin / pi_batch_bin: runs the interaction (arguments as
- * pi_batch_interact, h one entry per system) once untimed and `reps` times
- * timed (1 <= reps <= 100) for each shape, keeps the shape with the
- * smallest median time for later calls, and returns it in *chosen and the
- * medians in ms[6] (milliseconds; either pointer may be NULL).  The shape
- * changes only the speed: the outputs are the same for every shape (each
- * target's terms are summed in the same order).  Synchronises `stream`.  The
- * output arrays hold the last run's results.
- * Errors: those of pi_batch_interact, PI_ERR_INVALID_ARG, PI_ERR_CUDA. */
+/* Autotuner of the interaction for the data of the last pi_bin /
+ * pi_batch_bin: runs the interaction (arguments as pi_batch_interact, h one
+ * entry per system) once untimed and `reps` times timed (1 <= reps <= 100)
+ * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..5) and then
+ * with PI_ALGO_PPNL, keeps the candidate with the smallest median time for
+ * later calls (setting PI_OPT_ALGO and PI_OPT_TILE), and returns its index in
+ * *chosen (0..5 = tile shape, 6 = PI_ALGO_PPNL) and the medians in ms[7]
+ * (milliseconds; either pointer may be NULL).  The choice changes only the
+ * speed: every tile shape sums each target's terms in the same order, so
+ * their outputs are identical; PPNL's agree with them within the stated
+ * tolerance.  Synchronises `stream`.  The output arrays hold the last run's
+ * results.  Errors: those of pi_batch_interact, PI_ERR_INVALID_ARG,
+ * PI_ERR_CUDA (the previous algorithm and shape are then kept). */
 pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                       uint32_t* nbr, int out_order, int reps, int32_t* chosen, float* ms,
                       pi_stream stream);

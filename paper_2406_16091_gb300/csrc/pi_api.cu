@@ -19,6 +19,7 @@
 using pi::Ctrl;
 using pi::Grid;
 using pi::SysDesc;
+using pi::Rec;
 
 struct pi_ctx {
     int S;
@@ -51,8 +52,7 @@ struct pi_ctx {
     double* d_partial;            // [S * TOTAL_PARTS] scratch of pi_total_f64
     uint32_t* cell;
     uint32_t* rank;
-    uint32_t* perm_u;
-    float4* pos_u;
+    Rec* rec;
     uint32_t* perm;
     float* sx;
     float* sy;
@@ -288,8 +288,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_partial = k.take<double>((size_t)S * pi::TOTAL_PARTS);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
-    const size_t o_permu = k.take<uint32_t>(nm + 4);
-    const size_t o_posu = k.take<float4>(nm + 4);
+    const size_t o_rec = k.take<Rec>(nm + 4);
     const size_t o_perm = k.take<uint32_t>(nm + 4);
     const size_t o_sx = k.take<float>(nm + 4);
     const size_t o_sy = k.take<float>(nm + 4);
@@ -317,8 +316,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->d_partial = (double*)(base + o_partial);
     c->cell = (uint32_t*)(base + o_cell);
     c->rank = (uint32_t*)(base + o_rank);
-    c->perm_u = (uint32_t*)(base + o_permu);
-    c->pos_u = (float4*)(base + o_posu);
+    c->rec = (Rec*)(base + o_rec);
     c->perm = (uint32_t*)(base + o_perm);
     c->sx = (float*)(base + o_sx);
     c->sy = (float*)(base + o_sy);
@@ -524,9 +522,9 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
                            ctx->wait_limit_ns, ctx->withhold_scan, s));
     ctx->launches += 1;
     if (nn > 0) {
-        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, ctx->offsets, ctx->perm_u,
-                                  ctx->pos_u, ctx->ctrl, ctx->num_sms, s));
-        PI_TRY(pi::launch_stabilise(ctx->perm_u, ctx->pos_u, nn, sy, ctx->offsets, ctx->perm, ctx->sx,
+        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, ctx->offsets, ctx->rec, ctx->ctrl,
+                                  ctx->num_sms, s));
+        PI_TRY(pi::launch_stabilise(ctx->rec, nn, sy, ctx->offsets, ctx->perm, ctx->sx,
                                     ctx->sy, ctx->sz, ctx->P, ctx->xbins, ctx->ctrl, ctx->num_sms,
                                     s));
         ctx->launches += 2;
@@ -623,8 +621,7 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_autotune: set device");
     cudaStream_t st = (cudaStream_t)stream;
-    const int saved_algo = ctx->algo;
-    ctx->algo = PI_ALGO_TILED;
+    const int saved_algo = ctx->algo, saved_tile = ctx->tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PI_TRY(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -632,11 +629,14 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
         cudaEventDestroy(e0);
         return cuda_fail(ce, "pi_autotune: event");
     }
+    // candidates: every tile shape of the tiled algorithm, then Alg. 1
+    constexpr int PPNL = pi::NUM_TILES;
     float best = 0.f;
-    int best_tile = ctx->tile;
+    int best_c = -1;
     pi_status result = PI_OK;
-    for (int t = 0; t < pi::NUM_TILES && result == PI_OK; ++t) {
-        ctx->tile = t;
+    for (int t = 0; t <= PPNL && result == PI_OK; ++t) {
+        ctx->algo = t == PPNL ? PI_ALGO_PPNL : PI_ALGO_TILED;
+        if (t < PPNL) ctx->tile = t;
         // one untimed run, then the timed ones; the median counts
         result = pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr, out_order, stream);
         std::vector<float> times;
@@ -654,16 +654,21 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
         std::sort(times.begin(), times.end());
         const float med = times[times.size() / 2];
         if (ms) ms[t] = med;
-        if (t == 0 || med < best) {
+        if (best_c < 0 || med < best) {
             best = med;
-            best_tile = t;
+            best_c = t;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->algo = saved_algo;
-    ctx->tile = best_tile;
-    if (chosen) *chosen = best_tile;
+    if (result != PI_OK || best_c < 0) {
+        ctx->algo = saved_algo;
+        ctx->tile = saved_tile;
+        return result;
+    }
+    ctx->algo = best_c == PPNL ? PI_ALGO_PPNL : PI_ALGO_TILED;
+    ctx->tile = best_c == PPNL ? saved_tile : best_c;
+    if (chosen) *chosen = best_c;
     return result;
 }
 

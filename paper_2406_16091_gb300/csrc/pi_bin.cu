@@ -278,35 +278,106 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
 
 // ---- a4 ---------------------------------------------------------------------
 
+// One record as a single 256-bit store: a whole 32-byte DRAM sector, so the
+// random write needs no read of the rest of the sector.
+__device__ __forceinline__ void store_rec(Rec* dst, float x, uint32_t i, float y, float z, uint32_t c)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst),
+                 "r"(__float_as_uint(x)), "r"(i), "r"(__float_as_uint(y)), "r"(__float_as_uint(z)), "r"(c),
+                 "r"(0u), "r"(0u), "r"(0u)
+                 : "memory");
+}
+
+__device__ __forceinline__ Rec load_rec(const Rec* src)
+{
+    Rec r;
+    uint32_t x, y, z, p0, p1, p2;
+    asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(x), "=r"(r.i), "=r"(y), "=r"(z), "=r"(r.c), "=r"(p0), "=r"(p1), "=r"(p2)
+                 : "l"(src));
+    r.x = __uint_as_float(x);
+    r.y = __uint_as_float(y);
+    r.z = __uint_as_float(z);
+    r.pad[0] = p0;
+    r.pad[1] = p1;
+    r.pad[2] = p2;
+    return r;
+}
+
+// a4, first half: each particle to its provisional slot offsets[cell] +
+// rank.  Each lane owns a group of 4 consecutive particles (vector loads when
+// the inputs are 16-byte aligned), so four records are in flight at once.
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cell,
                                                  const uint32_t* __restrict__ rank,
                                                  const float* __restrict__ x,
                                                  const float* __restrict__ y,
                                                  const float* __restrict__ z, uint32_t n,
                                                  const uint32_t* __restrict__ offsets,
-                                                 uint32_t* __restrict__ perm_u,
-                                                 float4* __restrict__ pos_u,
-                                                 Ctrl* __restrict__ ctrl)
+                                                 Rec* __restrict__ rec, Ctrl* __restrict__ ctrl,
+                                                 int vec)
 {
     if (load_error(ctrl)) return;
     bool bad = false;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t c = cell[i], r = rank[i];
-        const float px = x[i], py = y[i], pz = z[i];
-        const uint32_t slot = offsets[c] + r;
-        if (slot < offsets[c + 1]) {
-            perm_u[slot] = i;
-            pos_u[slot] = make_float4(px, py, pz, __uint_as_float(c));
+    const uint32_t groups = (n + 3u) / 4u;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4u * g;
+        uint32_t c[4], r[4];
+        float px[4], py[4], pz[4];
+        bool valid[4];
+        if (i0 + 4u <= n) {
+            const uint4 cc = reinterpret_cast<const uint4*>(cell)[g];
+            const uint4 rr = reinterpret_cast<const uint4*>(rank)[g];
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+            r[0] = rr.x; r[1] = rr.y; r[2] = rr.z; r[3] = rr.w;
+            if (vec) {
+                const float4 a = __ldcs(reinterpret_cast<const float4*>(x) + g);
+                const float4 b = __ldcs(reinterpret_cast<const float4*>(y) + g);
+                const float4 d = __ldcs(reinterpret_cast<const float4*>(z) + g);
+                px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
+                py[0] = b.x; py[1] = b.y; py[2] = b.z; py[3] = b.w;
+                pz[0] = d.x; pz[1] = d.y; pz[2] = d.z; pz[3] = d.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    px[j] = x[i0 + j];
+                    py[j] = y[i0 + j];
+                    pz[j] = z[i0 + j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid[j] = true;
         } else {
-            bad = true;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t i = i0 + j;
+                valid[j] = i < n;
+                c[j] = valid[j] ? cell[i] : 0u;
+                r[j] = valid[j] ? rank[i] : 0u;
+                px[j] = valid[j] ? x[i] : 0.f;
+                py[j] = valid[j] ? y[i] : 0.f;
+                pz[j] = valid[j] ? z[i] : 0.f;
+            }
+        }
+        uint32_t lo[4], hi[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            lo[j] = valid[j] ? offsets[c[j]] : 0u;
+            hi[j] = valid[j] ? offsets[c[j] + 1] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!valid[j]) continue;
+            const uint32_t slot = lo[j] + r[j];
+            if (slot < hi[j]) store_rec(rec + slot, px[j], i0 + j, py[j], pz[j], c[j]);
+            else bad = true;
         }
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
 
 // a4, second half, one thread per provisional slot k.  The members of k's
-// cell sit contiguously in perm_u / pos_u, so every member read is coalesced
-// across the warp.  From them the thread computes
+// cell sit contiguously in rec, so every member read is coalesced across the
+// warp.  From them the thread computes
 //   - the stable rank: members with a smaller input index (input order
 //     inside the cell), and writes perm, sx, sy, sz at that slot;
 //   - the x-rank: members with smaller x (ties by input index), and writes
@@ -317,8 +388,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //     = members whose x-sub-bin is < b (see XSUB); byte 7 = 1 when the cell
 //     has more than 255 members, bytes 0..6 then 0 (every sub-bin starts at
 //     the cell).
-__global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ perm_u,
-                                                   const float4* __restrict__ pos_u, uint32_t n,
+__global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, uint32_t n,
                                                    Systems sy, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
                                                    float* __restrict__ sx, float* __restrict__ sy_out,
@@ -330,39 +400,46 @@ __global__ void __launch_bounds__(256) k_stabilise(const uint32_t* __restrict__ 
     bool bad = false;
     const uint32_t C = __ldg(sy.cbase + sy.S);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t i = perm_u[k];
-        const float4 pk = pos_u[k];
-        const uint32_t c = __float_as_uint(pk.w);
+        const Rec me = load_rec(rec + k);
+        const uint32_t i = me.i, c = me.c;
         if (i >= n || c >= C) { bad = true; continue; }
         const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
         if (k < s0 || k >= s1) { bad = true; continue; }
-        const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
-        const Grid& g = sy.sys[sid].g;
-        const float invs = g.inv_w[0] * (float)XSUB;
-        const int cxs = XSUB * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
-        uint32_t r = 0, xr = 0, lt[XSUB - 1] = {};
+        uint32_t r = 0, xr = 0;
         for (uint32_t q = s0; q < s1; ++q) {
-            const uint32_t j = perm_u[q];
-            const float xq = pos_u[q].x;
+            const uint2 m = *reinterpret_cast<const uint2*>(rec + q);  // (x, input index)
+            const float xq = __uint_as_float(m.x);
+            const uint32_t j = m.y;
             r += (j < i) ? 1u : 0u;
-            xr += (xq < pk.x || (xq == pk.x && j < i)) ? 1u : 0u;
-            const int sb =
-                min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
-#pragma unroll
-            for (int b = 1; b < XSUB; ++b) lt[b - 1] += sb < b ? 1u : 0u;
+            xr += (xq < me.x || (xq == me.x && j < i)) ? 1u : 0u;
         }
         const uint32_t dst = s0 + r;
         perm[dst] = i;
-        sx[dst] = pk.x;
-        sy_out[dst] = pk.y;
-        sz[dst] = pk.z;
-        P[s0 + xr] = make_float4(pk.x, pk.y, pk.z, __uint_as_float(dst));
+        sx[dst] = me.x;
+        sy_out[dst] = me.y;
+        sz[dst] = me.z;
+        P[s0 + xr] = make_float4(me.x, me.y, me.z, __uint_as_float(dst));
         if (xr == 0) {
+            // one thread per cell: where the cell's sub-bins start
             static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
-            xbins[c] = (s1 - s0 > 255u)
-                           ? make_uint2(0u, 1u << 24)
-                           : make_uint2(lt[0] | (lt[1] << 8) | (lt[2] << 16) | (lt[3] << 24),
-                                        lt[4] | (lt[5] << 8) | (lt[6] << 16));
+            uint2 word = make_uint2(0u, 1u << 24);
+            if (s1 - s0 <= 255u) {
+                const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
+                const Grid& g = sy.sys[sid].g;
+                const float invs = g.inv_w[0] * (float)XSUB;
+                const int cxs = XSUB * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
+                uint32_t lt[XSUB - 1] = {};
+                for (uint32_t q = s0; q < s1; ++q) {
+                    const float xq = rec[q].x;
+                    const int sb =
+                        min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
+#pragma unroll
+                    for (int bb = 1; bb < XSUB; ++bb) lt[bb - 1] += sb < bb ? 1u : 0u;
+                }
+                word = make_uint2(lt[0] | (lt[1] << 8) | (lt[2] << 16) | (lt[3] << 24),
+                                  lt[4] | (lt[5] << 8) | (lt[6] << 16));
+            }
+            xbins[c] = word;
         }
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
@@ -425,20 +502,21 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
 
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
                            const float* y, const float* z, uint32_t n, const uint32_t* offsets,
-                           uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s)
+                           Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
-    k_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(cell, rank, x, y, z, n, offsets,
-                                                           perm_u, pos_u, ctrl);
+    const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
+    const uint64_t groups = ((uint64_t)n + 3) / 4;
+    k_scatter<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(cell, rank, x, y, z, n, offsets, rec,
+                                                                ctrl, vec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
-                             const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
-                             float* sy_out, float* sz, float4* P, uint2* xbins, Ctrl* ctrl,
-                             int num_sms, cudaStream_t s)
+cudaError_t launch_stabilise(const Rec* rec, uint32_t n, const Systems& sy, const uint32_t* offsets,
+                             uint32_t* perm, float* sx, float* sy_out, float* sz, float4* P,
+                             uint2* xbins, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
-    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(perm_u, pos_u, n, sy, offsets, perm, sx,
-                                                             sy_out, sz, P, xbins, ctrl);
+    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(rec, n, sy, offsets, perm, sx, sy_out, sz,
+                                                             P, xbins, ctrl);
     return cudaGetLastError();
 }
 

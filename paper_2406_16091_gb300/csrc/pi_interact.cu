@@ -213,6 +213,12 @@ using Tile64 = Tile<64, 576, 14, 16>;
 using Tile128 = Tile<128, 1280, 7, SEG_CELLS>;
 using Tile256 = Tile<256, 2432, 4, SEG_CELLS>;
 
+// Sentinel slots staged after every row: the window loop reads whole groups
+// of four candidates, and up to three slots past a window's end are either
+// particles of the same row outside the window or these sentinels; the
+// pair test rejects both.
+constexpr int ROW_PAD = 3;
+
 // Lookup-table entries per row of a chunk read from global memory (mode 1:
 // one target cell, so at most 3 source cells).
 constexpr int RB_GLOBAL = 3 * XSUB + 1;
@@ -228,7 +234,7 @@ struct Plan {
     int xa, xb;
     int x1;
     int mode;   // 0: rows staged in shared memory, 1: rows read from global
-    int total;  // staged particles
+    int total;  // staged particles (without the sentinel slots)
 };
 
 template <class T>
@@ -245,8 +251,8 @@ struct Smem {
         uint32_t global[9][RB_GLOBAL];
     } tbl;
     // Per target (thread): its non-empty x-windows as byte offsets into buf,
-    // first | end << 16, plus one spare row read after the last window.
-    uint32_t win[10][T::TT];
+    // first | end << 16, plus two spare rows read after the last window.
+    uint32_t win[11][T::TT];
     Plan plan;
     SysDesc d;             // the system of the current X-row
     float t;               // its kernel scale
@@ -271,6 +277,25 @@ static_assert(fits_sm<Tile32>() && fits_sm<Tile64>() && fits_sm<Tile128>() && fi
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory loads by 32-bit shared-window address.  The "memory"
+// clobber keeps them after the C++ stores that wrote the data.
+__device__ __forceinline__ float4 lds_f4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
@@ -357,7 +382,7 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
                 staged += a.offsets[cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + xb + 1] -
                           rstart[r];
             }
-            fits = staged <= (uint32_t)T::CAP;
+            fits = staged + 9u * ROW_PAD <= (uint32_t)T::CAP;
             valid = fits && targets <= (uint32_t)T::TT;
         }
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
@@ -381,18 +406,24 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
             len = a.offsets[rb + xb + 1] - gb;
         }
     }
-    uint32_t incl = len;
+    // staged rows follow each other with ROW_PAD sentinel slots after each
+    const uint32_t slots = lane < 9 ? len + ROW_PAD : 0u;
+    uint32_t incl = slots, tot = len;
 #pragma unroll
     for (int o = 1; o < 16; o <<= 1) {
         const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += v;
+        const uint32_t u = __shfl_up_sync(0xffffffffu, tot, o);
+        if (lane >= (unsigned)o) {
+            incl += v;
+            tot += u;
+        }
     }
     if (lane < 9) {
         p.gbeg[lane] = gb;
         p.rlen[lane] = (int)len;
-        p.sbeg[lane] = (int)(incl - len);
+        p.sbeg[lane] = (int)(incl - slots);
     }
-    if (lane == 8) p.total = (int)incl;
+    if (lane == 8) p.total = (int)tot;
     if (lane == 0) {
         p.xa = xa;
         p.xb = xb;
@@ -401,45 +432,86 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
     }
 }
 
+// A particle far from every other one (finite coordinates, so its pair
+// terms are exact zeros).
+__device__ __forceinline__ float4 sentinel()
+{
+    return make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
+}
+
+// The sentinel slots after the staged rows of a chunk (one warp).
+__device__ __forceinline__ void write_row_pads(float4* buf, const Plan& p, unsigned lane)
+{
+    if (lane < 9u * ROW_PAD) {
+        const int rr = (int)lane / ROW_PAD;
+        buf[p.sbeg[rr] + p.rlen[rr] + (int)lane % ROW_PAD] = sentinel();
+    }
+}
+
 // Lookup table of one chunk, built from the offsets and the per-cell
 // sub-bin starts (no staged data needed, so it overlaps the bulk copies).
-// Warps take rows, lanes take cells; rows without particles (or outside the
-// grid) get all-zero entries, i.e. empty windows.
-template <int NW, class E, int RB>
+// The NT threads share the (row, cell) items; every thread first issues the
+// loads of all its items, then writes them, so the loads overlap.  Rows
+// without particles (or outside the grid) get all-zero entries, i.e. empty
+// windows.
+template <int NT, class E, int RB>
 __device__ __forceinline__ void build_table(const InteractArgs& a, const SysDesc& d, const Plan& p,
                                             int cy, int cz, int ncell, E (*tbl)[RB],
-                                            uint32_t* coarse_mask, unsigned warp, unsigned lane)
+                                            uint32_t* coarse_mask, unsigned t)
 {
+    constexpr int MAXC = RB / XSUB + 1;              // bound of ncell + 1
+    constexpr int MAXI = (9 * MAXC + NT - 1) / NT;   // items per thread
     const int nx = d.g.n[0], ny = d.g.n[1];
-    for (int rr = (int)warp; rr < 9; rr += NW) {
-        const int len = p.rlen[rr];
-        const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
-        const uint32_t rb = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + p.xa;
-        // mode 0: staged index = sbeg + (P index - gbeg); mode 1: P index
-        const uint32_t shift = sizeof(E) == 2 ? (uint32_t)p.sbeg[rr] - p.gbeg[rr] : 0u;
-        for (int k = (int)lane; k <= ncell; k += 32) {
-            E* e = &tbl[rr][XSUB * k];
-            if (len == 0) {
-                if (k == ncell) e[0] = 0;
-                else
+    const int per = ncell + 1, total = 9 * per;
+    const float inv = 1.0f / (float)per;
+    uint32_t start[MAXI];
+    uint2 w[MAXI];
 #pragma unroll
-                    for (int b = 0; b < XSUB; ++b) e[b] = 0;
-                continue;
-            }
-            const uint32_t start = a.offsets[rb + k] + shift;
-            if (k == ncell) {
-                e[0] = (E)start;
-                continue;
-            }
-            const uint2 w = a.xbins[rb + k];
-            if (w.y >> 24) atomicOr(coarse_mask, 1u << rr);
-            e[0] = (E)start;
+    for (int i = 0; i < MAXI; ++i) {
+        const int e = (int)t + i * NT;
+        // e / per in FP32: (e + 1/2) / per is at least 1/(2 per) from an integer
+        const int rr = (int)(((float)e + 0.5f) * inv), k = e - rr * per;
+        start[i] = 0u;
+        w[i] = make_uint2(0u, 0u);
+        if (e < total && p.rlen[rr] > 0) {
+            const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
+            const uint32_t cidx =
+                d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + p.xa + k;
+            // mode 0: staged index = sbeg + (P index - gbeg); mode 1: P index
+            const uint32_t shift = sizeof(E) == 2 ? (uint32_t)p.sbeg[rr] - p.gbeg[rr] : 0u;
+            start[i] = a.offsets[cidx] + shift;
+            if (k < ncell) w[i] = a.xbins[cidx];
+        }
+    }
 #pragma unroll
-            for (int b = 1; b < XSUB; ++b) {
-                const uint32_t word = b <= 4 ? w.x : w.y;
-                const uint32_t cnt = (word >> (8 * ((b - 1) & 3))) & 255u;
-                e[b] = (E)(start + cnt);
-            }
+    for (int i = 0; i < MAXI; ++i) {
+        const int e = (int)t + i * NT;
+        if (e >= total) break;
+        const int rr = (int)(((float)e + 0.5f) * inv), k = e - rr * per;
+        E* ent = &tbl[rr][XSUB * k];
+        if (k == ncell) {
+            ent[0] = (E)start[i];
+            continue;
+        }
+        if (w[i].y >> 24) atomicOr(coarse_mask, 1u << rr);
+        E v[XSUB];
+        v[0] = (E)start[i];
+#pragma unroll
+        for (int b = 1; b < XSUB; ++b) {
+            const uint32_t word = b <= 4 ? w[i].x : w[i].y;
+            v[b] = (E)(start[i] + ((word >> (8 * ((b - 1) & 3))) & 255u));
+        }
+        if constexpr (sizeof(E) == 2) {
+            static_assert(XSUB == 8 && RB % 8 == 0, "one 16-byte store per cell");
+            uint4 q;
+            q.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+            q.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+            q.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+            q.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+            *reinterpret_cast<uint4*>(ent) = q;
+        } else {
+#pragma unroll
+            for (int b = 0; b < XSUB; ++b) ent[b] = v[b];
         }
     }
 }
@@ -645,37 +717,42 @@ __device__ __forceinline__ void target_sums_staged(const float4* buf, const uint
     PackedSums ps;
     if constexpr (packed_path<Acc, KERNEL>()) {
         const float2 ks = make_float2(kp.t, kp.t);
-        // byte offsets: candidates from buf[0], window words from this
-        // thread's first one
-        const char* cb = reinterpret_cast<const char*>(buf);
-        const char* wb = reinterpret_cast<const char*>(&win[0][tid]);
-        constexpr uint32_t SENT = (uint32_t)CAP * 16u, WSTEP = (uint32_t)WT * 4u;
-        uint32_t wo = 0;
-        const uint32_t woe = (uint32_t)nw * WSTEP;
-        uint32_t w = *reinterpret_cast<const uint32_t*>(wb);
-        uint32_t c = w & 0xffffu, ce = w >> 16;
-        // The window switch is written as selects so that no lane waits for
-        // the others at the end of a window: a lane leaves only after its
-        // last window.  Four candidates per trip, in two packed pairs; slots
-        // past the window's end read the sentinel, so the pairs and their
-        // order are those of the two-at-a-time loop.
+        // the row after the last window: a valid address for the last
+        // prefetch (its data is never used)
+        win[nw][tid] = 0u;
+        // shared-window addresses: candidates, this thread's window words
+        const uint32_t cb = smem_addr(buf), wb = smem_addr(&win[0][tid]);
+        constexpr uint32_t WSTEP = (uint32_t)WT * 4u;
+        const uint32_t we = wb + (uint32_t)nw * WSTEP;
+        uint32_t wa = wb;
+        const uint32_t w0 = lds_u32(wa);
+        uint32_t wnext = lds_u32(wa + WSTEP);
+        uint32_t c = cb + (w0 & 0xffffu), ce = cb + (w0 >> 16);
+        float4 s0 = lds_f4(c), s1 = lds_f4(c + 16u), s2 = lds_f4(c + 32u), s3 = lds_f4(c + 48u);
+        // All windows in one loop with the switch written as selects, so no
+        // lane waits for the others at the end of a window (a lane leaves
+        // after its last one).  Four candidates per trip in two packed pairs;
+        // the up to three slots read past a window's end (same row outside
+        // the window, or the row's sentinel slots) add exact zeros, so the
+        // sums are those of the two-at-a-time loop.  Each trip loads the next
+        // trip's candidates and window word before its own arithmetic.
         do {
-            const uint32_t c1 = c + 16u < ce ? c + 16u : SENT;
-            const uint32_t c2 = c + 32u < ce ? c + 32u : SENT;
-            const uint32_t c3 = c + 48u < ce ? c + 48u : SENT;
-            const float4 s0 = *reinterpret_cast<const float4*>(cb + c);
-            const float4 s1 = *reinterpret_cast<const float4*>(cb + c1);
-            const float4 s2 = *reinterpret_cast<const float4*>(cb + c2);
-            const float4 s3 = *reinterpret_cast<const float4*>(cb + c3);
+            const uint32_t cc = c + 64u;
+            const bool sw = cc >= ce;
+            const uint32_t cn = sw ? cb + (wnext & 0xffffu) : cc;
+            const uint32_t cen = sw ? cb + (wnext >> 16) : ce;
+            wa += sw ? WSTEP : 0u;
+            const float4 n0 = lds_f4(cn), n1 = lds_f4(cn + 16u), n2 = lds_f4(cn + 32u), n3 = lds_f4(cn + 48u);
+            wnext = lds_u32(wa + WSTEP);
             ps.pair2u(s0, s1, xt, yt, zt, rc2, ks);
             ps.pair2u(s2, s3, xt, yt, zt, rc2, ks);
-            c += 64u;
-            const bool sw = c >= ce;
-            wo += sw ? WSTEP : 0u;
-            const uint32_t wn = *reinterpret_cast<const uint32_t*>(wb + wo);
-            c = sw ? (wn & 0xffffu) : c;
-            ce = sw ? (wn >> 16) : ce;
-        } while (wo < woe);
+            s0 = n0;
+            s1 = n1;
+            s2 = n2;
+            s3 = n3;
+            c = cn;
+            ce = cen;
+        } while (wa < we);
         finish_packed(ps, r);
     } else {
         for (int k = 0; k < nw; ++k) {
@@ -719,7 +796,7 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
 
     if (tid == 0) {
         sm.failed = 0;
-        sm.buf[T::CAP] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
+        sm.buf[T::CAP] = sentinel();
         bar_init(&sm.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -763,6 +840,7 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
                 if (lane == 0) sm.coarse_mask = 0u;
                 plan_chunk<T>(a, d, sm.plan, x0, xe, cy, cz, lane);
                 __syncwarp();
+                if (sm.plan.mode == 0) write_row_pads(sm.buf, sm.plan, lane);
                 if (lane == 0 && sm.plan.mode == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_expect_tx(&sm.bar, (uint32_t)sm.plan.total * 16u);
@@ -778,9 +856,9 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             const int ncell = p.xb - p.xa + 1;
             // lookup tables, built while the bulk copies are in flight
             if (mode == 0)
-                build_table<T::TT / 32>(a, d, p, cy, cz, ncell, sm.tbl.staged, &sm.coarse_mask, warp, lane);
+                build_table<T::TT>(a, d, p, cy, cz, ncell, sm.tbl.staged, &sm.coarse_mask, tid);
             else
-                build_table<T::TT / 32>(a, d, p, cy, cz, ncell, sm.tbl.global, &sm.coarse_mask, warp, lane);
+                build_table<T::TT>(a, d, p, cy, cz, ncell, sm.tbl.global, &sm.coarse_mask, tid);
             if (mode == 0) {
                 if (!bar_wait_bounded(&sm.bar, phase, a.wait_limit_ns)) {
                     sm.failed = 1;
@@ -869,7 +947,7 @@ struct WsStage {
 template <class T>
 struct WsSmem {
     WsStage<T> st[T::NS];
-    uint32_t win[10][32 * T::W];  // per consumer thread: its windows (see target_sums_staged)
+    uint32_t win[11][32 * T::W];  // per consumer thread: its windows (see target_sums_staged)
     int failed;
 };
 
@@ -952,6 +1030,7 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
             __syncwarp();
             const Plan& p = st.plan;
             const int x1 = p.x1, mode = p.mode, ncell = p.xb - p.xa + 1;
+            if (mode == 0) write_row_pads(st.buf, p, lane);
             if (lane == 0 && mode == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 bar_expect_tx_only(&st.full, (uint32_t)p.total * 16u);
@@ -962,9 +1041,9 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
             last_use[s] = (int)u;
             copies[s] = mode == 0;
             if (mode == 0) {
-                build_table<1>(a, d, p, cy, cz, ncell, st.tbl.staged, &st.coarse_mask, 0u, lane);
+                build_table<32>(a, d, p, cy, cz, ncell, st.tbl.staged, &st.coarse_mask, lane);
             } else {
-                build_table<1>(a, d, p, cy, cz, ncell, st.tbl.global, &st.coarse_mask, 0u, lane);
+                build_table<32>(a, d, p, cy, cz, ncell, st.tbl.global, &st.coarse_mask, lane);
             }
             if (lane == 0) {
                 const uint32_t tb = a.offsets[rb0 + x0];
@@ -1053,7 +1132,7 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
         if (blockIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
         sm.failed = load_error(a.ctrl) != 0u;
         for (int s = 0; s < T::NS; ++s) {
-            sm.st[s].buf[T::CAP] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
+            sm.st[s].buf[T::CAP] = sentinel();
             bar_init(&sm.st[s].full, 32);
             bar_init(&sm.st[s].empty, 32 * T::W);
         }
@@ -1110,12 +1189,11 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
-    using TD = Tile32;
-    static_assert(DEFAULT_TILE == 0, "the comparator kernels use the default shape");
+    static_assert(DEFAULT_TILE == 4, "the comparator kernels use the default shape");
     switch (a.kernel) {
-        case KERNEL_LJ: launch_tiled_one<TD, Acc, KERNEL_LJ>(a, g, s); break;
-        case KERNEL_LOWFLOP: launch_tiled_one<TD, Acc, KERNEL_LOWFLOP>(a, g, s); break;
-        case KERNEL_HIGHFLOP: launch_tiled_one<TD, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
+        case KERNEL_LJ: launch_ws_one<Ws4, Acc, KERNEL_LJ>(a, g, s); break;
+        case KERNEL_LOWFLOP: launch_ws_one<Ws4, Acc, KERNEL_LOWFLOP>(a, g, s); break;
+        case KERNEL_HIGHFLOP: launch_ws_one<Ws4, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
         default:
             switch (tile) {
                 case 0: launch_tiled_one<Tile32, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
@@ -1169,7 +1247,17 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
     if ((e = occupancy_of<Tile128, Acc>(&per_sm[2])) != cudaSuccess) return e;
     if ((e = occupancy_of<Tile256, Acc>(&per_sm[3])) != cudaSuccess) return e;
     if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[4])) != cudaSuccess) return e;
-    return ws_occupancy_of<Ws8, Acc>(&per_sm[5]);
+    if ((e = ws_occupancy_of<Ws8, Acc>(&per_sm[5])) != cudaSuccess) return e;
+    // the comparator kernels run with the default shape: allow its shared memory
+    constexpr int bytes = (int)sizeof(WsSmem<Ws4>);
+    if ((e = cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_LJ>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_LOWFLOP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_HIGHFLOP>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t tiled_occupancy(bool kahan, int* per_sm)

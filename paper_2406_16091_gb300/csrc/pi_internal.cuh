@@ -16,8 +16,8 @@
 //   sys[S], cbase[S+1], wbase[S+1], kscale[S]   per-system constants
 //   cell[n_max]     cell of each input particle            (binning scratch)
 //   rank[n_max]     provisional slot inside its cell        (binning scratch)
-//   perm_u[n_max]   unstable slot -> input index            (binning scratch)
-//   pos_u[n_max]    float4 (x, y, z, cell) in unstable slot order (binning scratch)
+//   rec[n_max]      32-byte Rec per particle in unstable slot order (binning
+//                   scratch): one full DRAM sector per random write
 //   perm[n_max]     stable   slot -> input index
 //   sx, sy, sz      positions in sorted order
 //   P[n_max]        float4 (x, y, z, stable slot): sorted order, and inside
@@ -138,6 +138,19 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// One particle in provisional (unstable) slot order: position, input index
+// and cell.  32 bytes, aligned, so that the scatter writes whole DRAM
+// sectors; x and the input index come first, the pair the stable ranking
+// compares.
+struct __align__(32) Rec {
+    float x;
+    uint32_t i;
+    float y, z;
+    uint32_t c;
+    uint32_t pad[3];
+};
+static_assert(sizeof(Rec) == 32, "one DRAM sector per record");
+
 // Parameters of k_zero: clear [p, p + n_words), then write the S + 1
 // particle bases of this step.
 template <int NB>
@@ -160,8 +173,8 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         uint64_t wait_limit_ns, int withhold_first, cudaStream_t s);
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
                            const float* y, const float* z, uint32_t n, const uint32_t* offsets,
-                           uint32_t* perm_u, float4* pos_u, Ctrl* ctrl, int num_sms, cudaStream_t s);
-cudaError_t launch_stabilise(const uint32_t* perm_u, const float4* pos_u, uint32_t n,
+                           Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s);
+cudaError_t launch_stabilise(const Rec* rec, uint32_t n,
                              const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
                              float* sy_out, float* sz, float4* P, uint2* xbins, Ctrl* ctrl,
                              int num_sms, cudaStream_t s);
@@ -217,7 +230,7 @@ cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms,
 // 4, 5 = warp-specialised, 4 or 8 consumer warps; per_sm[tile] = resident
 // CTAs.
 constexpr int NUM_TILES = 6;
-constexpr int DEFAULT_TILE = 0;
+constexpr int DEFAULT_TILE = 4;
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
                                   int tile, cudaStream_t s, int* launches);
 // Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[NUM_TILES]).

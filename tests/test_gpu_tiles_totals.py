@@ -39,10 +39,20 @@ def test_tile_shapes_identical_and_autotune(name):
             for a, b in zip(res[0], r):
                 assert np.array_equal(a, b)
         chosen, ms = B.pi_autotune(ctx, [w.h], *out, nb, B.PI_ORDER_SORTED, 2, s)
-        assert chosen in range(B.PI_NUM_TILES) and all(m > 0 for m in ms)
+        assert len(ms) == B.PI_NUM_TILES + 1
+        assert chosen in range(B.PI_NUM_TILES + 1) and all(m > 0 for m in ms)
         assert ms[chosen] == min(ms)
-        for a, b in zip(res[0], [o.cpu().numpy().view(np.uint32) for o in out + [nb]]):
-            assert np.array_equal(a, b)
+        # the chosen candidate stays in use
+        B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+        got = [o.cpu().numpy().view(np.uint32) for o in out + [nb]]
+        if chosen < B.PI_NUM_TILES:
+            for a, b in zip(res[0], got):
+                assert np.array_equal(a, b)
+        else:  # Alg. 1: same counts, sums within rounding
+            assert np.array_equal(res[0][4], got[4])
+            for a, b in zip(res[0][:4], got[:4]):
+                fa, fb = a.view(np.float32), b.view(np.float32)
+                assert np.allclose(fa, fb, rtol=1e-4, atol=1e-6)
         B.pi_sync_status(ctx, s)
     finally:
         B.pi_destroy(ctx)
