@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from paper_2406_16091_gb300 import replicas  # noqa: E402
 from paper_2406_16091_gb300 import workloads as W  # noqa: E402
 
 METRIC = "within-cutoff pair interactions/s"
@@ -58,7 +59,7 @@ def parse():
                    help="tile shape of the tiled interaction (auto: pi_autotune during warm-up)")
     p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
                    default="none", help="run one of the extra studies instead of the main line")
-    p.add_argument("--jobs", type=int, default=400, help="serving study: number of jobs")
+    p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
     return p.parse_args()
 
 
@@ -245,7 +246,7 @@ def run_ours(args):
 
     w = W.WORKLOADS[args.workload]
     # replicas: each rank runs its own independent system of the same shape
-    x, y, z = W.uniform(w.n, w.seed + 1000 * rank) if w.layout == "uniform" and rank else w.positions()
+    x, y, z = replicas.replica_positions(w, rank)
     n = w.n
     s = torch.cuda.current_stream()
     ctx = B.pi_create(w.lo, w.hi, w.rc, n)
@@ -309,19 +310,8 @@ def run_ours(args):
     t_bin = [e[0].elapsed_time(e[1]) * 1e-3 for e in ev]
     t_int = [e[1].elapsed_time(e[2]) * 1e-3 for e in ev]
     dev_time = sum(t_step)
-    if ws > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([dev_time], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_time_max = float(tt.item())
-        pt = torch.tensor([pairs], dtype=torch.float64, device=dev)
-        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
-        pairs_all = float(pt.item())
-    else:
-        dev_time_max = dev_time
-        pairs_all = float(pairs)
-    value = pairs_all * K / dev_time_max
+    dev_time_max, pairs_all = replicas.aggregate(dev_time, pairs, dev)
+    value = replicas.job_rate(pairs_all, K, dev_time_max)
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     e2e = None
@@ -337,18 +327,8 @@ def run_ours(args):
             B.pi_run_host(ctx, hx, hy, hz, n, w.h, *hout, hnb, B.PI_ORDER_SORTED, s)
             te.append(time.perf_counter() - t0)
         e2e_pairs = int(hnb.numpy().astype(np.int64).sum())
-        t_e2e = sum(te)
-        if ws > 1:
-            import torch.distributed as dist
-
-            tt = torch.tensor([t_e2e, float(e2e_pairs)], dtype=torch.float64, device=dev)
-            mx = tt.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-            t_e2e, e2e_pairs_all = float(mx[0]), float(tt[1])
-        else:
-            e2e_pairs_all = float(e2e_pairs)
-        e2e = {"value": e2e_pairs_all * args.e2e_steps / t_e2e, "unit": UNIT,
+        t_e2e, e2e_pairs_all = replicas.aggregate(sum(te), e2e_pairs, dev)
+        e2e = {"value": replicas.job_rate(e2e_pairs_all, args.e2e_steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 3 * 4 * n, "d2h_bytes_per_step": 5 * 4 * n,
                "ms_per_step": 1e3 * t_e2e / args.e2e_steps, "steps": args.e2e_steps,
                "api": "pi_run_host (pinned host buffers)"}
@@ -366,7 +346,10 @@ def run_ours(args):
     mean_int = statistics.fmean(t_int)
     achieved = FLOP_PER_PAIR * pairs / mean_int / 1e12
     src = os.path.join(ROOT, "paper_2406_16091_gb300", "csrc")
-    kname = "k_interact_tiled" if args.algo == "tiled" else "k_interact_ppnl"
+    if args.algo != "tiled":
+        kname = "k_interact_ppnl"
+    else:
+        kname = "k_interact_ws" if tile in (4, 5) else "k_interact_tiled"
     traffic = recorded_traffic(kname, source_hash([os.path.join(src, "pi_interact.cu"),
                                                    os.path.join(src, "pi_internal.cuh")]))
     roofline = {
@@ -394,14 +377,19 @@ def run_ours(args):
         import oracle
 
         oracle.build()
-        t0 = time.perf_counter()
-        b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
-        r = oracle.interact(b, w.rc, w.h)
-        t_cpu = time.perf_counter() - t0
-        cpu = {"value": int(r.nbr.sum()) / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
+        # whole oracle steps on the same particles, repeated for about 10 s
+        reps, t_cpu, cpu_pairs = 0, 0.0, 0
+        while reps == 0 or t_cpu < 10.0:
+            t0 = time.perf_counter()
+            b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
+            r = oracle.interact(b, w.rc, w.h)
+            t_cpu += time.perf_counter() - t0
+            cpu_pairs += int(r.nbr.sum())
+            reps += 1
+        cpu = {"value": cpu_pairs / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
                "kind": "oracle",
-               "sample": f"one full step (bin + interact) of the {w.name} workload, "
-                         f"{n} particles, FP64 oracle, {t_cpu:.2f} s"}
+               "sample": f"{reps} full steps (bin + interact) of the {w.name} workload, "
+                         f"{n} particles each, FP64 oracle, {t_cpu:.1f} s in all"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -603,10 +591,12 @@ def study_serving(args):
 
     specs = W.serving_jobs(args.jobs)
     t0 = time.perf_counter()
+    pool = {k: [torch.from_numpy(a).pin_memory() for a in v] for k, v in W.serving_pool().items()}
     jobs = []
     for k, sp in enumerate(specs):
-        x, y, z = sp.positions()
-        jobs.append(make_job(k, x, y, z, sp.lo, sp.hi, sp.rc, sp.h))
+        x, y, z = (a[: sp.n] for a in pool[sp.layout])
+        # results of every 500th job are kept; the others land in slot buffers
+        jobs.append(make_job(k, x, y, z, sp.lo, sp.hi, sp.rc, sp.h, outputs=k % 500 == 0))
     t_gen = time.perf_counter() - t0
     srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=8)
     res = {"study": "serving", "jobs": len(jobs), "particles": sum(j.n for j in jobs),
@@ -621,6 +611,26 @@ def study_serving(args):
             j.arrival = 0.0
         cap = srv.run(jobs)
         res["capacity"] = cap
+        # the plain queue: the same jobs one after another, each a blocking
+        # pi_run_host on one context sized for the largest job
+        ctx = B.pi_create((0, 0, 0), (1, 1, 1), W.rc_for_cells(int(round(
+            max(j.cells for j in jobs) ** (1 / 3))) + 1), max(j.n for j in jobs))
+        try:
+            hout = [torch.empty(max(j.n for j in jobs)).pin_memory() for _ in range(4)]
+            hnb = torch.empty(max(j.n for j in jobs), dtype=torch.int32).pin_memory()
+            s0 = torch.cuda.current_stream()
+            B.pi_run_host(ctx, hout[0], hout[0], hout[0], 0, 0.5, *hout, hnb, B.PI_ORDER_ORIGINAL, s0)
+            t1 = time.perf_counter()
+            for j in jobs:
+                B.pi_reconfigure(ctx, j.lo, j.hi, j.rc, s0)
+                B.pi_run_host(ctx, j.x, j.y, j.z, j.n, j.h, *hout, hnb, B.PI_ORDER_ORIGINAL, s0)
+            t_plain = time.perf_counter() - t1
+        finally:
+            B.pi_destroy(ctx)
+        res["plain_sequential"] = {"jobs_per_s": len(jobs) / t_plain,
+                                   "particles_per_s": sum(j.n for j in jobs) / t_plain,
+                                   "makespan_s": t_plain}
+        res["speedup_vs_plain"] = cap["jobs_per_s"] / res["plain_sequential"]["jobs_per_s"]
         rng = np.random.default_rng(1005)
         for frac in (0.5, 0.8, 0.95):
             rate = frac * cap["jobs_per_s"]

@@ -115,7 +115,7 @@ enum { PI_KERNEL_GAUSSIAN = 0, PI_KERNEL_LJ = 1, PI_KERNEL_LOWFLOP = 2, PI_KERNE
  *         (Sec. 3); C = nx*ny*nz must stay below 2^31.
  *   n_max largest particle count a later pi_bin may pass, 0 <= n_max < 2^31 - 64.
  *   out   receives the context; the caller owns it and frees it with pi_destroy.
- * Allocates all device buffers once (about 28 B per particle + 8 B per cell).
+ * Allocates all device buffers once (about 72 B per particle + 28 B per cell).
  * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA. */
 pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out);
 
@@ -173,6 +173,22 @@ pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, floa
 pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
                       int64_t n, float h, float* hS, float* hVx, float* hVy, float* hVz,
                       uint32_t* hnbr, int out_order, pi_stream stream);
+
+/* One job of a request loop, enqueued without waiting: re-targets the
+ * context to (box, r_c) when they differ from its current ones (as
+ * pi_reconfigure: the new grid must fit the context), copies the n host
+ * positions into the context's device staging buffers, runs pi_bin and
+ * pi_interact, and copies the outputs back into the host arrays -- all on
+ * `stream`, in that order, nothing synchronised.  The host arrays must stay
+ * valid and untouched until the stream reaches this point (record an event
+ * after the call); pinned memory makes the copies asynchronous.  The staging
+ * buffers are allocated on the first pi_run_host / pi_submit_host call of a
+ * context (a warm-up call keeps that out of a request loop).  Device-side
+ * errors surface in pi_sync_status.  Errors returned at once: those of
+ * pi_reconfigure, pi_bin and pi_interact, PI_ERR_NOMEM. */
+pi_status pi_submit_host(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
+                         const float* hz, int64_t n, float h, float* hS, float* hVx, float* hVy,
+                         float* hVz, uint32_t* hnbr, int out_order, pi_stream stream);
 
 /* ---- Batches: many independent systems per context --------------------
  *

@@ -84,6 +84,7 @@ def load():
         "pi_bin": ([P, P, P, P, i64, P], i32),
         "pi_interact": ([P, f32, P, P, P, P, P, i32, P], i32),
         "pi_run_host": ([P, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
+        "pi_submit_host": ([P, ctypes.POINTER(PiBox), f32, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
         "pi_grid": ([P, P], i32),
         "pi_binned": ([P] + [ctypes.POINTER(P)] * 6, i32),
         "pi_copy_binned": ([P, P, P, P, P, P, P, P], i32),
@@ -213,6 +214,16 @@ def pi_run_host(ctx, x, y, z, n: int, h: float, S, Vx, Vy, Vz, nbr=None,
     return _check(load().pi_run_host(ctx, _ptr(x), _ptr(y), _ptr(z), int(n), float(h), _ptr(S),
                                      _ptr(Vx), _ptr(Vy), _ptr(Vz), _ptr(nbr), int(out_order),
                                      _stream(stream)), "pi_run_host")
+
+
+def pi_submit_host(ctx, lo, hi, r_c: float, x, y, z, n: int, h: float, S, Vx, Vy, Vz, nbr=None,
+                   out_order: int = PI_ORDER_ORIGINAL, stream=None) -> None:
+    """One job from host arrays to host arrays, enqueued on `stream` without
+    waiting (re-targets the context to the box and cutoff first if needed)."""
+    box = PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi))
+    _check(load().pi_submit_host(ctx, ctypes.byref(box), float(r_c), _ptr(x), _ptr(y), _ptr(z), int(n),
+                                 float(h), _ptr(S), _ptr(Vx), _ptr(Vy), _ptr(Vz), _ptr(nbr),
+                                 int(out_order), _stream(stream)), "pi_submit_host")
 
 
 def pi_grid(ctx):

@@ -709,31 +709,31 @@ pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)
     return PI_OK;
 }
 
-pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz, int64_t n,
-                      float h, float* hS, float* hVx, float* hVy, float* hVz, uint32_t* hnbr,
-                      int out_order, pi_stream stream)
+// Device staging buffers of the host-memory entry points (allocated on the
+// first call: n_max entries for x, y, z, S, Vx, Vy, Vz, nbr).
+static pi_status ensure_io(pi_ctx* ctx)
 {
-    if (!ctx) return PI_ERR_INVALID_ARG;
-    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
-    if (n < 0) return PI_ERR_INVALID_ARG;
-    if (n > ctx->n_max[0]) return PI_ERR_CAPACITY;
-    if (n > 0 && (!hx || !hy || !hz || !hS || !hVx || !hVy || !hVz)) return PI_ERR_INVALID_ARG;
-    DeviceScope ds(ctx->device);
-    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_run_host: set device");
-    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->io) return PI_OK;
     const size_t nm = (size_t)ctx->n_max_total + 4;
-    if (!ctx->io) {
-        PI_TRY(cudaMalloc(&ctx->io, nm * 8 * sizeof(float)));
-        float* f = (float*)ctx->io;
-        ctx->io_x = f;
-        ctx->io_y = f + nm;
-        ctx->io_z = f + 2 * nm;
-        ctx->io_S = f + 3 * nm;
-        ctx->io_Vx = f + 4 * nm;
-        ctx->io_Vy = f + 5 * nm;
-        ctx->io_Vz = f + 6 * nm;
-        ctx->io_nbr = (uint32_t*)(f + 7 * nm);
-    }
+    PI_TRY(cudaMalloc(&ctx->io, nm * 8 * sizeof(float)));
+    float* f = (float*)ctx->io;
+    ctx->io_x = f;
+    ctx->io_y = f + nm;
+    ctx->io_z = f + 2 * nm;
+    ctx->io_S = f + 3 * nm;
+    ctx->io_Vx = f + 4 * nm;
+    ctx->io_Vy = f + 5 * nm;
+    ctx->io_Vz = f + 6 * nm;
+    ctx->io_nbr = (uint32_t*)(f + 7 * nm);
+    return PI_OK;
+}
+
+// The asynchronous body of pi_run_host / pi_submit_host.
+static pi_status host_step(pi_ctx* ctx, const float* hx, const float* hy, const float* hz, int64_t n,
+                           float h, float* hS, float* hVx, float* hVy, float* hVz, uint32_t* hnbr,
+                           int out_order, pi_stream stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * sizeof(float);
     if (n > 0) {
         PI_TRY(cudaMemcpyAsync(ctx->io_x, hx, bytes, cudaMemcpyHostToDevice, s));
@@ -752,7 +752,50 @@ pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float
         PI_TRY(cudaMemcpyAsync(hVz, ctx->io_Vz, bytes, cudaMemcpyDeviceToHost, s));
         if (hnbr) PI_TRY(cudaMemcpyAsync(hnbr, ctx->io_nbr, bytes, cudaMemcpyDeviceToHost, s));
     }
+    return PI_OK;
+}
+
+static pi_status host_args_ok(const pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
+                              int64_t n, const float* hS, const float* hVx, const float* hVy,
+                              const float* hVz)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (ctx->S != 1) return PI_ERR_INVALID_ARG;
+    if (n < 0) return PI_ERR_INVALID_ARG;
+    if (n > ctx->n_max[0]) return PI_ERR_CAPACITY;
+    if (n > 0 && (!hx || !hy || !hz || !hS || !hVx || !hVy || !hVz)) return PI_ERR_INVALID_ARG;
+    return PI_OK;
+}
+
+pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz, int64_t n,
+                      float h, float* hS, float* hVx, float* hVy, float* hVz, uint32_t* hnbr,
+                      int out_order, pi_stream stream)
+{
+    pi_status st = host_args_ok(ctx, hx, hy, hz, n, hS, hVx, hVy, hVz);
+    if (st != PI_OK) return st;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_run_host: set device");
+    if ((st = ensure_io(ctx)) != PI_OK) return st;
+    st = host_step(ctx, hx, hy, hz, n, h, hS, hVx, hVy, hVz, hnbr, out_order, stream);
+    if (st != PI_OK) return st;
     return pi_sync_status(ctx, stream, nullptr);
+}
+
+pi_status pi_submit_host(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
+                         const float* hz, int64_t n, float h, float* hS, float* hVx, float* hVy,
+                         float* hVz, uint32_t* hnbr, int out_order, pi_stream stream)
+{
+    pi_status st = host_args_ok(ctx, hx, hy, hz, n, hS, hVx, hVy, hVz);
+    if (st != PI_OK) return st;
+    if (!box) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_submit_host: set device");
+    if ((st = ensure_io(ctx)) != PI_OK) return st;
+    const pi_box& cur = ctx->boxes[0];
+    bool same = r_c == ctx->rc[0];
+    for (int d = 0; d < 3; ++d) same = same && box->lo[d] == cur.lo[d] && box->hi[d] == cur.hi[d];
+    if (!same && (st = pi_reconfigure(ctx, box, r_c, stream)) != PI_OK) return st;
+    return host_step(ctx, hx, hy, hz, n, h, hS, hVx, hVy, hVz, hnbr, out_order, stream);
 }
 
 }  // extern "C"

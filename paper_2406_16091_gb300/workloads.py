@@ -17,6 +17,13 @@ that structure at GB300 sizes:
 * ``clustered``  N = 4,194,304: 10 % uniform background, 90 % split evenly over
                  64 isotropic Gaussian clusters (sigma 0.03, uniform centres),
                  r_c = 1/128; samples outside [0,1)^3 are drawn again.
+* ``batched_systems``  256 independent systems, N log-uniform in [1024,
+                 262144], each uniform in its own unit box with a mean
+                 occupancy uniform in [2, 16] (cells per axis max(3,
+                 round(cbrt(N / occupancy)))).
+* ``serving_jobs``  10,000 jobs, N log-uniform in [1024, 1048576], occupancy
+                 in {2, 4, 8, 16}, half uniform and half clustered; their
+                 particles come from ``serving_pool``.
 
 The kernel width is h = r_c / 2 everywhere.
 """
@@ -166,6 +173,14 @@ def batched_systems(count: int = 256, seed: int = 1004, n_lo: int = 1024, n_hi: 
     ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
     ppc = rng.uniform(ppc_lo, ppc_hi, count)
     return [_system_for(int(ns[k]), float(ppc[k]), seed * 1000 + k) for k in range(count)]
+
+
+def serving_pool(n: int = 1048576, seed: int = 1006):
+    """Positions the serving jobs draw from: one uniform and one clustered
+    set of ``n`` particles in [0,1)^3.  A job of N particles takes the first N
+    of its layout's set -- a random sample of that layout, since both sets are
+    in random order -- so that 10,000 jobs need no 10,000 separate draws."""
+    return {"uniform": uniform(n, seed), "clustered": clustered(n, seed + 1)}
 
 
 def serving_jobs(count: int = 10000, seed: int = 1005, n_lo: int = 1024, n_hi: int = 1048576):

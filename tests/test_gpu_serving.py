@@ -96,3 +96,27 @@ def test_memory_budget_limits_slots_and_jobs_wait():
         srv.close()
     assert stats["slots"] == {65536: 1}
     assert stats["jobs"] == 10
+
+
+def test_submit_host_checks_the_grid_capacity():
+    torch = pytest.importorskip("torch")
+    ctx = B.pi_create((0, 0, 0), (1, 1, 1), W.rc_for_cells(8), 1000)
+    try:
+        x = torch.zeros(10).pin_memory()
+        out = [torch.empty(10).pin_memory() for _ in range(4)]
+        nb = torch.empty(10, dtype=torch.int32).pin_memory()
+        # 16^3 cells do not fit a context sized for 8^3
+        with pytest.raises(B.PiError) as e:
+            B.pi_submit_host(ctx, (0, 0, 0), (1, 1, 1), W.rc_for_cells(16), x, x, x, 10, 0.03, *out, nb)
+        assert e.value.status == B.PI_ERR_CAPACITY
+        # 4^3 cells do: the job runs and matches the oracle's counts
+        xs = W.uniform(10, 42)
+        t = [torch.from_numpy(a).pin_memory() for a in xs]
+        rc = W.rc_for_cells(4)
+        B.pi_submit_host(ctx, (0, 0, 0), (1, 1, 1), rc, *t, 10, rc / 2, *out, nb)
+        B.pi_sync_status(ctx)
+        b = oracle.bin_particles(*xs, (0, 0, 0), (1, 1, 1), rc)
+        r = oracle.interact(b, rc, rc / 2)
+        assert np.array_equal(nb.numpy().view(np.uint32)[b.perm], r.nbr)
+    finally:
+        B.pi_destroy(ctx)
