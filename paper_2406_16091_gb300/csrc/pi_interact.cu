@@ -193,14 +193,16 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 
 // ---- tiled interaction ----------------------------------------------------------
 
-// Tile shapes: threads per CTA (= targets per chunk), staged particles per
+// Tile shapes of the one-CTA-per-chunk kernel: threads per CTA (each takes
+// two targets, so a chunk has up to 2 NT targets), staged particles per
 // chunk, CTAs per SM the register and shared-memory budget is sized for, and
 // target cells per chunk along X.  The autotuner (pi_autotune) picks one per
 // context; every shape gives the same per-target summation order, so the
 // results are identical.
-template <int TT_, int CAP_, int MINB_, int MAXLX_>
+template <int NT_, int CAP_, int MINB_, int MAXLX_>
 struct Tile {
-    static constexpr int TT = TT_;
+    static constexpr int NT = NT_;
+    static constexpr int TT = 2 * NT_;  // most targets per chunk (planner limit)
     static constexpr int CAP = CAP_;
     static constexpr int MINB = MINB_;
     static constexpr int MAXLX = MAXLX_;
@@ -208,10 +210,9 @@ struct Tile {
     // rounded up so that every row starts 16-byte aligned
     static constexpr int RB = ((MAXLX + 2) * XSUB + 1 + 7) / 8 * 8;
 };
-using Tile32 = Tile<32, 512, 16, 16>;
-using Tile64 = Tile<64, 576, 14, 16>;
-using Tile128 = Tile<128, 1280, 7, SEG_CELLS>;
-using Tile256 = Tile<256, 2432, 4, SEG_CELLS>;
+using TileS = Tile<32, 768, 12, 16>;
+using TileM = Tile<64, 1280, 7, SEG_CELLS>;
+using TileL = Tile<128, 2432, 4, SEG_CELLS>;
 
 // Sentinel slots staged after every row: the window loop reads whole groups
 // of four candidates, and up to three slots past a window's end are either
@@ -250,9 +251,9 @@ struct Smem {
         __align__(16) uint16_t staged[9][T::RB];
         uint32_t global[9][RB_GLOBAL];
     } tbl;
-    // Per target (thread): its non-empty x-windows as byte offsets into buf,
-    // first | end << 16, plus two spare rows read after the last window.
-    uint32_t win[11][T::TT];
+    // Per thread: the non-empty x-windows of its targets as byte offsets
+    // into buf, first | end << 16, plus one spare row read after the last.
+    uint32_t win[10][T::NT];
     Plan plan;
     SysDesc d;             // the system of the current X-row
     float t;               // its kernel scale
@@ -271,7 +272,7 @@ constexpr bool fits_sm()
 {
     return T::MINB * (sizeof(Smem<T>) + 1024) <= 228u * 1024u;
 }
-static_assert(fits_sm<Tile32>() && fits_sm<Tile64>() && fits_sm<Tile128>() && fits_sm<Tile256>(),
+static_assert(fits_sm<TileS>() && fits_sm<TileM>() && fits_sm<TileL>(),
               "tile shapes exceed the shared memory of their CTAs per SM");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -587,36 +588,26 @@ __device__ __forceinline__ float lt_mask(float a, float b)
     return m;
 }
 
-// 1.0f if a < b and c < ce else 0.0f (the second comparison masks an odd
-// tail: the same set instruction, with a predicate combined by AND).
-__device__ __forceinline__ float lt_mask_and(float a, float b, int c, int ce)
-{
-    float m;
-    asm("{\n\t.reg .pred q;\n\t"
-        "setp.lt.s32 q, %3, %4;\n\t"
-        "set.lt.and.f32.f32 %0, %1, %2, q;\n\t}"
-        : "=f"(m)
-        : "f"(a), "f"(b), "r"(c), "r"(ce));
-    return m;
-}
-
-// Two Gaussian candidates at once with packed FP32 (f32x2) arithmetic:
-// every element is rounded exactly as the scalar operation would be.  The
-// pair test gives a 1/0 mask m; K = 2^(r2 t) * m and n += m.  2^(r2 t) is in
-// [0, 1] for every finite candidate, so K is exactly the kernel value or +0.
-struct PackedSums {
+// Two targets a and b against one candidate source with packed FP32
+// (f32x2) arithmetic: element .x belongs to target a, .y to target b, and
+// every element is rounded exactly as the scalar steps of Sums::pair_nb
+// round it, candidate after candidate, so each target's sums are those of
+// the sequential scalar loop.  The pair test gives a 1/0 mask m; K =
+// 2^(r2 t) * m and n += m.  2^(r2 t) lies in [0, 1] for every finite
+// candidate, so K is the kernel value or exactly +0, and adding +0 leaves a
+// sum as it was: candidates outside a target's own window (the other
+// target's, a row's sentinel slots) change nothing.
+struct PairSums {
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
 
-    // Sources s0 and s1, both real candidates or s1 the sentinel.  The
-    // offsets are formed by scalar subtractions straight into register
-    // pairs, which is cheaper than packing the loaded positions first.
-    __device__ __forceinline__ void pair2u(const float4& s0, const float4& s1, float xt, float yt,
-                                           float zt, float rc2, float2 ks)
+    __device__ __forceinline__ void cand(const float4& p, const float4& ta, const float4& tb, float rc2,
+                                         float2 ks)
     {
-        const float2 dx = make_float2(__fsub_rn(s0.x, xt), __fsub_rn(s1.x, xt));
-        const float2 dy = make_float2(__fsub_rn(s0.y, yt), __fsub_rn(s1.y, yt));
-        const float2 dz = make_float2(__fsub_rn(s0.z, zt), __fsub_rn(s1.z, zt));
+        // offsets by scalar subtractions straight into register pairs
+        const float2 dx = make_float2(__fsub_rn(p.x, ta.x), __fsub_rn(p.x, tb.x));
+        const float2 dy = make_float2(__fsub_rn(p.y, ta.y), __fsub_rn(p.y, tb.y));
+        const float2 dz = make_float2(__fsub_rn(p.z, ta.z), __fsub_rn(p.z, tb.z));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const float2 t = __fmul2_rn(r2, ks);
         const float2 m = make_float2(lt_mask(r2.x, rc2), lt_mask(r2.y, rc2));
@@ -628,25 +619,14 @@ struct PackedSums {
         n = __fadd2_rn(n, m);
     }
 
-    // Sources s0 = candidate c and s1 = candidate c + 1 (or c again when
-    // c + 1 == ce, then masked out).  The offsets are formed by
-    // scalar subtractions straight into register pairs, which is cheaper
-    // than packing the loaded positions into pairs first.
-    __device__ __forceinline__ void pair2s(const float4& s0, const float4& s1, float xt, float yt,
-                                           float zt, float rc2, float2 ks, int c1, int ce)
+    // target a's (second = false) or b's sums into r
+    __device__ __forceinline__ void to(Sums<PlainAcc, KERNEL_GAUSSIAN>& r, bool second) const
     {
-        const float2 dx = make_float2(__fsub_rn(s0.x, xt), __fsub_rn(s1.x, xt));
-        const float2 dy = make_float2(__fsub_rn(s0.y, yt), __fsub_rn(s1.y, yt));
-        const float2 dz = make_float2(__fsub_rn(s0.z, zt), __fsub_rn(s1.z, zt));
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 t = __fmul2_rn(r2, ks);
-        const float2 m = make_float2(lt_mask(r2.x, rc2), lt_mask_and(r2.y, rc2, c1, ce));
-        const float2 K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
-        s = __fadd2_rn(s, K);
-        vx = __ffma2_rn(dx, K, vx);
-        vy = __ffma2_rn(dy, K, vy);
-        vz = __ffma2_rn(dz, K, vz);
-        n = __fadd2_rn(n, m);
+        r.s.v = second ? s.y : s.x;
+        r.vx.v = second ? vx.y : vx.x;
+        r.vy.v = second ? vy.y : vy.x;
+        r.vz.v = second ? vz.y : vz.x;
+        r.n = (uint32_t)(second ? n.y : n.x);  // exact: at most 2^24 neighbours
     }
 };
 
@@ -656,133 +636,150 @@ __host__ __device__ constexpr bool packed_path()
     return std::is_same<Acc, PlainAcc>::value && KERNEL == KERNEL_GAUSSIAN;
 }
 
-// The candidates [j, je) of one window, in order.  The Gaussian FP32 path
-// takes them two at a time (packed, even and odd partial sums); the others
-// one at a time.
+// The candidates [j, je) of one window for one target, in order, one at a
+// time (every path that does not pack two targets).
 template <class Acc, int KERNEL>
 __device__ __forceinline__ void window_sums(const float4* src, int j, int je, float xt, float yt,
                                             float zt, uint32_t slot, float rc2, const KParams& kp,
-                                            PackedSums& ps, Sums<Acc, KERNEL>& r)
+                                            Sums<Acc, KERNEL>& r)
 {
     constexpr bool by_id = self_by_identity<KERNEL, Acc>();
-    if constexpr (packed_path<Acc, KERNEL>()) {
-        const float2 ks = make_float2(kp.t, kp.t);
-        for (; j < je; j += 2) {
-            const float4 s0 = src[j], s1 = src[min(j + 1, je - 1)];
-            ps.pair2s(s0, s1, xt, yt, zt, rc2, ks, j + 1, je);
-        }
-    } else {
-        for (; j < je; ++j) {
-            const float4 s0 = src[j];
-            r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), rc2, kp,
-                      by_id && __float_as_uint(s0.w) == slot);
-        }
+    for (; j < je; ++j) {
+        const float4 s0 = src[j];
+        r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), rc2, kp,
+                  by_id && __float_as_uint(s0.w) == slot);
     }
 }
 
-template <class Acc, int KERNEL>
-__device__ __forceinline__ void finish_packed(const PackedSums& ps, Sums<Acc, KERNEL>& r)
+// Mode 0, two targets a and b of one thread (b may repeat a when the thread
+// has one target): per row the union of their windows goes to the thread's
+// column of `win` (rows where both are empty dropped), then all of them are
+// walked in one loop, so that a lane whose window in one row is short goes
+// on with the next row instead of idling until the warp's longest window of
+// that row ends.  Every source read is evaluated against both targets: one
+// shared-memory load feeds two pair evaluations.  Each target's terms come
+// in the order of its own windows (row by row, x-sorted), as in the
+// per-target loops of the other paths, so every path gives the same sums.
+template <int CAP, int RB, int WT>
+__device__ __forceinline__ void target_pair_sums_staged(const float4* buf, const uint16_t (*tbl)[RB],
+                                                        uint32_t coarse_mask, const SysDesc& d,
+                                                        uint32_t (*win)[WT], unsigned tid,
+                                                        const float4& ta, const float4& tb, int cy,
+                                                        int cz, int base, const KParams& kp,
+                                                        Sums<PlainAcc, KERNEL_GAUSSIAN>& ra,
+                                                        Sums<PlainAcc, KERNEL_GAUSSIAN>& rb)
 {
-    if constexpr (packed_path<Acc, KERNEL>()) {
-        r.s.add(ps.s.x + ps.s.y);
-        r.vx.add(ps.vx.x + ps.vx.y);
-        r.vy.add(ps.vy.x + ps.vy.y);
-        r.vz.add(ps.vz.x + ps.vz.y);
-        r.n += (uint32_t)(ps.n.x + ps.n.y);
+    int nw = 0;
+    {
+        int ja[9], jea[9], jb[9], jeb[9];
+        target_windows(tbl, coarse_mask, d, ta.x, ta.y, ta.z, cy, cz, base, ja, jea);
+        target_windows(tbl, coarse_mask, d, tb.x, tb.y, tb.z, cy, cz, base, jb, jeb);
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) {
+            const bool ea = jea[rr] > ja[rr], eb = jeb[rr] > jb[rr];
+            const int lo = ea ? (eb ? min(ja[rr], jb[rr]) : ja[rr]) : jb[rr];
+            const int hi = ea ? (eb ? max(jea[rr], jeb[rr]) : jea[rr]) : jeb[rr];
+            if (ea || eb) win[nw++][tid] = (uint32_t)lo * 16u | ((uint32_t)hi * 16u << 16);
+        }
     }
+    // nw >= 1: the window of a's own row holds a
+    const float rc2 = d.rc2;
+    const float2 ks = make_float2(kp.t, kp.t);
+    PairSums ps;
+    // shared-window addresses: candidates, this thread's window words
+    const uint32_t cb = smem_addr(buf), wb = smem_addr(&win[0][tid]);
+    constexpr uint32_t WSTEP = (uint32_t)WT * 4u;
+    const uint32_t we = wb + (uint32_t)nw * WSTEP;
+    uint32_t wa = wb;
+    const uint32_t w0 = lds_u32(wa);
+    uint32_t c = cb + (w0 & 0xffffu), ce = cb + (w0 >> 16);
+    // All windows in one loop with the switch written as selects, so no lane
+    // waits for the others at the end of a window (a lane leaves after its
+    // last one).  Four sources per trip; the up to three slots read past a
+    // window's end (the same row outside the windows, or the row's sentinel
+    // slots) add exact zeros.
+    do {
+        const float4 s0 = lds_f4(c), s1 = lds_f4(c + 16u), s2 = lds_f4(c + 32u), s3 = lds_f4(c + 48u);
+        ps.cand(s0, ta, tb, rc2, ks);
+        ps.cand(s1, ta, tb, rc2, ks);
+        ps.cand(s2, ta, tb, rc2, ks);
+        ps.cand(s3, ta, tb, rc2, ks);
+        c += 64u;
+        const bool sw = c >= ce;
+        wa += sw ? WSTEP : 0u;
+        const uint32_t wn = lds_u32(wa);
+        c = sw ? cb + (wn & 0xffffu) : c;
+        ce = sw ? cb + (wn >> 16) : ce;
+    } while (wa < we);
+    ps.to(ra, false);
+    ps.to(rb, true);
 }
 
-// Mode 0, one target: its windows over the staged rows go to the thread's
-// column of sm.win (empty ones dropped), then all of them are walked in one
-// loop, so that a lane whose window in one row is short goes on with the
-// next row instead of idling until the warp's longest window of that row
-// ends.  The candidates and their order are those of the per-row loop of
-// mode 1 (window by window, two at a time, odd tails alone), so both modes
-// give the same sums.
-template <int CAP, int RB, int WT, class Acc, int KERNEL>
+// Mode 0, one target, one candidate at a time over its own windows (the
+// kernels and precision modes without the packed two-target path).
+template <int RB, class Acc, int KERNEL>
 __device__ __forceinline__ void target_sums_staged(const float4* buf, const uint16_t (*tbl)[RB],
-                                                   uint32_t coarse_mask, const SysDesc& d,
-                                                   uint32_t (*win)[WT], unsigned tid, float xt, float yt,
-                                                   float zt, uint32_t slot, int cy, int cz, int base,
-                                                   const KParams& kp, Sums<Acc, KERNEL>& r)
+                                                   uint32_t coarse_mask, const SysDesc& d, const float4& t,
+                                                   int cy, int cz, int base, const KParams& kp,
+                                                   Sums<Acc, KERNEL>& r)
 {
     int j[9], je[9];
-    target_windows(tbl, coarse_mask, d, xt, yt, zt, cy, cz, base, j, je);
-    int nw = 0;
-#pragma unroll
+    target_windows(tbl, coarse_mask, d, t.x, t.y, t.z, cy, cz, base, j, je);
+    const uint32_t slot = __float_as_uint(t.w);
+#pragma unroll 1
     for (int rr = 0; rr < 9; ++rr)
-        if (je[rr] > j[rr]) win[nw++][tid] = (uint32_t)j[rr] * 16u | ((uint32_t)je[rr] * 16u << 16);
-    // nw >= 1: the window of the target's own row holds the target
-    const float rc2 = d.rc2;
-    PackedSums ps;
-    if constexpr (packed_path<Acc, KERNEL>()) {
-        const float2 ks = make_float2(kp.t, kp.t);
-        // the row after the last window: a valid address for the last
-        // prefetch (its data is never used)
-        win[nw][tid] = 0u;
-        // shared-window addresses: candidates, this thread's window words
-        const uint32_t cb = smem_addr(buf), wb = smem_addr(&win[0][tid]);
-        constexpr uint32_t WSTEP = (uint32_t)WT * 4u;
-        const uint32_t we = wb + (uint32_t)nw * WSTEP;
-        uint32_t wa = wb;
-        const uint32_t w0 = lds_u32(wa);
-        uint32_t wnext = lds_u32(wa + WSTEP);
-        uint32_t c = cb + (w0 & 0xffffu), ce = cb + (w0 >> 16);
-        float4 s0 = lds_f4(c), s1 = lds_f4(c + 16u), s2 = lds_f4(c + 32u), s3 = lds_f4(c + 48u);
-        // All windows in one loop with the switch written as selects, so no
-        // lane waits for the others at the end of a window (a lane leaves
-        // after its last one).  Four candidates per trip in two packed pairs;
-        // the up to three slots read past a window's end (same row outside
-        // the window, or the row's sentinel slots) add exact zeros, so the
-        // sums are those of the two-at-a-time loop.  Each trip loads the next
-        // trip's candidates and window word before its own arithmetic.
-        do {
-            const uint32_t cc = c + 64u;
-            const bool sw = cc >= ce;
-            const uint32_t cn = sw ? cb + (wnext & 0xffffu) : cc;
-            const uint32_t cen = sw ? cb + (wnext >> 16) : ce;
-            wa += sw ? WSTEP : 0u;
-            const float4 n0 = lds_f4(cn), n1 = lds_f4(cn + 16u), n2 = lds_f4(cn + 32u), n3 = lds_f4(cn + 48u);
-            wnext = lds_u32(wa + WSTEP);
-            ps.pair2u(s0, s1, xt, yt, zt, rc2, ks);
-            ps.pair2u(s2, s3, xt, yt, zt, rc2, ks);
-            s0 = n0;
-            s1 = n1;
-            s2 = n2;
-            s3 = n3;
-            c = cn;
-            ce = cen;
-        } while (wa < we);
-        finish_packed(ps, r);
-    } else {
-        for (int k = 0; k < nw; ++k) {
-            const uint32_t w = win[k][tid];
-            window_sums<Acc, KERNEL>(buf, (int)((w & 0xffffu) >> 4), (int)(w >> 20), xt, yt, zt, slot, rc2,
-                                     kp, ps, r);
-        }
-    }
+        window_sums<Acc, KERNEL>(buf, j[rr], je[rr], t.x, t.y, t.z, slot, d.rc2, kp, r);
 }
 
 // Mode 1, one target: the same windows, read from P in global memory.
 template <class Acc, int KERNEL>
 __device__ __forceinline__ void target_sums_global(const float4* P, const uint32_t (*tbl)[RB_GLOBAL],
-                                                   uint32_t coarse_mask, const SysDesc& d, float xt,
-                                                   float yt, float zt, uint32_t slot, int cy, int cz,
-                                                   int base, const KParams& kp, Sums<Acc, KERNEL>& r)
+                                                   uint32_t coarse_mask, const SysDesc& d, const float4& t,
+                                                   int cy, int cz, int base, const KParams& kp,
+                                                   Sums<Acc, KERNEL>& r)
 {
     int j[9], je[9];
-    target_windows(tbl, coarse_mask, d, xt, yt, zt, cy, cz, base, j, je);
-    PackedSums ps;
+    target_windows(tbl, coarse_mask, d, t.x, t.y, t.z, cy, cz, base, j, je);
+    const uint32_t slot = __float_as_uint(t.w);
 #pragma unroll 1
     for (int rr = 0; rr < 9; ++rr)
-        window_sums<Acc, KERNEL>(P, j[rr], je[rr], xt, yt, zt, slot, d.rc2, kp, ps, r);
-    finish_packed(ps, r);
+        window_sums<Acc, KERNEL>(P, j[rr], je[rr], t.x, t.y, t.z, slot, d.rc2, kp, r);
+}
+
+// The sums of a thread's targets qa and qb = qa + 1 of a chunk (qb only if
+// has_b), whichever path the chunk and the kernel take, stored.  `first`
+// gives a target's position: staged index in mode 0, P index in mode 1.
+template <int CAP, int RB, int WT, class Acc, int KERNEL>
+__device__ __forceinline__ void chunk_pair(const InteractArgs& a, const float4* buf,
+                                           const uint16_t (*tbl_s)[RB], const uint32_t (*tbl_g)[RB_GLOBAL],
+                                           uint32_t coarse_mask, const SysDesc& d, uint32_t (*win)[WT],
+                                           unsigned tid, int mode, int first, int qa, bool has_b, int cy,
+                                           int cz, int base, const KParams& kp, float kself, uint32_t nself)
+{
+    const int qb = has_b ? qa + 1 : qa;
+    const float4 ta = mode == 0 ? buf[first + qa] : a.P[first + qa];
+    const float4 tb = mode == 0 ? buf[first + qb] : a.P[first + qb];
+    Sums<Acc, KERNEL> ra, rb;
+    if (mode == 0) {
+        if constexpr (packed_path<Acc, KERNEL>()) {
+            target_pair_sums_staged<CAP, RB, WT>(buf, tbl_s, coarse_mask, d, win, tid, ta, tb, cy, cz, base, kp,
+                                                 ra, rb);
+        } else {
+            target_sums_staged<RB, Acc, KERNEL>(buf, tbl_s, coarse_mask, d, ta, cy, cz, base, kp, ra);
+            if (has_b) target_sums_staged<RB, Acc, KERNEL>(buf, tbl_s, coarse_mask, d, tb, cy, cz, base, kp, rb);
+        }
+    } else {
+        target_sums_global<Acc, KERNEL>(a.P, tbl_g, coarse_mask, d, ta, cy, cz, base, kp, ra);
+        if (has_b) target_sums_global<Acc, KERNEL>(a.P, tbl_g, coarse_mask, d, tb, cy, cz, base, kp, rb);
+    }
+    store_out(a, __float_as_uint(ta.w), ra, kself, nself);
+    if (has_b) store_out(a, __float_as_uint(tb.w), rb, kself, nself);
 }
 
 template <class T, class Acc, int KERNEL>
-__global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs a)
+__global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs a)
 {
-    constexpr int TT = T::TT;
+    constexpr int NT = T::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
 
@@ -856,9 +853,9 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             const int ncell = p.xb - p.xa + 1;
             // lookup tables, built while the bulk copies are in flight
             if (mode == 0)
-                build_table<T::TT>(a, d, p, cy, cz, ncell, sm.tbl.staged, &sm.coarse_mask, tid);
+                build_table<NT>(a, d, p, cy, cz, ncell, sm.tbl.staged, &sm.coarse_mask, tid);
             else
-                build_table<T::TT>(a, d, p, cy, cz, ncell, sm.tbl.global, &sm.coarse_mask, tid);
+                build_table<NT>(a, d, p, cy, cz, ncell, sm.tbl.global, &sm.coarse_mask, tid);
             if (mode == 0) {
                 if (!bar_wait_bounded(&sm.bar, phase, a.wait_limit_ns)) {
                     sm.failed = 1;
@@ -875,21 +872,15 @@ __global__ void __launch_bounds__(T::TT, T::MINB) k_interact_tiled(InteractArgs 
             const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
             const int base = XSUB * p.xa;
             if (!sm.failed) {
-                for (int q0 = 0; q0 < ntarget; q0 += TT) {
-                    const int q = q0 + (int)tid;
-                    if (q >= ntarget) continue;
-                    Sums<Acc, KERNEL> r;
-                    const KParams kp{sm.t, a.one, a.zero};
-                    const float4 me = mode == 0 ? sm.buf[t0 + q] : a.P[tb + q];
-                    const uint32_t slot = __float_as_uint(me.w);
-                    if (mode == 0)
-                        target_sums_staged<T::CAP, T::RB, T::TT, Acc, KERNEL>(
-                            sm.buf, sm.tbl.staged, sm.coarse_mask, sm.d, sm.win, tid, me.x, me.y, me.z, slot,
-                            cy, cz, base, kp, r);
-                    else
-                        target_sums_global<Acc, KERNEL>(a.P, sm.tbl.global, sm.coarse_mask, sm.d, me.x, me.y,
-                                                        me.z, slot, cy, cz, base, kp, r);
-                    store_out(a, slot, r, kself, nself);
+                const KParams kp{sm.t, a.one, a.zero};
+                const int first = mode == 0 ? t0 : (int)tb;
+                for (int q0 = 0; q0 < ntarget; q0 += 2 * NT) {
+                    const int qa = q0 + 2 * (int)tid;
+                    if (qa >= ntarget) continue;
+                    chunk_pair<T::CAP, T::RB, NT, Acc, KERNEL>(a, sm.buf, sm.tbl.staged, sm.tbl.global,
+                                                               sm.coarse_mask, sm.d, sm.win, tid, mode, first,
+                                                               qa, qa + 1 < ntarget, cy, cz, base, kp, kself,
+                                                               nself);
                 }
             }
             __syncthreads();
@@ -918,12 +909,12 @@ struct WsTile {
     static constexpr int NS = NS_;            // stages
     static constexpr int MAXLX = MAXLX_;      // target cells per chunk along X
     static constexpr int MINB = MINB_;        // CTAs per SM the budget is sized for
-    static constexpr int TT = 32 * GMAX_;     // most targets per chunk (planner limit)
+    static constexpr int TT = 64 * GMAX_;     // most targets per chunk (planner limit)
     static constexpr int THREADS = 32 * (W + 1);
     static constexpr int RB = ((MAXLX + 2) * XSUB + 1 + 7) / 8 * 8;
 };
-using Ws4 = WsTile<4, 1152, 2, SEG_CELLS, 4, 8>;
-using Ws8 = WsTile<8, 1152, 3, SEG_CELLS, 2, 8>;
+using Ws4 = WsTile<4, 2432, 2, SEG_CELLS, 2, 4>;
+using Ws8 = WsTile<8, 2432, 2, SEG_CELLS, 2, 4>;
 
 template <class T>
 struct WsStage {
@@ -939,7 +930,7 @@ struct WsStage {
     int cy, cz;            // the chunk's X-row
     uint32_t tb;           // P index of its first target
     int ntarget, ngroups;
-    int next_group;        // next 32-target group handed to a consumer warp
+    int next_group;        // next 64-target group (two per lane) handed to a consumer warp
     int done;              // set instead of a chunk when the work is over
     uint64_t full, empty;
 };
@@ -947,7 +938,7 @@ struct WsStage {
 template <class T>
 struct WsSmem {
     WsStage<T> st[T::NS];
-    uint32_t win[11][32 * T::W];  // per consumer thread: its windows (see target_sums_staged)
+    uint32_t win[10][32 * T::W];  // per consumer thread: its windows (see target_pair_sums_staged)
     int failed;
 };
 
@@ -1054,7 +1045,7 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
                 st.cz = cz;
                 st.tb = tb;
                 st.ntarget = nt;
-                st.ngroups = (nt + 31) / 32;
+                st.ngroups = (nt + 63) / 64;
                 st.next_group = 0;
                 st.done = 0;
             }
@@ -1094,27 +1085,19 @@ __device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, 
         const int mode = p.mode, base = XSUB * p.xa, cy = st.cy, cz = st.cz, nt = st.ntarget,
                   ng = st.ngroups;
         const uint32_t tb = st.tb;
-        const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
+        const int first = mode == 0 ? p.sbeg[4] + (int)(tb - p.gbeg[4]) : (int)tb;
         const KParams kp{st.t, a.one, a.zero};
         for (;;) {
             int g = 0;
             if (lane == 0) g = atomicAdd(&st.next_group, 1);
             g = __shfl_sync(0xffffffffu, g, 0);
             if (g >= ng) break;
-            const int q = 32 * g + (int)lane;
-            if (q < nt) {
-                Sums<Acc, KERNEL> r;
-                const float4 me = mode == 0 ? st.buf[t0 + q] : a.P[tb + q];
-                const uint32_t slot = __float_as_uint(me.w);
-                if (mode == 0)
-                    target_sums_staged<T::CAP, T::RB, 32 * T::W, Acc, KERNEL>(
-                        st.buf, st.tbl.staged, st.coarse_mask, st.d, sm.win, tid, me.x, me.y, me.z, slot, cy,
-                        cz, base, kp, r);
-                else
-                    target_sums_global<Acc, KERNEL>(a.P, st.tbl.global, st.coarse_mask, st.d, me.x, me.y,
-                                                    me.z, slot, cy, cz, base, kp, r);
-                store_out(a, slot, r, kself, nself);
-            }
+            const int qa = 64 * g + 2 * (int)lane;
+            if (qa < nt)
+                chunk_pair<T::CAP, T::RB, 32 * T::W, Acc, KERNEL>(a, st.buf, st.tbl.staged, st.tbl.global,
+                                                                  st.coarse_mask, st.d, sm.win, tid, mode,
+                                                                  first, qa, qa + 1 < nt, cy, cz, base, kp,
+                                                                  kself, nself);
         }
         __syncwarp();
         bar_arrive(&st.empty);
@@ -1170,7 +1153,7 @@ cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
 template <class T, class Acc, int KERNEL>
 void launch_tiled_one(const InteractArgs& a, unsigned grid, cudaStream_t s)
 {
-    k_interact_tiled<T, Acc, KERNEL><<<grid, T::TT, sizeof(Smem<T>), s>>>(a);
+    k_interact_tiled<T, Acc, KERNEL><<<grid, T::NT, sizeof(Smem<T>), s>>>(a);
 }
 
 template <class T, class Acc, int KERNEL>
@@ -1189,19 +1172,18 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
-    static_assert(DEFAULT_TILE == 4, "the comparator kernels use the default shape");
+    static_assert(DEFAULT_TILE == 2, "the comparator kernels use the default shape");
     switch (a.kernel) {
-        case KERNEL_LJ: launch_ws_one<Ws4, Acc, KERNEL_LJ>(a, g, s); break;
-        case KERNEL_LOWFLOP: launch_ws_one<Ws4, Acc, KERNEL_LOWFLOP>(a, g, s); break;
-        case KERNEL_HIGHFLOP: launch_ws_one<Ws4, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
+        case KERNEL_LJ: launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s); break;
+        case KERNEL_LOWFLOP: launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s); break;
+        case KERNEL_HIGHFLOP: launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
         default:
             switch (tile) {
-                case 0: launch_tiled_one<Tile32, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                case 1: launch_tiled_one<Tile64, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                case 3: launch_tiled_one<Tile256, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                case 4: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                case 5: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                default: launch_tiled_one<Tile128, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 0: launch_tiled_one<TileS, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 1: launch_tiled_one<TileM, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 2: launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 4: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                default: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
             }
             break;
     }
@@ -1225,7 +1207,7 @@ cudaError_t occupancy_of(int* per_sm)
     auto fn = k_interact_tiled<T, Acc, KERNEL_GAUSSIAN>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<T>));
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T::TT, sizeof(Smem<T>));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T::NT, sizeof(Smem<T>));
 }
 
 }  // namespace
@@ -1242,27 +1224,26 @@ template <class Acc>
 cudaError_t tiled_occupancy_acc(int* per_sm)
 {
     cudaError_t e;
-    if ((e = occupancy_of<Tile32, Acc>(&per_sm[0])) != cudaSuccess) return e;
-    if ((e = occupancy_of<Tile64, Acc>(&per_sm[1])) != cudaSuccess) return e;
-    if ((e = occupancy_of<Tile128, Acc>(&per_sm[2])) != cudaSuccess) return e;
-    if ((e = occupancy_of<Tile256, Acc>(&per_sm[3])) != cudaSuccess) return e;
-    if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[4])) != cudaSuccess) return e;
-    if ((e = ws_occupancy_of<Ws8, Acc>(&per_sm[5])) != cudaSuccess) return e;
+    if ((e = occupancy_of<TileS, Acc>(&per_sm[0])) != cudaSuccess) return e;
+    if ((e = occupancy_of<TileM, Acc>(&per_sm[1])) != cudaSuccess) return e;
+    if ((e = occupancy_of<TileL, Acc>(&per_sm[2])) != cudaSuccess) return e;
+    if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[3])) != cudaSuccess) return e;
+    if ((e = ws_occupancy_of<Ws8, Acc>(&per_sm[4])) != cudaSuccess) return e;
     // the comparator kernels run with the default shape: allow its shared memory
-    constexpr int bytes = (int)sizeof(WsSmem<Ws4>);
-    if ((e = cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_LJ>,
+    constexpr int bytes = (int)sizeof(Smem<TileL>);
+    if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_LJ>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_LOWFLOP>,
+    if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_LOWFLOP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_interact_ws<Ws4, Acc, KERNEL_HIGHFLOP>,
+    return cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_HIGHFLOP>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t tiled_occupancy(bool kahan, int* per_sm)
 {
-    static_assert(NUM_TILES == 6, "one occupancy entry per tile shape");
+    static_assert(NUM_TILES == 5, "one occupancy entry per tile shape");
     return kahan ? tiled_occupancy_acc<KahanAcc>(per_sm) : tiled_occupancy_acc<PlainAcc>(per_sm);
 }
 

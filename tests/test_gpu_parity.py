@@ -18,9 +18,9 @@ from gpu_harness import check_binning, check_interaction, oracle_run, run_gpu
 pytestmark = pytest.mark.gpu
 
 ALGOS = [B.PI_ALGO_TILED, B.PI_ALGO_PPNL]
-# (algorithm, tile shape): the one-thread-per-target shapes of 32 and 128
-# targets, both warp-specialised shapes, and Alg. 1
-VARIANTS = [(B.PI_ALGO_TILED, 0), (B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 4), (B.PI_ALGO_TILED, 5),
+# (algorithm, tile shape): the one-CTA-per-chunk shapes of 32 and 128
+# threads, both warp-specialised shapes, and Alg. 1
+VARIANTS = [(B.PI_ALGO_TILED, 0), (B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 3), (B.PI_ALGO_TILED, 4),
             (B.PI_ALGO_PPNL, None)]
 VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "ppnl"]
 
@@ -157,8 +157,8 @@ def test_kahan_precision_mode():
 
 def test_repeat_is_deterministic():
     x, y, z, lo, hi, rc, h = _case(W.scaled(W.CLUSTERED, 50000))
-    a = run_gpu(x, y, z, lo, hi, rc, h, repeat=1, tile=4)
-    c = run_gpu(x, y, z, lo, hi, rc, h, repeat=3, tile=4)
+    a = run_gpu(x, y, z, lo, hi, rc, h, repeat=1, tile=3)
+    c = run_gpu(x, y, z, lo, hi, rc, h, repeat=3, tile=3)
     for k in ("counts", "offsets", "perm", "sx", "nbr", "S", "Vx", "Vy", "Vz"):
         assert np.array_equal(a[k].view(np.uint32), c[k].view(np.uint32)), k
 
