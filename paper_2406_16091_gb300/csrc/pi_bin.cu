@@ -16,6 +16,8 @@
 //                tiled interaction stages, and each cell's x-sub-bin starts
 //
 // All kernels are HBM- or L2-bound integer work; none uses tensor cores.
+#include <mutex>
+
 #include "pi_internal.cuh"
 
 namespace pi {
@@ -445,6 +447,25 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
 
+// Resident CTAs per SM of a binning kernel (256 threads, no dynamic shared
+// memory) on the current device, queried once per device and kernel.
+template <class F>
+int resident_per_sm(F* fn, int slot)
+{
+    constexpr int MAXDEV = 64, SLOTS = 4;
+    static std::mutex mu;
+    static int cache[MAXDEV][SLOTS] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return 4;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev][slot] == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 256, 0) != cudaSuccess || b < 1) b = 4;
+        cache[dev][slot] = b;
+    }
+    return cache[dev][slot];
+}
+
 inline int grid_for(uint64_t work, int threads, int num_sms, int per_sm)
 {
     uint64_t b = (work + threads - 1) / threads;
@@ -485,7 +506,8 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + 3) / 4;
-    k_hist<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(x, y, z, n, sy, counts, cell, rank,
+    // exactly the resident CTAs (grid-stride loop): no partial last wave
+    k_hist<<<grid_for(groups, 256, num_sms, resident_per_sm(k_hist, 0)), 256, 0, s>>>(x, y, z, n, sy, counts, cell, rank,
                                                              ctrl, vec);
     return cudaGetLastError();
 }
@@ -506,7 +528,7 @@ cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const flo
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + 3) / 4;
-    k_scatter<<<grid_for(groups, 256, num_sms, 8), 256, 0, s>>>(cell, rank, x, y, z, n, offsets, rec,
+    k_scatter<<<grid_for(groups, 256, num_sms, resident_per_sm(k_scatter, 1)), 256, 0, s>>>(cell, rank, x, y, z, n, offsets, rec,
                                                                 ctrl, vec);
     return cudaGetLastError();
 }
@@ -515,7 +537,7 @@ cudaError_t launch_stabilise(const Rec* rec, uint32_t n, const Systems& sy, cons
                              uint32_t* perm, float* sx, float* sy_out, float* sz, float4* P,
                              uint2* xbins, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
-    k_stabilise<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(rec, n, sy, offsets, perm, sx, sy_out, sz,
+    k_stabilise<<<grid_for(n, 256, num_sms, resident_per_sm(k_stabilise, 2)), 256, 0, s>>>(rec, n, sy, offsets, perm, sx, sy_out, sz,
                                                              P, xbins, ctrl);
     return cudaGetLastError();
 }
