@@ -522,8 +522,8 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
                            ctx->wait_limit_ns, ctx->withhold_scan, s));
     ctx->launches += 1;
     if (nn > 0) {
-        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, ctx->offsets, ctx->rec, ctx->ctrl,
-                                  ctx->num_sms, s));
+        PI_TRY(pi::launch_scatter(ctx->cell, ctx->rank, x, y, z, nn, sy, ctx->offsets, ctx->rec,
+                                  ctx->ctrl, ctx->num_sms, s));
         PI_TRY(pi::launch_stabilise(ctx->rec, nn, sy, ctx->offsets, ctx->perm, ctx->sx,
                                     ctx->sy, ctx->sz, ctx->P, ctx->xbins, ctx->ctrl, ctx->num_sms,
                                     s));

@@ -26,13 +26,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ unsigned lanemask_lt()
-{
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 template <int NB>
 __global__ void k_zero(ZeroArgs<NB> z)
 {
@@ -46,9 +39,7 @@ __global__ void k_zero(ZeroArgs<NB> z)
 }
 
 // a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
-// float4 per component when the arrays are 16-byte aligned.  The loop bound
-// is warp-uniform so that every lane takes part in the match/shuffle.  The
-// system of each particle comes from the particle bases; its cell is offset
+// float4 per component when the arrays are 16-byte aligned.  The of each particle comes from the particle bases; its cell is offset
 // by the system's first cell.
 __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               const float* __restrict__ y,
@@ -88,10 +79,10 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
             }
         }
         int s = (sy.S == 1 || grp >= groups) ? 0 : find_system(sy.pbase, sy.S, i0);
-        // all four matches, then all four atomics, then the shuffles: the
-        // atomics of one lane are in flight together instead of one by one
-        uint32_t cell[4], rank[4], key[4];
-        unsigned peers[4];
+        // all four cells, then all four atomics: the atomics of one lane are
+        // in flight together.  Particles come in no spatial order, so a warp
+        // almost never holds two of one cell: no warp aggregation.
+        uint32_t cell[4], rank[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (sy.S > 1 && valid[j])
@@ -100,20 +91,9 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
             bool ok = true;
             cell[j] = cell_of(px[j], py[j], pz[j], d.g, ok) + d.cell_base;
             all_ok &= ok | !valid[j];
-            key[j] = valid[j] ? cell[j] : 0xffffffffu;
-            peers[j] = __match_any_sync(FULL, key[j]);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int leader = __ffs(peers[j]) - 1;
-            rank[j] = 0;
-            if ((int)lane == leader && key[j] != 0xffffffffu)
-                rank[j] = atomicAdd(&counts[key[j]], __popc(peers[j]));
-        }
-        const unsigned lt = lanemask_lt();
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            rank[j] = __shfl_sync(FULL, rank[j], __ffs(peers[j]) - 1) + __popc(peers[j] & lt);
+        for (int j = 0; j < 4; ++j) rank[j] = valid[j] ? atomicAdd(&counts[cell[j]], 1u) : 0u;
         if (full) {
             reinterpret_cast<uint4*>(cell_out)[grp] = make_uint4(cell[0], cell[1], cell[2], cell[3]);
             reinterpret_cast<uint4*>(rank_out)[grp] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
@@ -282,28 +262,40 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
 
 // One record as a single 256-bit store: a whole 32-byte DRAM sector, so the
 // random write needs no read of the rest of the sector.
-__device__ __forceinline__ void store_rec(Rec* dst, float x, uint32_t i, float y, float z, uint32_t c)
+__device__ __forceinline__ void store_rec(Rec* dst, float x, uint32_t i, uint32_t t_lo, uint32_t t_hi, float y,
+                                          float z, uint32_t c)
 {
     asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst),
-                 "r"(__float_as_uint(x)), "r"(i), "r"(__float_as_uint(y)), "r"(__float_as_uint(z)), "r"(c),
-                 "r"(0u), "r"(0u), "r"(0u)
+                 "r"(__float_as_uint(x)), "r"(i), "r"(t_lo), "r"(t_hi), "r"(__float_as_uint(y)),
+                 "r"(__float_as_uint(z)), "r"(c), "r"(0u)
                  : "memory");
 }
 
 __device__ __forceinline__ Rec load_rec(const Rec* src)
 {
     Rec r;
-    uint32_t x, y, z, p0, p1, p2;
+    uint32_t x, y, z;
     asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(x), "=r"(r.i), "=r"(y), "=r"(z), "=r"(r.c), "=r"(p0), "=r"(p1), "=r"(p2)
+                 : "=r"(x), "=r"(r.i), "=r"(r.t_lo), "=r"(r.t_hi), "=r"(y), "=r"(z), "=r"(r.c), "=r"(r.pad)
                  : "l"(src));
     r.x = __uint_as_float(x);
     r.y = __uint_as_float(y);
     r.z = __uint_as_float(z);
-    r.pad[0] = p0;
-    r.pad[1] = p1;
-    r.pad[2] = p2;
     return r;
+}
+
+// The x-sub-bin thermometer of a particle at x in cell c_local of grid g
+// (see Rec): sub-bin = clamp(floor((x - lo) * XSUB * inv_w) - XSUB * cx, 0,
+// XSUB - 1), monotone in x along an X-row.
+__device__ __forceinline__ uint2 sub_bin_thermometer(float x, uint32_t c_local, const Grid& g)
+{
+    static_assert(XSUB == 8, "the thermometer has 7 one-byte counts");
+    const float invs = g.inv_w[0] * (float)XSUB;
+    const int cxs = XSUB * (int)(c_local % (uint32_t)g.n[0]);
+    const int sb = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
+    // bytes sb .. 6 are 1 (byte b - 1 counts "sub-bin < b")
+    const unsigned long long t = 0x01010101010101ull & (~0ull << (8 * sb));
+    return make_uint2((uint32_t)t, (uint32_t)(t >> 32));
 }
 
 // a4, first half: each particle to its provisional slot offsets[cell] +
@@ -313,7 +305,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
                                                  const uint32_t* __restrict__ rank,
                                                  const float* __restrict__ x,
                                                  const float* __restrict__ y,
-                                                 const float* __restrict__ z, uint32_t n,
+                                                 const float* __restrict__ z, uint32_t n, Systems sy,
                                                  const uint32_t* __restrict__ offsets,
                                                  Rec* __restrict__ rec, Ctrl* __restrict__ ctrl,
                                                  int vec)
@@ -369,8 +361,11 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!valid[j]) continue;
+            const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c[j]);
+            const SysDesc& d = sy.sys[sid];
+            const uint2 t = sub_bin_thermometer(px[j], c[j] - d.cell_base, d.g);
             const uint32_t slot = lo[j] + r[j];
-            if (slot < hi[j]) store_rec(rec + slot, px[j], i0 + j, py[j], pz[j], c[j]);
+            if (slot < hi[j]) store_rec(rec + slot, px[j], i0 + j, t.x, t.y, py[j], pz[j], c[j]);
             else bad = true;
         }
     }
@@ -387,9 +382,9 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //     contiguous and monotone in x, so every X-row of P is sorted by x as a
 //     whole -- the tiled interaction stages such rows;
 //   - (the member of x-rank 0 only) xbins[c]: byte b - 1 (b = 1 .. XSUB - 1)
-//     = members whose x-sub-bin is < b (see XSUB); byte 7 = 1 when the cell
-//     has more than 255 members, bytes 0..6 then 0 (every sub-bin starts at
-//     the cell).
+//     = members whose x-sub-bin is < b, the sum of the members' thermometers
+//     (see Rec); byte 7 = 1 when the cell has more than 255 members, bytes
+//     0..6 then 0 (every sub-bin starts at the cell).
 __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, uint32_t n,
                                                    Systems sy, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
@@ -407,13 +402,17 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         if (i >= n || c >= C) { bad = true; continue; }
         const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
         if (k < s0 || k >= s1) { bad = true; continue; }
-        uint32_t r = 0, xr = 0;
+        // stable rank, x-rank and the sum of the members' sub-bin
+        // thermometers (byte b - 1 = members whose sub-bin is < b)
+        uint32_t r = 0, xr = 0, lt_lo = 0, lt_hi = 0;
         for (uint32_t q = s0; q < s1; ++q) {
-            const uint2 m = *reinterpret_cast<const uint2*>(rec + q);  // (x, input index)
+            const uint4 m = *reinterpret_cast<const uint4*>(rec + q);  // (x, input index, thermometer)
             const float xq = __uint_as_float(m.x);
             const uint32_t j = m.y;
             r += (j < i) ? 1u : 0u;
             xr += (xq < me.x || (xq == me.x && j < i)) ? 1u : 0u;
+            lt_lo += m.z;
+            lt_hi += m.w;
         }
         const uint32_t dst = s0 + r;
         perm[dst] = i;
@@ -421,28 +420,10 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         sy_out[dst] = me.y;
         sz[dst] = me.z;
         P[s0 + xr] = make_float4(me.x, me.y, me.z, __uint_as_float(dst));
-        if (xr == 0) {
-            // one thread per cell: where the cell's sub-bins start
-            static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
-            uint2 word = make_uint2(0u, 1u << 24);
-            if (s1 - s0 <= 255u) {
-                const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
-                const Grid& g = sy.sys[sid].g;
-                const float invs = g.inv_w[0] * (float)XSUB;
-                const int cxs = XSUB * (int)((c - sy.sys[sid].cell_base) % (uint32_t)g.n[0]);
-                uint32_t lt[XSUB - 1] = {};
-                for (uint32_t q = s0; q < s1; ++q) {
-                    const float xq = rec[q].x;
-                    const int sb =
-                        min(max(__float2int_rd(__fmul_rn(__fsub_rn(xq, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
-#pragma unroll
-                    for (int bb = 1; bb < XSUB; ++bb) lt[bb - 1] += sb < bb ? 1u : 0u;
-                }
-                word = make_uint2(lt[0] | (lt[1] << 8) | (lt[2] << 16) | (lt[3] << 24),
-                                  lt[4] | (lt[5] << 8) | (lt[6] << 16));
-            }
-            xbins[c] = word;
-        }
+        // the first member in x order writes the cell's sub-bin starts; the
+        // byte sums are exact up to 255 members, larger cells are flagged
+        static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
+        if (xr == 0) xbins[c] = (s1 - s0 > 255u) ? make_uint2(0u, 1u << 24) : make_uint2(lt_lo, lt_hi);
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }
@@ -523,13 +504,13 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
 }
 
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
-                           const float* y, const float* z, uint32_t n, const uint32_t* offsets,
-                           Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s)
+                           const float* y, const float* z, uint32_t n, const Systems& sy,
+                           const uint32_t* offsets, Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + 3) / 4;
-    k_scatter<<<grid_for(groups, 256, num_sms, resident_per_sm(k_scatter, 1)), 256, 0, s>>>(cell, rank, x, y, z, n, offsets, rec,
-                                                                ctrl, vec);
+    k_scatter<<<grid_for(groups, 256, num_sms, resident_per_sm(k_scatter, 1)), 256, 0, s>>>(cell, rank, x, y, z, n, sy, offsets,
+                                                                                         rec, ctrl, vec);
     return cudaGetLastError();
 }
 

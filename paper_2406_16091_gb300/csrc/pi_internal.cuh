@@ -138,16 +138,20 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// One particle in provisional (unstable) slot order: position, input index
-// and cell.  32 bytes, aligned, so that the scatter writes whole DRAM
-// sectors; x and the input index come first, the pair the stable ranking
-// compares.
+// One particle in provisional (unstable) slot order: position, input index,
+// cell, and its x-sub-bin as a thermometer (byte b - 1 is 1 when the
+// sub-bin is < b, b = 1 .. XSUB - 1; t_lo holds bytes 0..3, t_hi bytes
+// 4..6), so that summing the thermometers of a cell's members gives the
+// cell's sub-bin starts.  32 bytes, aligned, so that the scatter writes
+// whole DRAM sectors; (x, i, t_lo, t_hi) come first: what the ranking reads
+// of every member.
 struct __align__(32) Rec {
     float x;
     uint32_t i;
+    uint32_t t_lo, t_hi;
     float y, z;
     uint32_t c;
-    uint32_t pad[3];
+    uint32_t pad;
 };
 static_assert(sizeof(Rec) == 32, "one DRAM sector per record");
 
@@ -172,8 +176,8 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
                         uint64_t wait_limit_ns, int withhold_first, cudaStream_t s);
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
-                           const float* y, const float* z, uint32_t n, const uint32_t* offsets,
-                           Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s);
+                           const float* y, const float* z, uint32_t n, const Systems& sy,
+                           const uint32_t* offsets, Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s);
 cudaError_t launch_stabilise(const Rec* rec, uint32_t n,
                              const Systems& sy, const uint32_t* offsets, uint32_t* perm, float* sx,
                              float* sy_out, float* sz, float4* P, uint2* xbins, Ctrl* ctrl,
