@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--flush-mb", type=int, default=512)
-    p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4"],
+    p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
                    help="tile shape of the tiled interaction (auto: pi_autotune during warm-up)")
     p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
                    default="none", help="run one of the extra studies instead of the main line")
@@ -349,7 +349,7 @@ def run_ours(args):
     if args.algo != "tiled":
         kname = "k_interact_ppnl"
     else:
-        kname = "k_interact_ws" if tile in (3, 4) else "k_interact_tiled"
+        kname = {3: "k_interact_ws", 4: "k_interact_ws", 5: "k_interact_direct"}.get(tile, "k_interact_tiled")
     traffic = recorded_traffic(kname, source_hash([os.path.join(src, "pi_interact.cu"),
                                                    os.path.join(src, "pi_internal.cuh")]))
     roofline = {
@@ -670,7 +670,7 @@ def study_sweep(args):
             run = lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
             for algo_name, algo in (("tiled", B.PI_ALGO_TILED), ("ppnl", B.PI_ALGO_PPNL)):
                 B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
-                B.pi_set_option(ctx, B.PI_OPT_TILE, 2)
+                B.pi_set_option(ctx, B.PI_OPT_TILE, 5)
                 run()
                 ms, _ = _time_events(torch, run, 10, flush)
                 entry[f"{algo_name}_ms"] = ms

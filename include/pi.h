@@ -89,7 +89,10 @@ enum {
      * targets): 0, 1, 2 for one CTA per chunk with 32, 64, 128 threads and
      * 768, 1280, 2432 staged particles; 3, 4 for the warp-specialised form
      * (one producer warp stages chunks of up to 2432 particles into 2
-     * buffers for 4 or 8 consumer warps).  Default 2.  pi_autotune sets it
+     * buffers for 4 or 8 consumer warps); 5 for the direct form (no
+     * staging: one thread per target pair reads its sources from global
+     * memory through L1; the Gaussian kernel in FP32 only, the others run
+     * shape 2).  Default 5.  pi_autotune sets it
      * from measurements.  Results do not depend on it. */
     PI_OPT_TILE = 6
 };
@@ -226,10 +229,10 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
 /* Autotuner of the interaction for the data of the last pi_bin /
  * pi_batch_bin: runs the interaction (arguments as pi_batch_interact, h one
  * entry per system) once untimed and `reps` times timed (1 <= reps <= 100)
- * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..4) and then
+ * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..5) and then
  * with PI_ALGO_PPNL, keeps the candidate with the smallest median time for
  * later calls (setting PI_OPT_ALGO and PI_OPT_TILE), and returns its index in
- * *chosen (0..4 = tile shape, 5 = PI_ALGO_PPNL) and the medians in ms[6]
+ * *chosen (0..5 = tile shape, 6 = PI_ALGO_PPNL) and the medians in ms[7]
  * (milliseconds; either pointer may be NULL).  The choice changes only the
  * speed: every tile shape sums each target's terms in the same order, so
  * their outputs are identical; PPNL's agree with them within the stated

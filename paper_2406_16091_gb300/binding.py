@@ -32,7 +32,7 @@ PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
-PI_NUM_TILES = 5  # tile shapes of PI_OPT_TILE (see include/pi.h)
+PI_NUM_TILES = 6  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_AUTOTUNE_PPNL = PI_NUM_TILES  # pi_autotune's index of PI_ALGO_PPNL
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1

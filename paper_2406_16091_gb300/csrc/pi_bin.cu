@@ -394,6 +394,11 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
                                                    Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
+    // P[n]: a particle far from every other one (finite coordinates, so its
+    // pair terms are exact zeros), read by the direct interaction for slots
+    // past a window's end
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        P[n] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
     bool bad = false;
     const uint32_t C = __ldg(sy.cbase + sy.S);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {

@@ -1137,6 +1137,164 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
         ws_consumer<T, Acc, KERNEL>(a, sm, tid, lane, kself, nself);
 }
 
+// ---- direct interaction (no staging) ------------------------------------------
+//
+// The same windows, pairs of targets and summation order as the tiled
+// kernels, without shared-memory staging: one thread takes two consecutive
+// targets of the sorted order, reads the sub-bin starts of its windows from
+// the offsets and `xbins` in global memory, and loads every source straight
+// from P through L1 (neighbouring threads work on the same rows, so the
+// loads hit).  No chunks, no barriers: only the window lists live in shared
+// memory, so occupancy is set by registers alone.
+
+constexpr int DIRECT_THREADS = 128;
+
+// First index of P whose sub-bin in the row starting at cell `rb` is >= b
+// (b counted from the row's first cell); `upper`: round a sub-bin of a cell
+// without sub-bin starts up to the cell's end instead of down to its start.
+__device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_t rb, int b, bool upper)
+{
+    const uint32_t k = (uint32_t)(b >> 3), sub = (uint32_t)(b & 7);
+    const uint32_t start = __ldg(a.offsets + rb + k);
+    if (sub == 0) return start;
+    const uint2 w = __ldg(a.xbins + rb + k);
+    if (w.y >> 24) return upper ? __ldg(a.offsets + rb + k + 1) : start;
+    const uint32_t word = sub <= 4 ? w.x : w.y;
+    return start + ((word >> (8 * ((sub - 1) & 3))) & 255u);
+}
+
+// The 9 x-windows of one target as ranges of P (see target_windows; here
+// the lookups read global memory).
+__device__ __forceinline__ void target_windows_direct(const InteractArgs& a, const SysDesc& d, const float4& t,
+                                                      int cx, int cy, int cz, uint32_t (&j)[9],
+                                                      uint32_t (&je)[9])
+{
+    const Faces f = faces_of(d, t.y, t.z, cy, cz);
+    const float rcm2 = d.rc2 * 1.00002f;
+    const float xlo = d.g.lo[0], slack = d.slack, invs = d.g.inv_w[0] * (float)XSUB;
+    const int nx = d.g.n[0], ny = d.g.n[1], nz = d.g.n[2];
+    const int lo = XSUB * max(cx - 1, 0);
+    const int hi = XSUB * (min(cx + 1, nx - 1) + 1) - 1;
+#pragma unroll
+    for (int rr = 0; rr < 9; ++rr) {
+        const int dy = rr % 3 - 1, dz = rr / 3 - 1;
+        const int by = cy + dy, bz = cz + dz;
+        const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
+        const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
+        const float tw = rcm2 - fmaf(ey, ey, ez * ez);
+        j[rr] = 0u;
+        je[rr] = 0u;
+        if (by < 0 || by >= ny || bz < 0 || bz >= nz || !(tw > 0.f)) continue;
+        const float tt = fmaxf(tw, 1e-30f);
+        const float w = tt * rsqrtf(tt) + slack;
+        const uint32_t rb = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
+        const int b0 = sub_bin(t.x - w, xlo, invs, 0, lo, hi);
+        const int b1 = sub_bin(t.x + w, xlo, invs, 0, lo, hi) + 1;
+        j[rr] = sub_bin_start(a, rb, b0, false);
+        je[rr] = sub_bin_start(a, rb, b1, true);
+    }
+}
+
+// A source of P, or the sentinel P[n] for slots past a window's end.
+__device__ __forceinline__ float4 ldg_src(const float4* P, uint32_t k, uint32_t end, uint32_t n)
+{
+    return __ldg(P + (k < end ? k : n));
+}
+
+// Targets a and b (b may repeat a) of one row, their union windows in column
+// `col` of `win`, summed like pair_loop with sources from global memory.
+template <int WT>
+__device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
+                                            unsigned col, const float4& ta, const float4& tb, int cxa, int cxb,
+                                            int cy, int cz, const KParams& kp,
+                                            Sums<PlainAcc, KERNEL_GAUSSIAN>& ra,
+                                            Sums<PlainAcc, KERNEL_GAUSSIAN>& rb)
+{
+    int nw = 0;
+    {
+        uint32_t ja[9], jea[9], jb[9], jeb[9];
+        target_windows_direct(a, d, ta, cxa, cy, cz, ja, jea);
+        target_windows_direct(a, d, tb, cxb, cy, cz, jb, jeb);
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) {
+            const bool ea = jea[rr] > ja[rr], eb = jeb[rr] > jb[rr];
+            const uint32_t lo = ea ? (eb ? min(ja[rr], jb[rr]) : ja[rr]) : jb[rr];
+            const uint32_t hi = ea ? (eb ? max(jea[rr], jeb[rr]) : jea[rr]) : jeb[rr];
+            if (ea || eb) {
+                win[2 * nw][col] = lo;
+                win[2 * nw + 1][col] = hi;
+                ++nw;
+            }
+        }
+    }
+    // nw >= 1: the window of a's own row holds a
+    const float rc2 = d.rc2;
+    const float2 ks = make_float2(kp.t, kp.t);
+    const uint32_t n = a.n;
+    PairSums ps;
+    int k = 0;
+    uint32_t c = win[0][col], ce = win[1][col];
+    for (;;) {
+        const float4 s0 = __ldg(a.P + c), s1 = ldg_src(a.P, c + 1u, ce, n), s2 = ldg_src(a.P, c + 2u, ce, n),
+                     s3 = ldg_src(a.P, c + 3u, ce, n);
+        ps.cand(s0, ta, tb, rc2, ks);
+        ps.cand(s1, ta, tb, rc2, ks);
+        ps.cand(s2, ta, tb, rc2, ks);
+        ps.cand(s3, ta, tb, rc2, ks);
+        c += 4u;
+        if (c >= ce) {
+            if (++k >= nw) break;
+            c = win[2 * k][col];
+            ce = win[2 * k + 1][col];
+        }
+    }
+    ps.to(ra, false);
+    ps.to(rb, true);
+}
+
+__global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs a)
+{
+    __shared__ uint32_t win[18][DIRECT_THREADS];
+    // keep the work counters of the tiled launches in step (see k_interact_tiled)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
+    if (load_error(a.ctrl)) return;
+    const uint32_t p = blockIdx.x * DIRECT_THREADS + threadIdx.x;
+    const uint32_t ka = 2u * p;
+    if (ka >= a.n) return;
+    const float4 ta = __ldg(a.P + ka);
+    const bool has_b = ka + 1u < a.n;
+    const float4 t1 = has_b ? __ldg(a.P + ka + 1u) : ta;
+    const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.pbase, a.sy.S, ka);
+    const int sid1 = (a.sy.S == 1 || !has_b) ? sid : find_system(a.sy.pbase, a.sy.S, ka + 1u);
+    const SysDesc& d = a.sy.sys[sid];
+    const Grid& g = d.g;
+    const int cxa = axis_cell(ta.x, g.lo[0], g.inv_w[0], g.n[0]);
+    const int cy = axis_cell(ta.y, g.lo[1], g.inv_w[1], g.n[1]);
+    const int cz = axis_cell(ta.z, g.lo[2], g.inv_w[2], g.n[2]);
+    const int cxb = axis_cell(t1.x, g.lo[0], g.inv_w[0], g.n[0]);
+    // the two targets share the union of their windows when they lie in one
+    // X-row of one system; otherwise each runs alone (b repeating a)
+    const bool together = has_b && sid1 == sid && axis_cell(t1.y, g.lo[1], g.inv_w[1], g.n[1]) == cy &&
+                          axis_cell(t1.z, g.lo[2], g.inv_w[2], g.n[2]) == cz;
+    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
+    const float kself = ex2_approx(0.f);
+    Sums<PlainAcc, KERNEL_GAUSSIAN> ra, rb;
+    direct_pair(a, d, win, threadIdx.x, ta, together ? t1 : ta, cxa, together ? cxb : cxa, cy, cz, kp, ra, rb);
+    store_out(a, __float_as_uint(ta.w), ra, kself, 1u);
+    if (together) {
+        store_out(a, __float_as_uint(t1.w), rb, kself, 1u);
+    } else if (has_b) {
+        const SysDesc& d1 = a.sy.sys[sid1];
+        const Grid& g1 = d1.g;
+        const KParams kp1{a.kscale ? a.kscale[sid1] : a.kscale0, a.one, a.zero};
+        const int cx1 = axis_cell(t1.x, g1.lo[0], g1.inv_w[0], g1.n[0]);
+        const int cy1 = axis_cell(t1.y, g1.lo[1], g1.inv_w[1], g1.n[1]);
+        const int cz1 = axis_cell(t1.z, g1.lo[2], g1.inv_w[2], g1.n[2]);
+        direct_pair(a, d1, win, threadIdx.x, t1, t1, cx1, cx1, cy1, cz1, kp1, rb, ra);
+        store_out(a, __float_as_uint(t1.w), rb, kself, 1u);
+    }
+}
+
 template <class Acc>
 cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
 {
@@ -1166,13 +1324,12 @@ template <class Acc>
 cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
                              cudaStream_t s)
 {
-    // the other kernels are comparators: they run with one tile shape
-    if (a.kernel != KERNEL_GAUSSIAN) tile = DEFAULT_TILE;
+    // the other kernels are comparators: they run with the 128-thread shape
+    if (a.kernel != KERNEL_GAUSSIAN) tile = 2;
     uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
-    static_assert(DEFAULT_TILE == 2, "the comparator kernels use the default shape");
     switch (a.kernel) {
         case KERNEL_LJ: launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s); break;
         case KERNEL_LOWFLOP: launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s); break;
@@ -1183,6 +1340,15 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
                 case 1: launch_tiled_one<TileM, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 2: launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 4: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
+                case 5:
+                    if constexpr (std::is_same<Acc, PlainAcc>::value) {
+                        const uint64_t pairs = ((uint64_t)a.n + 1) / 2;
+                        k_interact_direct<<<(unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS),
+                                            DIRECT_THREADS, 0, s>>>(a);
+                    } else {
+                        launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s);  // packed path only
+                    }
+                    break;
                 default: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
             }
             break;
@@ -1229,7 +1395,8 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
     if ((e = occupancy_of<TileL, Acc>(&per_sm[2])) != cudaSuccess) return e;
     if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[3])) != cudaSuccess) return e;
     if ((e = ws_occupancy_of<Ws8, Acc>(&per_sm[4])) != cudaSuccess) return e;
-    // the comparator kernels run with the default shape: allow its shared memory
+    per_sm[5] = 1;  // the direct kernel launches one thread per target pair
+    // the comparator kernels run with the 128-thread shape: allow its shared memory
     constexpr int bytes = (int)sizeof(Smem<TileL>);
     if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_LJ>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
@@ -1243,7 +1410,7 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
 
 cudaError_t tiled_occupancy(bool kahan, int* per_sm)
 {
-    static_assert(NUM_TILES == 5, "one occupancy entry per tile shape");
+    static_assert(NUM_TILES == 6, "one occupancy entry per tile shape");
     return kahan ? tiled_occupancy_acc<KahanAcc>(per_sm) : tiled_occupancy_acc<PlainAcc>(per_sm);
 }
 

@@ -231,10 +231,10 @@ struct InteractArgs {
 cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms, cudaStream_t s,
                                  int* launches);
 // tile: 0, 1, 2 = one CTA per chunk with 32, 64, 128 threads (two targets
-// each); 3, 4 = warp-specialised, 4 or 8 consumer warps; per_sm[tile] =
-// resident CTAs.
-constexpr int NUM_TILES = 5;
-constexpr int DEFAULT_TILE = 2;
+// each); 3, 4 = warp-specialised, 4 or 8 consumer warps; 5 = direct (no
+// staging, sources through L1); per_sm[tile] = resident CTAs.
+constexpr int NUM_TILES = 6;
+constexpr int DEFAULT_TILE = 5;
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
                                   int tile, cudaStream_t s, int* launches);
 // Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[NUM_TILES]).

@@ -19,10 +19,10 @@ pytestmark = pytest.mark.gpu
 
 ALGOS = [B.PI_ALGO_TILED, B.PI_ALGO_PPNL]
 # (algorithm, tile shape): the one-CTA-per-chunk shapes of 32 and 128
-# threads, both warp-specialised shapes, and Alg. 1
+# threads, both warp-specialised shapes, the direct form, and Alg. 1
 VARIANTS = [(B.PI_ALGO_TILED, 0), (B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 3), (B.PI_ALGO_TILED, 4),
-            (B.PI_ALGO_PPNL, None)]
-VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "ppnl"]
+            (B.PI_ALGO_TILED, 5), (B.PI_ALGO_PPNL, None)]
+VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "direct", "ppnl"]
 
 
 def _case(w):
