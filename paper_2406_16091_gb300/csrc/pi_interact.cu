@@ -1232,9 +1232,15 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     const float2 ks = make_float2(kp.t, kp.t);
     const uint32_t n = a.n;
     PairSums ps;
-    int k = 0;
-    uint32_t c = win[0][col], ce = win[1][col];
-    for (;;) {
+    // the window words of this column by shared-window address (the
+    // switch is written as selects: a lane leaves after its last window
+    // without waiting for the others at the end of each row)
+    const uint32_t wb = smem_addr(&win[0][col]);
+    constexpr uint32_t WSTEP = (uint32_t)WT * 8u;  // one window = two rows of win
+    const uint32_t we = wb + (uint32_t)nw * WSTEP;
+    uint32_t wa = wb;
+    uint32_t c = lds_u32(wa), ce = lds_u32(wa + WT * 4u);
+    do {
         const float4 s0 = __ldg(a.P + c), s1 = ldg_src(a.P, c + 1u, ce, n), s2 = ldg_src(a.P, c + 2u, ce, n),
                      s3 = ldg_src(a.P, c + 3u, ce, n);
         ps.cand(s0, ta, tb, rc2, ks);
@@ -1242,19 +1248,19 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
         ps.cand(s2, ta, tb, rc2, ks);
         ps.cand(s3, ta, tb, rc2, ks);
         c += 4u;
-        if (c >= ce) {
-            if (++k >= nw) break;
-            c = win[2 * k][col];
-            ce = win[2 * k + 1][col];
-        }
-    }
+        const bool sw = c >= ce;
+        wa += sw ? WSTEP : 0u;
+        const uint32_t cn = lds_u32(wa), cen = lds_u32(wa + WT * 4u);
+        c = sw ? cn : c;
+        ce = sw ? cen : ce;
+    } while (wa < we);
     ps.to(ra, false);
     ps.to(rb, true);
 }
 
 __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs a)
 {
-    __shared__ uint32_t win[18][DIRECT_THREADS];
+    __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
     // keep the work counters of the tiled launches in step (see k_interact_tiled)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
