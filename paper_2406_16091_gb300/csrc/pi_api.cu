@@ -29,8 +29,10 @@ struct pi_ctx {
     std::vector<SysDesc> sys;     // host copy of the per-system constants
     std::vector<uint32_t> cbase;  // [S+1]
     std::vector<uint32_t> wbase;  // [S+1]
+    std::vector<uint32_t> rbase;  // [S+1] first X-row of each system
     int64_t C;                    // cells of all systems
     int64_t C_alloc;              // cells the arena was sized for
+    int64_t rows = 0;             // X-rows of all systems
     int64_t n_max_total;
     uint32_t work;                // work items of the tiled interaction
     int device;
@@ -48,6 +50,7 @@ struct pi_ctx {
     SysDesc* d_sys;
     uint32_t* d_cbase;
     uint32_t* d_wbase;
+    uint32_t* d_rbase;
     float* d_kscale;
     double* d_partial;            // [S * TOTAL_PARTS] scratch of pi_total_f64
     uint32_t* cell;
@@ -225,9 +228,10 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->sys.resize(S);
     c->cbase.assign(S + 1, 0);
     c->wbase.assign(S + 1, 0);
+    c->rbase.assign(S + 1, 0);
     c->pbase_h.assign(S + 1, 0);
     c->kscale_h.assign(S, std::nanf(""));
-    int64_t C = 0, N = 0, R = 0;
+    int64_t C = 0, N = 0, R = 0, RW = 0;
     for (int s = 0; s < S; ++s) {
         int64_t cells = 0;
         pi_status st = make_system(boxes[s], r_c[s], c->sys[s], cells);
@@ -240,10 +244,13 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
         d.nseg = (uint32_t)((d.g.n[0] + pi::SEG_CELLS - 1) / pi::SEG_CELLS);
         d.cell_base = (uint32_t)C;
         d.work_base = (uint32_t)R;
+        d.row_base = (uint32_t)RW;
         c->cbase[s] = (uint32_t)C;
         c->wbase[s] = (uint32_t)R;
+        c->rbase[s] = (uint32_t)RW;
         C += cells;
         R += (int64_t)d.g.n[1] * d.g.n[2] * d.nseg;
+        RW += (int64_t)d.g.n[1] * d.g.n[2];
         N += n_max[s];
         if (C >= ((int64_t)1 << 31) - 1 || N >= (int64_t)2147483647 - 64 || R >= ((int64_t)1 << 31)) {
             delete c;
@@ -252,6 +259,8 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     }
     c->cbase[S] = (uint32_t)C;
     c->wbase[S] = (uint32_t)R;
+    c->rbase[S] = (uint32_t)RW;
+    c->rows = RW;
     c->C = C;
     c->C_alloc = C;
     c->n_max_total = N;
@@ -284,6 +293,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_sys = k.take<SysDesc>((size_t)S);
     const size_t o_cbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_wbase = k.take<uint32_t>((size_t)S + 1);
+    const size_t o_rbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_kscale = k.take<float>((size_t)S);
     const size_t o_partial = k.take<double>((size_t)S * pi::TOTAL_PARTS);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
@@ -293,7 +303,9 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_sx = k.take<float>(nm + 4);
     const size_t o_sy = k.take<float>(nm + 4);
     const size_t o_sz = k.take<float>(nm + 4);
-    const size_t o_P = k.take<float4>(nm + 4);
+    // P: the particles plus ROW_PADS slots per X-row; rows <= cells for
+    // every grid pi_reconfigure may set
+    const size_t o_P = k.take<float4>(nm + (size_t)pi::ROW_PADS * (size_t)C + 8);
     const size_t total = align_up(k.off, 256);
 
     e = cudaMalloc(&c->arena, total);
@@ -312,6 +324,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->d_sys = (SysDesc*)(base + o_sys);
     c->d_cbase = (uint32_t*)(base + o_cbase);
     c->d_wbase = (uint32_t*)(base + o_wbase);
+    c->d_rbase = (uint32_t*)(base + o_rbase);
     c->d_kscale = (float*)(base + o_kscale);
     c->d_partial = (double*)(base + o_partial);
     c->cell = (uint32_t*)(base + o_cell);
@@ -331,6 +344,8 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
         e = cudaMemcpy(c->d_cbase, c->cbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_wbase, c->wbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_rbase, c->rbase.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         pi_status st = cuda_fail(e, "pi_batch_create: initialise");
@@ -373,17 +388,21 @@ pi_status pi_reconfigure(pi_ctx* ctx, const pi_box* box, float r_c, pi_stream st
     d.nseg = (uint32_t)((d.g.n[0] + pi::SEG_CELLS - 1) / pi::SEG_CELLS);
     d.cell_base = 0;
     d.work_base = 0;
+    d.row_base = 0;
     const int64_t work = (int64_t)d.g.n[1] * d.g.n[2] * d.nseg;
+    const int64_t rows = (int64_t)d.g.n[1] * d.g.n[2];
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_reconfigure: set device");
-    PI_TRY(pi::launch_set_system(ctx->d_sys, ctx->d_cbase, ctx->d_wbase, d, (uint32_t)cells,
-                                 (uint32_t)work, (cudaStream_t)stream));
+    PI_TRY(pi::launch_set_system(ctx->d_sys, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, d, (uint32_t)cells,
+                                 (uint32_t)work, (uint32_t)rows, (cudaStream_t)stream));
     ctx->launches += 1;
     ctx->boxes[0] = *box;
     ctx->rc[0] = r_c;
     ctx->sys[0] = d;
     ctx->cbase[1] = (uint32_t)cells;
     ctx->wbase[1] = (uint32_t)work;
+    ctx->rbase[1] = (uint32_t)rows;
+    ctx->rows = rows;
     ctx->C = cells;
     ctx->work = (uint32_t)work;
     ctx->binned = 0;
@@ -505,7 +524,7 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
     for (int k = 0; k < ctx->S; ++k) ctx->pbase_h[k + 1] = ctx->pbase_h[k] + (uint32_t)n[k];
     const uint32_t nn = (uint32_t)total;
     const uint32_t C = (uint32_t)ctx->C;
-    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
+    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, ctx->S};
 
     // control block, counts and xbins are one contiguous zeroed prefix of the
     // arena; the same launch writes this step's particle bases
@@ -557,7 +576,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     cudaStream_t st = (cudaStream_t)stream;
 
     pi::InteractArgs a{};
-    a.sy = pi::Systems{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
+    a.sy = pi::Systems{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, ctx->S};
     a.P = ctx->P;
     a.xbins = ctx->xbins;
     a.sx = ctx->sx;
@@ -566,6 +585,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     a.offsets = ctx->offsets;
     a.perm = ctx->perm;
     a.n = (uint32_t)ctx->n;
+    a.np = (uint32_t)(ctx->n + pi::ROW_PADS * ctx->rows);
     a.work = ctx->work;
     a.kernel = ctx->kernel;
     a.one = 1.0f;
@@ -687,7 +707,7 @@ pi_status pi_total_f64(pi_ctx* ctx, const float* v, double* out, pi_stream strea
     if (ctx->n > 0 && !v) return PI_ERR_INVALID_ARG;
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_total_f64: set device");
-    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->S};
+    pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, ctx->S};
     PI_TRY(pi::launch_total_f64(ctx->n > 0 ? v : ctx->sx, sy, ctx->d_partial, pi::TOTAL_PARTS, out,
                                 (cudaStream_t)stream));
     ctx->launches += 2;

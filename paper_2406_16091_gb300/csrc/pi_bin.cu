@@ -378,9 +378,10 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //   - the stable rank: members with a smaller input index (input order
 //     inside the cell), and writes perm, sx, sy, sz at that slot;
 //   - the x-rank: members with smaller x (ties by input index), and writes
-//     P[s0 + x-rank] = (x, y, z, stable slot).  The cells of an X-row are
-//     contiguous and monotone in x, so every X-row of P is sorted by x as a
-//     whole -- the tiled interaction stages such rows;
+//     P[s0 + x-rank + ROW_PADS * row] = (x, y, z, stable slot).  The cells
+//     of an X-row are contiguous and monotone in x, so every X-row of P is
+//     sorted by x as a whole -- the tiled interaction stages such rows --
+//     and followed by ROW_PADS sentinel slots (written here too);
 //   - (the member of x-rank 0 only) xbins[c]: byte b - 1 (b = 1 .. XSUB - 1)
 //     = members whose x-sub-bin is < b, the sum of the members' thermometers
 //     (see Rec); byte 7 = 1 when the cell has more than 255 members, bytes
@@ -394,13 +395,20 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
                                                    Ctrl* __restrict__ ctrl)
 {
     if (load_error(ctrl)) return;
-    // P[n]: a particle far from every other one (finite coordinates, so its
-    // pair terms are exact zeros), read by the direct interaction for slots
-    // past a window's end
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        P[n] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
     bool bad = false;
     const uint32_t C = __ldg(sy.cbase + sy.S);
+    // the sentinel slots after every X-row of P: a particle far from every
+    // other one (finite coordinates, so its pair terms are exact zeros)
+    const uint32_t rows = __ldg(sy.rbase + sy.S);
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const int sid = sy.S == 1 ? 0 : find_system(sy.rbase, sy.S, r);
+        const SysDesc& d = sy.sys[sid];
+        const uint32_t end_cell = d.cell_base + (r - d.row_base + 1u) * (uint32_t)d.g.n[0];
+        const uint32_t pos = offsets[end_cell] + ROW_PADS * r;
+#pragma unroll
+        for (int k = 0; k < ROW_PADS; ++k)
+            P[pos + k] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
+    }
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const Rec me = load_rec(rec + k);
         const uint32_t i = me.i, c = me.c;
@@ -424,7 +432,10 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         sx[dst] = me.x;
         sy_out[dst] = me.y;
         sz[dst] = me.z;
-        P[s0 + xr] = make_float4(me.x, me.y, me.z, __uint_as_float(dst));
+        const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
+        const SysDesc& d = sy.sys[sid];
+        const uint32_t row = d.row_base + (c - d.cell_base) / (uint32_t)d.g.n[0];
+        P[s0 + xr + ROW_PADS * row] = make_float4(me.x, me.y, me.z, __uint_as_float(dst));
         // the first member in x order writes the cell's sub-bin starts; the
         // byte sums are exact up to 255 members, larger cells are flagged
         static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
@@ -529,13 +540,14 @@ cudaError_t launch_stabilise(const Rec* rec, uint32_t n, const Systems& sy, cons
 }
 
 namespace {
-__global__ void k_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, SysDesc d, uint32_t cells,
-                             uint32_t work)
+__global__ void k_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uint32_t* rbase, SysDesc d,
+                             uint32_t cells, uint32_t work, uint32_t rows)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sys[0] = d;
         cbase[1] = cells;
         wbase[1] = work;
+        rbase[1] = rows;
     }
 }
 
@@ -552,10 +564,10 @@ __global__ void k_set_kscale(KscaleArgs k)
 }
 }  // namespace
 
-cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, const SysDesc& d,
-                              uint32_t cells, uint32_t work, cudaStream_t s)
+cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uint32_t* rbase,
+                              const SysDesc& d, uint32_t cells, uint32_t work, uint32_t rows, cudaStream_t s)
 {
-    k_set_system<<<1, 32, 0, s>>>(sys, cbase, wbase, d, cells, work);
+    k_set_system<<<1, 32, 0, s>>>(sys, cbase, wbase, rbase, d, cells, work, rows);
     return cudaGetLastError();
 }
 

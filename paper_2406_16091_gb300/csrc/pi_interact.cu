@@ -402,9 +402,11 @@ __device__ void plan_chunk(const InteractArgs& a, const SysDesc& d, Plan& p, int
     if (lane < 9) {
         const int by = cy + (int)lane % 3 - 1, bz = cz + (int)lane / 3 - 1;
         if (by >= 0 && by < ny && bz >= 0 && bz < nz) {
-            const uint32_t rb = cb + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
-            gb = a.offsets[rb + xa];
-            len = a.offsets[rb + xb + 1] - gb;
+            const uint32_t row = (uint32_t)by + (uint32_t)ny * (uint32_t)bz;
+            const uint32_t rb = cb + (uint32_t)nx * row;
+            const uint32_t s0 = a.offsets[rb + xa];
+            len = a.offsets[rb + xb + 1] - s0;
+            gb = s0 + ROW_PADS * (d.row_base + row);  // P index
         }
     }
     // staged rows follow each other with ROW_PAD sentinel slots after each
@@ -476,10 +478,11 @@ __device__ __forceinline__ void build_table(const InteractArgs& a, const SysDesc
         w[i] = make_uint2(0u, 0u);
         if (e < total && p.rlen[rr] > 0) {
             const int by = cy + rr % 3 - 1, bz = cz + rr / 3 - 1;
-            const uint32_t cidx =
-                d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz) + p.xa + k;
+            const uint32_t row = (uint32_t)by + (uint32_t)ny * (uint32_t)bz;
+            const uint32_t cidx = d.cell_base + (uint32_t)nx * row + p.xa + k;
             // mode 0: staged index = sbeg + (P index - gbeg); mode 1: P index
-            const uint32_t shift = sizeof(E) == 2 ? (uint32_t)p.sbeg[rr] - p.gbeg[rr] : 0u;
+            const uint32_t shift = ROW_PADS * (d.row_base + row) +
+                                   (sizeof(E) == 2 ? (uint32_t)p.sbeg[rr] - p.gbeg[rr] : 0u);
             start[i] = a.offsets[cidx] + shift;
             if (k < ncell) w[i] = a.xbins[cidx];
         }
@@ -866,8 +869,9 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
                 phase ^= 1u;
             }
             __syncthreads();  // tables ready; sm.failed is uniform from here on
-            const uint32_t tb = a.offsets[rb0 + x0], te = a.offsets[rb0 + x1];
-            const int ntarget = (int)(te - tb);
+            const uint32_t tb0 = a.offsets[rb0 + x0], te = a.offsets[rb0 + x1];
+            const int ntarget = (int)(te - tb0);
+            const uint32_t tb = tb0 + ROW_PADS * (d.row_base + row);  // P index of the first target
             // staged index of the first target (the centre row is row 4)
             const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
             const int base = XSUB * p.xa;
@@ -1037,8 +1041,9 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
                 build_table<32>(a, d, p, cy, cz, ncell, st.tbl.global, &st.coarse_mask, lane);
             }
             if (lane == 0) {
-                const uint32_t tb = a.offsets[rb0 + x0];
-                const int nt = (int)(a.offsets[rb0 + x1] - tb);
+                const uint32_t tb0 = a.offsets[rb0 + x0];
+                const int nt = (int)(a.offsets[rb0 + x1] - tb0);
+                const uint32_t tb = tb0 + ROW_PADS * (d.row_base + row);  // P index
                 st.d = d;
                 st.t = t;
                 st.cy = cy;
@@ -1163,8 +1168,8 @@ __device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_
     return start + ((word >> (8 * ((sub - 1) & 3))) & 255u);
 }
 
-// The 9 x-windows of one target as ranges of P (see target_windows; here
-// the lookups read global memory).
+// The 9 x-windows of one target as ranges of P indices (see target_windows;
+// here the lookups read global memory).
 __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, const SysDesc& d, const float4& t,
                                                       int cx, int cy, int cz, uint32_t (&j)[9],
                                                       uint32_t (&je)[9])
@@ -1187,18 +1192,13 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
         if (by < 0 || by >= ny || bz < 0 || bz >= nz || !(tw > 0.f)) continue;
         const float tt = fmaxf(tw, 1e-30f);
         const float w = tt * rsqrtf(tt) + slack;
-        const uint32_t rb = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
+        const uint32_t row = (uint32_t)by + (uint32_t)ny * (uint32_t)bz;
+        const uint32_t rb = d.cell_base + (uint32_t)nx * row, pad = ROW_PADS * (d.row_base + row);
         const int b0 = sub_bin(t.x - w, xlo, invs, 0, lo, hi);
         const int b1 = sub_bin(t.x + w, xlo, invs, 0, lo, hi) + 1;
-        j[rr] = sub_bin_start(a, rb, b0, false);
-        je[rr] = sub_bin_start(a, rb, b1, true);
+        j[rr] = sub_bin_start(a, rb, b0, false) + pad;
+        je[rr] = sub_bin_start(a, rb, b1, true) + pad;
     }
-}
-
-// A source of P, or the sentinel P[n] for slots past a window's end.
-__device__ __forceinline__ float4 ldg_src(const float4* P, uint32_t k, uint32_t end, uint32_t n)
-{
-    return __ldg(P + (k < end ? k : n));
 }
 
 // Targets a and b (b may repeat a) of one row, their union windows in column
@@ -1230,7 +1230,6 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     // nw >= 1: the window of a's own row holds a
     const float rc2 = d.rc2;
     const float2 ks = make_float2(kp.t, kp.t);
-    const uint32_t n = a.n;
     PairSums ps;
     // the window words of this column by shared-window address (the
     // switch is written as selects: a lane leaves after its last window
@@ -1240,9 +1239,11 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     const uint32_t we = wb + (uint32_t)nw * WSTEP;
     uint32_t wa = wb;
     uint32_t c = lds_u32(wa), ce = lds_u32(wa + WT * 4u);
+    // the up to three slots read past a window's end are the same row
+    // outside the windows or the row's sentinel slots: exact zeros
     do {
-        const float4 s0 = __ldg(a.P + c), s1 = ldg_src(a.P, c + 1u, ce, n), s2 = ldg_src(a.P, c + 2u, ce, n),
-                     s3 = ldg_src(a.P, c + 3u, ce, n);
+        const float4* q = a.P + c;
+        const float4 s0 = __ldg(q), s1 = __ldg(q + 1), s2 = __ldg(q + 2), s3 = __ldg(q + 3);
         ps.cand(s0, ta, tb, rc2, ks);
         ps.cand(s1, ta, tb, rc2, ks);
         ps.cand(s2, ta, tb, rc2, ks);
@@ -1264,14 +1265,22 @@ __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs
     // keep the work counters of the tiled launches in step (see k_interact_tiled)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
-    const uint32_t p = blockIdx.x * DIRECT_THREADS + threadIdx.x;
-    const uint32_t ka = 2u * p;
-    if (ka >= a.n) return;
-    const float4 ta = __ldg(a.P + ka);
-    const bool has_b = ka + 1u < a.n;
-    const float4 t1 = has_b ? __ldg(a.P + ka + 1u) : ta;
-    const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.pbase, a.sy.S, ka);
-    const int sid1 = (a.sy.S == 1 || !has_b) ? sid : find_system(a.sy.pbase, a.sy.S, ka + 1u);
+    // slots 2p and 2p + 1 of P; sentinel slots (slot word all ones) are no targets
+    const uint32_t ka = 2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
+    if (ka >= a.np) return;
+    float4 ta = __ldg(a.P + ka);
+    float4 t1 = ka + 1u < a.np ? __ldg(a.P + ka + 1u) : ta;
+    constexpr uint32_t NONE = 0xffffffffu;
+    bool has_a = __float_as_uint(ta.w) != NONE, has_b = ka + 1u < a.np && __float_as_uint(t1.w) != NONE;
+    if (!has_a) {
+        if (!has_b) return;
+        ta = t1;
+        has_a = true;
+        has_b = false;
+    }
+    // the system of a target: from its stable slot (= sorted index)
+    const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.pbase, a.sy.S, __float_as_uint(ta.w));
+    const int sid1 = (a.sy.S == 1 || !has_b) ? sid : find_system(a.sy.pbase, a.sy.S, __float_as_uint(t1.w));
     const SysDesc& d = a.sy.sys[sid];
     const Grid& g = d.g;
     const int cxa = axis_cell(ta.x, g.lo[0], g.inv_w[0], g.n[0]);
@@ -1348,7 +1357,7 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
                 case 4: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 5:
                     if constexpr (std::is_same<Acc, PlainAcc>::value) {
-                        const uint64_t pairs = ((uint64_t)a.n + 1) / 2;
+                        const uint64_t pairs = ((uint64_t)a.np + 1) / 2;
                         k_interact_direct<<<(unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS),
                                             DIRECT_THREADS, 0, s>>>(a);
                     } else {

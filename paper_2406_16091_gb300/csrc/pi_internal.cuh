@@ -9,7 +9,7 @@
 // Layout of the device state (one cudaMalloc arena):
 //   Ctrl            control words (scan ticket, error bits, M_C, row counters)
 //   counts[C]       particles per cell (C = cells of all systems)
-//   xbins[C]        per cell, where its XSUB x-sub-bins start in P (k_stabilise)
+//   xbins[C]        per cell, where its XSUB x-sub-bins start (k_stabilise)
 //   pbase[S+1]      first particle of each system in the current step
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
@@ -63,7 +63,14 @@ struct SysDesc {
     uint32_t cell_base;
     uint32_t work_base;  // first work item of the tiled interaction
     uint32_t nseg;       // work items per X-row: segments of SEG_CELLS cells
+    uint32_t row_base;   // first X-row (rows are counted over all systems)
 };
+
+// P holds the sorted particles with ROW_PADS sentinel slots after every
+// X-row: sorted index k of X-row r (global) is P index k + ROW_PADS * r.
+// Loops that read four sources at a time may then run up to three slots
+// past a window's end without leaving the row's particles and sentinels.
+constexpr int ROW_PADS = 3;
 
 // The tiled interaction's work items are segments of SEG_CELLS consecutive
 // cells of an X-row; rows longer than that are split so that heavy rows do
@@ -78,6 +85,7 @@ struct Systems {
     const uint32_t* pbase;  // [S+1] first particle (= first sorted slot) of each system
     const uint32_t* cbase;  // [S+1] first cell
     const uint32_t* wbase;  // [S+1] first work item of the tiled interaction
+    const uint32_t* rbase;  // [S+1] first X-row
     int S;
 };
 
@@ -191,8 +199,8 @@ cudaError_t launch_total_f64(const float* v, const Systems& sy, double* partial,
 
 // Writes one system's constants (system 0 of a context) from launch
 // parameters: sys[0] = d, cbase[1] = cells, wbase[1] = work items.
-cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, const SysDesc& d,
-                              uint32_t cells, uint32_t work, cudaStream_t s);
+cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uint32_t* rbase,
+                              const SysDesc& d, uint32_t cells, uint32_t work, uint32_t rows, cudaStream_t s);
 
 // Per-system scale of the interaction kernel, written from launch parameters
 // (vals[s] for s < S) into kscale.
@@ -211,6 +219,7 @@ struct InteractArgs {
     const uint32_t* offsets;
     const uint32_t* perm;
     uint32_t n;             // particles of all systems
+    uint32_t np;            // entries of P: n plus ROW_PADS per X-row
     uint32_t work;          // work items (X-row segments) of all systems
     const float* kscale;    // [S]: Gaussian K = 2^(r2 * kscale[s]); Lennard-Jones sigma^2
     float kscale0;          // the scale when S == 1 (kscale may then be null)
