@@ -141,7 +141,7 @@ pi_status pi_destroy(pi_ctx* ctx);
  * that leaves an empty grid.  Enqueues, on `stream`:
  *   a1/a2  cell index of each particle, cell = cx + nx*(cy + ny*cz) with
  *          c_d = clamp(floor((x_d - lo_d) * inv_w_d), 0, n_d - 1) in FP32,
- *          and a warp-aggregated atomic count per cell;
+ *          and an atomic count per cell;
  *   a3     a single-pass exclusive scan (C+1 offsets, offsets[C] = n) that
  *          also records M_C, the largest cell count (Sec. 5.1);
  *   a4     a stable scatter: inside a cell, particles keep input order.

@@ -1,9 +1,9 @@
 // pi_bin.cu -- binning kernels (arXiv 2406.16091, Sec. 2 and Fig. 1).
 //
 //   k_zero       clears the control block and the per-cell counts
-//   k_hist       a1 + a2: cell index of each particle (float4 SoA loads) and a
-//                warp-aggregated atomic histogram; the value returned by the
-//                atomic is kept as a provisional slot inside the cell
+//   k_hist       a1 + a2: cell index of each particle (float4 SoA loads) and an
+//                atomic histogram, one atomicAdd per particle; the value it
+//                returns is kept as a provisional slot inside the cell
 //   k_scan       a3: single-pass exclusive scan over the C+1 counts with
 //                decoupled lookback (dynamic tile ticket, bounded waits), and
 //                M_C, the largest count (Sec. 5.1 keeps it during the scan)
@@ -12,8 +12,8 @@
 //                inside a cell is arbitrary)
 //   k_stabilise  a4, second half: rank each particle among its cell's members
 //                by input index, which makes the order stable; write the
-//                sorted positions, the per-cell x-ordered copy P that the
-//                tiled interaction stages, and each cell's x-sub-bin starts
+//                sorted positions, the row-padded x-ordered copy P that the
+//                interaction reads, and each cell's x-sub-bin starts
 //
 // All kernels are HBM- or L2-bound integer work; none uses tensor cores.
 #include <mutex>
@@ -39,8 +39,9 @@ __global__ void k_zero(ZeroArgs<NB> z)
 }
 
 // a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
-// float4 per component when the arrays are 16-byte aligned.  The of each particle comes from the particle bases; its cell is offset
-// by the system's first cell.
+// float4 per component when the arrays are 16-byte aligned.  The system of
+// each particle comes from the particle bases; its cell is offset by the
+// system's first cell.
 __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               const float* __restrict__ y,
                                               const float* __restrict__ z, uint32_t n, Systems sy,
