@@ -54,24 +54,32 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// Accumulators.  add(t, in) adds the term t of a candidate that passed the
+// pair test (in) or the exact zero of one that did not (!in); both leave the
+// sum exactly as it was for a zero, so that candidates outside a target's
+// own windows never change its sums.
 struct PlainAcc {
     float v = 0.f;
-    __device__ __forceinline__ void add(float t) { v += t; }
-    __device__ __forceinline__ void addmul(float a, float b) { v = fmaf(a, b, v); }
+    __device__ __forceinline__ void add(float t, bool) { v = __fadd_rn(v, t); }
+    __device__ __forceinline__ void addmul(float a, float b, bool) { v = __fmaf_rn(a, b, v); }
     __device__ __forceinline__ float value() const { return v; }
 };
 
-// Kahan-compensated FP32 accumulation (precision mode).
+// Kahan-compensated FP32 accumulation (precision mode).  A rejected
+// candidate is skipped altogether: a compensated add of zero would fold the
+// pending compensation into the sum, making the result depend on how many
+// rejected candidates a path reads.
 struct KahanAcc {
     float v = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float t)
+    __device__ __forceinline__ void add(float t, bool in)
     {
-        float y = __fsub_rn(t, c);
-        float u = __fadd_rn(v, y);
-        c = __fsub_rn(__fsub_rn(u, v), y);
-        v = u;
+        const float y = __fsub_rn(t, c);
+        const float u = __fadd_rn(v, y);
+        const float c1 = __fsub_rn(__fsub_rn(u, v), y);
+        v = in ? u : v;
+        c = in ? c1 : c;
     }
-    __device__ __forceinline__ void addmul(float a, float b) { add(__fmul_rn(a, b)); }
+    __device__ __forceinline__ void addmul(float a, float b, bool in) { add(__fmul_rn(a, b), in); }
     __device__ __forceinline__ float value() const { return v; }
 };
 
@@ -121,10 +129,10 @@ struct Sums {
 
     __device__ __forceinline__ void add(float dx, float dy, float dz, float K, bool in)
     {
-        s.add(K);
-        vx.addmul(dx, K);
-        vy.addmul(dy, K);
-        vz.addmul(dz, K);
+        s.add(K, in);
+        vx.addmul(dx, K, in);
+        vy.addmul(dy, K, in);
+        vz.addmul(dz, K, in);
         n += in ? 1u : 0u;
     }
 
@@ -591,39 +599,101 @@ __device__ __forceinline__ float lt_mask(float a, float b)
     return m;
 }
 
+// 1.0f if a < b and u != v, else 0.0f: the pair test of the kernels that
+// exclude the self pair by identity (u, v the slots of source and target).
+__device__ __forceinline__ float lt_ne_mask(float a, float b, float u, float v)
+{
+    float m;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %3, %4;\n\t"
+        "set.lt.and.f32.f32 %0, %1, %2, p;\n\t}"
+        : "=f"(m) : "f"(a), "f"(b), "r"(__float_as_uint(u)), "r"(__float_as_uint(v)));
+    return m;
+}
+
 // Two targets a and b against one candidate source with packed FP32
 // (f32x2) arithmetic: element .x belongs to target a, .y to target b, and
 // every element is rounded exactly as the scalar steps of Sums::pair_nb
 // round it, candidate after candidate, so each target's sums are those of
-// the sequential scalar loop.  The pair test gives a 1/0 mask m; K =
-// 2^(r2 t) * m and n += m.  2^(r2 t) lies in [0, 1] for every finite
-// candidate, so K is the kernel value or exactly +0, and adding +0 leaves a
-// sum as it was: candidates outside a target's own window (the other
-// target's, a row's sentinel slots) change nothing.
-struct PairSums {
+// the sequential scalar loop.  The pair test gives a 1/0 mask m and the
+// term is K = value * m, so a candidate that fails it (the other target's,
+// a row's sentinel slots, the target itself where it is excluded by
+// identity) contributes an exact zero, which leaves the plain sums as they
+// were.  The compensated sums take the same zero through the mask: with
+// y = t - c*m, u = v + y, c' = (u - v) - y and c <- c*(1 - m) + c', a
+// rejected candidate leaves v and c unchanged (up to the sign of a zero c)
+// and an accepted one is the Kahan step exactly.  Compensations are kept
+// negated (cn = -c) so that every step is one add or fma.
+template <class Acc, int KERNEL>
+struct PairSumsT {
+    static constexpr bool kahan = std::is_same<Acc, KahanAcc>::value;
+    static constexpr bool by_id = self_by_identity<KERNEL, Acc>();
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
+    float2 cs = make_float2(0.f, 0.f), cx = make_float2(0.f, 0.f), cy = make_float2(0.f, 0.f),
+           cz = make_float2(0.f, 0.f);
+
+    __device__ __forceinline__ static void comp_add(float2& v, float2& cn, float2 t, float2 m, float2 nm)
+    {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 y = __ffma2_rn(cn, m, t);      // t - c (t when rejected)
+        const float2 u = __fadd2_rn(v, y);
+        const float2 d = __ffma2_rn(v, m1, u);      // u - v
+        const float2 cn1 = __ffma2_rn(d, m1, y);    // -((u - v) - y)
+        cn = __ffma2_rn(cn, nm, cn1);
+        v = u;
+    }
 
     __device__ __forceinline__ void cand(const float4& p, const float4& ta, const float4& tb, float rc2,
-                                         float2 ks)
+                                         float2 ks, const KParams& kp)
     {
         // offsets by scalar subtractions straight into register pairs
         const float2 dx = make_float2(__fsub_rn(p.x, ta.x), __fsub_rn(p.x, tb.x));
         const float2 dy = make_float2(__fsub_rn(p.y, ta.y), __fsub_rn(p.y, tb.y));
         const float2 dz = make_float2(__fsub_rn(p.z, ta.z), __fsub_rn(p.z, tb.z));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 t = __fmul2_rn(r2, ks);
-        const float2 m = make_float2(lt_mask(r2.x, rc2), lt_mask(r2.y, rc2));
-        const float2 K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
-        s = __fadd2_rn(s, K);
-        vx = __ffma2_rn(dx, K, vx);
-        vy = __ffma2_rn(dy, K, vy);
-        vz = __ffma2_rn(dz, K, vz);
+        float2 m;
+        if constexpr (by_id)
+            m = make_float2(lt_ne_mask(r2.x, rc2, p.w, ta.w), lt_ne_mask(r2.y, rc2, p.w, tb.w));
+        else
+            m = make_float2(lt_mask(r2.x, rc2), lt_mask(r2.y, rc2));
+        float2 K;
+        if constexpr (KERNEL == KERNEL_GAUSSIAN) {
+            const float2 t = __fmul2_rn(r2, ks);
+            K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
+        } else if constexpr (KERNEL == KERNEL_LOWFLOP) {
+            K = m;
+        } else {
+            // kernel_value's Lennard-Jones steps, element by element
+            const float2 rs2 = __ffma2_rn(make_float2(0.01f, 0.01f), ks, r2);
+            const float2 sr = __fmul2_rn(ks, make_float2(__frcp_rn(rs2.x), __frcp_rn(rs2.y)));
+            const float2 s3 = __fmul2_rn(__fmul2_rn(sr, sr), sr);
+            const float2 q = __ffma2_rn(s3, make_float2(-1.f, -1.f), __fmul2_rn(s3, s3));
+            float2 e = __fmul2_rn(make_float2(4.0f, 4.0f), q);
+            if constexpr (KERNEL == KERNEL_HIGHFLOP) {
+                const float2 one = make_float2(kp.one, kp.one), zero = make_float2(kp.zero, kp.zero);
+#pragma unroll
+                for (int i = 0; i < 75; ++i) e = __ffma2_rn(e, one, zero);
+            }
+            K = __fmul2_rn(e, m);
+        }
+        if constexpr (!kahan) {
+            s = __fadd2_rn(s, K);
+            vx = __ffma2_rn(dx, K, vx);
+            vy = __ffma2_rn(dy, K, vy);
+            vz = __ffma2_rn(dz, K, vz);
+        } else {
+            const float2 nm = __ffma2_rn(m, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+            comp_add(s, cs, K, m, nm);
+            comp_add(vx, cx, __fmul2_rn(dx, K), m, nm);
+            comp_add(vy, cy, __fmul2_rn(dy, K), m, nm);
+            comp_add(vz, cz, __fmul2_rn(dz, K), m, nm);
+        }
         n = __fadd2_rn(n, m);
     }
 
     // target a's (second = false) or b's sums into r
-    __device__ __forceinline__ void to(Sums<PlainAcc, KERNEL_GAUSSIAN>& r, bool second) const
+    __device__ __forceinline__ void to(Sums<Acc, KERNEL>& r, bool second) const
     {
         r.s.v = second ? s.y : s.x;
         r.vx.v = second ? vx.y : vx.x;
@@ -632,6 +702,8 @@ struct PairSums {
         r.n = (uint32_t)(second ? n.y : n.x);  // exact: at most 2^24 neighbours
     }
 };
+
+using PairSums = PairSumsT<PlainAcc, KERNEL_GAUSSIAN>;
 
 template <class Acc, int KERNEL>
 __host__ __device__ constexpr bool packed_path()
@@ -703,10 +775,10 @@ __device__ __forceinline__ void target_pair_sums_staged(const float4* buf, const
     // slots) add exact zeros.
     do {
         const float4 s0 = lds_f4(c), s1 = lds_f4(c + 16u), s2 = lds_f4(c + 32u), s3 = lds_f4(c + 48u);
-        ps.cand(s0, ta, tb, rc2, ks);
-        ps.cand(s1, ta, tb, rc2, ks);
-        ps.cand(s2, ta, tb, rc2, ks);
-        ps.cand(s3, ta, tb, rc2, ks);
+        ps.cand(s0, ta, tb, rc2, ks, kp);
+        ps.cand(s1, ta, tb, rc2, ks, kp);
+        ps.cand(s2, ta, tb, rc2, ks, kp);
+        ps.cand(s3, ta, tb, rc2, ks, kp);
         c += 64u;
         const bool sw = c >= ce;
         wa += sw ? WSTEP : 0u;
@@ -1203,12 +1275,11 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
 
 // Targets a and b (b may repeat a) of one row, their union windows in column
 // `col` of `win`, summed like pair_loop with sources from global memory.
-template <int WT>
+template <int WT, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
                                             unsigned col, const float4& ta, const float4& tb, int cxa, int cxb,
-                                            int cy, int cz, const KParams& kp,
-                                            Sums<PlainAcc, KERNEL_GAUSSIAN>& ra,
-                                            Sums<PlainAcc, KERNEL_GAUSSIAN>& rb)
+                                            int cy, int cz, const KParams& kp, Sums<Acc, KERNEL>& ra,
+                                            Sums<Acc, KERNEL>& rb)
 {
     int nw = 0;
     {
@@ -1230,7 +1301,7 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     // nw >= 1: the window of a's own row holds a
     const float rc2 = d.rc2;
     const float2 ks = make_float2(kp.t, kp.t);
-    PairSums ps;
+    PairSumsT<Acc, KERNEL> ps;
     // the window words of this column by shared-window address (the
     // switch is written as selects: a lane leaves after its last window
     // without waiting for the others at the end of each row)
@@ -1244,10 +1315,10 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     do {
         const float4* q = a.P + c;
         const float4 s0 = __ldg(q), s1 = __ldg(q + 1), s2 = __ldg(q + 2), s3 = __ldg(q + 3);
-        ps.cand(s0, ta, tb, rc2, ks);
-        ps.cand(s1, ta, tb, rc2, ks);
-        ps.cand(s2, ta, tb, rc2, ks);
-        ps.cand(s3, ta, tb, rc2, ks);
+        ps.cand(s0, ta, tb, rc2, ks, kp);
+        ps.cand(s1, ta, tb, rc2, ks, kp);
+        ps.cand(s2, ta, tb, rc2, ks, kp);
+        ps.cand(s3, ta, tb, rc2, ks, kp);
         c += 4u;
         const bool sw = c >= ce;
         wa += sw ? WSTEP : 0u;
@@ -1259,6 +1330,7 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
     ps.to(rb, true);
 }
 
+template <class Acc, int KERNEL>
 __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs a)
 {
     __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
@@ -1292,12 +1364,16 @@ __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs
     const bool together = has_b && sid1 == sid && axis_cell(t1.y, g.lo[1], g.inv_w[1], g.n[1]) == cy &&
                           axis_cell(t1.z, g.lo[2], g.inv_w[2], g.n[2]) == cz;
     const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
-    const float kself = ex2_approx(0.f);
-    Sums<PlainAcc, KERNEL_GAUSSIAN> ra, rb;
+    // the self pair's contribution, taken off at the end (0 where the pair
+    // test excludes it by identity)
+    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
+    const float kself = by_id ? 0.f : (KERNEL == KERNEL_LOWFLOP ? 1.0f : ex2_approx(0.f));
+    const uint32_t nself = by_id ? 0u : 1u;
+    Sums<Acc, KERNEL> ra, rb;
     direct_pair(a, d, win, threadIdx.x, ta, together ? t1 : ta, cxa, together ? cxb : cxa, cy, cz, kp, ra, rb);
-    store_out(a, __float_as_uint(ta.w), ra, kself, 1u);
+    store_out(a, __float_as_uint(ta.w), ra, kself, nself);
     if (together) {
-        store_out(a, __float_as_uint(t1.w), rb, kself, 1u);
+        store_out(a, __float_as_uint(t1.w), rb, kself, nself);
     } else if (has_b) {
         const SysDesc& d1 = a.sy.sys[sid1];
         const Grid& g1 = d1.g;
@@ -1306,8 +1382,16 @@ __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs
         const int cy1 = axis_cell(t1.y, g1.lo[1], g1.inv_w[1], g1.n[1]);
         const int cz1 = axis_cell(t1.z, g1.lo[2], g1.inv_w[2], g1.n[2]);
         direct_pair(a, d1, win, threadIdx.x, t1, t1, cx1, cx1, cy1, cz1, kp1, rb, ra);
-        store_out(a, __float_as_uint(t1.w), rb, kself, 1u);
+        store_out(a, __float_as_uint(t1.w), rb, kself, nself);
     }
+}
+
+template <class Acc, int KERNEL>
+void launch_direct_one(const InteractArgs& a, cudaStream_t s)
+{
+    const uint64_t pairs = ((uint64_t)a.np + 1) / 2;
+    k_interact_direct<Acc, KERNEL>
+        <<<(unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS), DIRECT_THREADS, 0, s>>>(a);
 }
 
 template <class Acc>
@@ -1339,31 +1423,32 @@ template <class Acc>
 cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
                              cudaStream_t s)
 {
-    // the other kernels are comparators: they run with the 128-thread shape
-    if (a.kernel != KERNEL_GAUSSIAN) tile = 2;
+    // the comparator kernels run on the direct kernel or the 128-thread shape
+    if (a.kernel != KERNEL_GAUSSIAN && tile != 5) tile = 2;
     uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
+    const bool direct = tile == 5;
     switch (a.kernel) {
-        case KERNEL_LJ: launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s); break;
-        case KERNEL_LOWFLOP: launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s); break;
-        case KERNEL_HIGHFLOP: launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s); break;
+        case KERNEL_LJ:
+            direct ? launch_direct_one<Acc, KERNEL_LJ>(a, s) : launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s);
+            break;
+        case KERNEL_LOWFLOP:
+            direct ? launch_direct_one<Acc, KERNEL_LOWFLOP>(a, s)
+                   : launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s);
+            break;
+        case KERNEL_HIGHFLOP:
+            direct ? launch_direct_one<Acc, KERNEL_HIGHFLOP>(a, s)
+                   : launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s);
+            break;
         default:
             switch (tile) {
                 case 0: launch_tiled_one<TileS, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 1: launch_tiled_one<TileM, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 2: launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 4: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
-                case 5:
-                    if constexpr (std::is_same<Acc, PlainAcc>::value) {
-                        const uint64_t pairs = ((uint64_t)a.np + 1) / 2;
-                        k_interact_direct<<<(unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS),
-                                            DIRECT_THREADS, 0, s>>>(a);
-                    } else {
-                        launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s);  // packed path only
-                    }
-                    break;
+                case 5: launch_direct_one<Acc, KERNEL_GAUSSIAN>(a, s); break;
                 default: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
             }
             break;

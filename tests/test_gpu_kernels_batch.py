@@ -15,17 +15,44 @@ KERNELS = [(B.PI_KERNEL_LJ, oracle.LJ), (B.PI_KERNEL_LOWFLOP, oracle.LOWFLOP),
            (B.PI_KERNEL_HIGHFLOP, oracle.HIGHFLOP), (B.PI_KERNEL_GAUSSIAN, oracle.GAUSSIAN)]
 
 
-@pytest.mark.parametrize("algo", [B.PI_ALGO_TILED, B.PI_ALGO_PPNL])
+# (algorithm, tile shape): the staged one-target shape, the direct kernel
+# (two targets per thread, packed), Alg. 1
+PATHS = [(B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 5), (B.PI_ALGO_PPNL, None)]
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["staged", "direct", "ppnl"])
 @pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
-def test_kernel_parity(algo, kern, precision):
+def test_kernel_parity(path, kern, precision):
     gk, ok = kern
+    algo, tile = path
     w = W.scaled(W.SMALL, 20000)
     x, y, z = w.positions()
     b, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h, ok)
-    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, algo=algo, precision=precision, kernel=gk)
+    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, algo=algo, precision=precision, kernel=gk, tile=tile)
     check_binning(g, b)
     check_interaction(g, r)
+
+
+@pytest.mark.parametrize("kern", KERNELS)
+@pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
+def test_staged_and_direct_paths_bitwise_equal(kern, precision):
+    """Every target's terms are summed in the order of its own windows on
+    every path; candidates a path reads beyond them (the other target's of a
+    packed pair, sentinel slots, the target itself) are exact no-ops, also
+    for the compensated sums.  So the one-target staged path and the packed
+    two-target direct kernel agree bit for bit, for every kernel and both
+    precision modes, on a clustered layout with dense cells."""
+    gk, ok = kern
+    w = W.scaled(W.CLUSTERED, 40000)
+    x, y, z = w.positions()
+    _, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h, ok)
+    res = {t: run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, precision=precision, kernel=gk, tile=t, binned=False)
+           for t in (0, 2, 3, 5)}
+    for t in (0, 3, 5):
+        for k in ("S", "Vx", "Vy", "Vz", "nbr"):
+            assert np.array_equal(res[2][k].view(np.uint32), res[t][k].view(np.uint32)), (t, k)
+    check_interaction(res[5], r)
 
 
 def _systems(seed=5):
