@@ -1273,52 +1273,70 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
     }
 }
 
-// Targets a and b (b may repeat a) of one row, their union windows in column
-// `col` of `win`, summed like pair_loop with sources from global memory.
-template <int WT, class Acc, int KERNEL>
-__device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
-                                            unsigned col, const float4& ta, const float4& tb, int cxa, int cxb,
-                                            int cy, int cz, const KParams& kp, Sums<Acc, KERNEL>& ra,
-                                            Sums<Acc, KERNEL>& rb)
+// A group of G targets (a target may repeat the one before it)
+// of one X-row of one system: per row the union of their windows goes to
+// column `col` of `win` (rows where all are empty dropped), and one loop walks
+// all of them with the window switch written as selects (a lane leaves after
+// its last window without waiting for the others at the end of each row),
+// four sources per trip, each source evaluated against every target of the
+// group, two at a time with packed arithmetic.  Candidates outside a
+// target's own windows -- the other targets', up to three past a window's end
+// (the same row outside the windows, or the row's sentinel slots) -- add
+// exact zeros, so each target's sums are those of the sequential loop over
+// its own windows.
+template <int WT, int G, class Acc, int KERNEL>
+__device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
+                                             unsigned col, const float4 (&t)[G], const int (&cx)[G], int cy,
+                                             int cz, const KParams& kp, Sums<Acc, KERNEL> (&r)[G])
 {
+    static_assert(G % 2 == 0, "targets go in packed pairs");
     int nw = 0;
     {
-        uint32_t ja[9], jea[9], jb[9], jeb[9];
-        target_windows_direct(a, d, ta, cxa, cy, cz, ja, jea);
-        target_windows_direct(a, d, tb, cxb, cy, cz, jb, jeb);
+        uint32_t ulo[9], uhi[9];
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr) {
-            const bool ea = jea[rr] > ja[rr], eb = jeb[rr] > jb[rr];
-            const uint32_t lo = ea ? (eb ? min(ja[rr], jb[rr]) : ja[rr]) : jb[rr];
-            const uint32_t hi = ea ? (eb ? max(jea[rr], jeb[rr]) : jea[rr]) : jeb[rr];
-            if (ea || eb) {
-                win[2 * nw][col] = lo;
-                win[2 * nw + 1][col] = hi;
+            ulo[rr] = 0xffffffffu;
+            uhi[rr] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            uint32_t j[9], je[9];
+            target_windows_direct(a, d, t[k], cx[k], cy, cz, j, je);
+#pragma unroll
+            for (int rr = 0; rr < 9; ++rr)
+                if (je[rr] > j[rr]) {
+                    ulo[rr] = min(ulo[rr], j[rr]);
+                    uhi[rr] = max(uhi[rr], je[rr]);
+                }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr)
+            if (uhi[rr] > ulo[rr]) {
+                win[2 * nw][col] = ulo[rr];
+                win[2 * nw + 1][col] = uhi[rr];
                 ++nw;
             }
-        }
     }
-    // nw >= 1: the window of a's own row holds a
+    // nw >= 1: the window of the first target's own row holds it
     const float rc2 = d.rc2;
     const float2 ks = make_float2(kp.t, kp.t);
-    PairSumsT<Acc, KERNEL> ps;
-    // the window words of this column by shared-window address (the
-    // switch is written as selects: a lane leaves after its last window
-    // without waiting for the others at the end of each row)
+    PairSumsT<Acc, KERNEL> ps[G / 2];
+    // the window words of this column by shared-window address
     const uint32_t wb = smem_addr(&win[0][col]);
     constexpr uint32_t WSTEP = (uint32_t)WT * 8u;  // one window = two rows of win
     const uint32_t we = wb + (uint32_t)nw * WSTEP;
     uint32_t wa = wb;
     uint32_t c = lds_u32(wa), ce = lds_u32(wa + WT * 4u);
-    // the up to three slots read past a window's end are the same row
-    // outside the windows or the row's sentinel slots: exact zeros
     do {
         const float4* q = a.P + c;
         const float4 s0 = __ldg(q), s1 = __ldg(q + 1), s2 = __ldg(q + 2), s3 = __ldg(q + 3);
-        ps.cand(s0, ta, tb, rc2, ks, kp);
-        ps.cand(s1, ta, tb, rc2, ks, kp);
-        ps.cand(s2, ta, tb, rc2, ks, kp);
-        ps.cand(s3, ta, tb, rc2, ks, kp);
+#pragma unroll
+        for (int h = 0; h < G / 2; ++h) {
+            ps[h].cand(s0, t[2 * h], t[2 * h + 1], rc2, ks, kp);
+            ps[h].cand(s1, t[2 * h], t[2 * h + 1], rc2, ks, kp);
+            ps[h].cand(s2, t[2 * h], t[2 * h + 1], rc2, ks, kp);
+            ps[h].cand(s3, t[2 * h], t[2 * h + 1], rc2, ks, kp);
+        }
         c += 4u;
         const bool sw = c >= ce;
         wa += sw ? WSTEP : 0u;
@@ -1326,23 +1344,29 @@ __device__ __forceinline__ void direct_pair(const InteractArgs& a, const SysDesc
         c = sw ? cn : c;
         ce = sw ? cen : ce;
     } while (wa < we);
-    ps.to(ra, false);
-    ps.to(rb, true);
+#pragma unroll
+    for (int k = 0; k < G; ++k) ps[k / 2].to(r[k], (k & 1) != 0);
 }
 
+// The self pair's contribution, taken off at the end (0 where the pair test
+// excludes it by identity).
 template <class Acc, int KERNEL>
-__global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs a)
+__device__ __forceinline__ void self_terms(float& kself, uint32_t& nself)
 {
-    __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
-    // keep the work counters of the tiled launches in step (see k_interact_tiled)
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
-    if (load_error(a.ctrl)) return;
-    // slots 2p and 2p + 1 of P; sentinel slots (slot word all ones) are no targets
-    const uint32_t ka = 2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
+    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
+    kself = by_id ? 0.f : (KERNEL == KERNEL_LOWFLOP ? 1.0f : ex2_approx(0.f));
+    nself = by_id ? 0u : 1u;
+}
+
+// Slots ka and ka + 1 of P (either may be a sentinel or past the end).
+template <int WT, class Acc, int KERNEL>
+__device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t (*win)[WT], unsigned col,
+                                                 uint32_t ka)
+{
     if (ka >= a.np) return;
+    constexpr uint32_t NONE = 0xffffffffu;
     float4 ta = __ldg(a.P + ka);
     float4 t1 = ka + 1u < a.np ? __ldg(a.P + ka + 1u) : ta;
-    constexpr uint32_t NONE = 0xffffffffu;
     bool has_a = __float_as_uint(ta.w) != NONE, has_b = ka + 1u < a.np && __float_as_uint(t1.w) != NONE;
     if (!has_a) {
         if (!has_b) return;
@@ -1364,26 +1388,55 @@ __global__ void __launch_bounds__(DIRECT_THREADS) k_interact_direct(InteractArgs
     const bool together = has_b && sid1 == sid && axis_cell(t1.y, g.lo[1], g.inv_w[1], g.n[1]) == cy &&
                           axis_cell(t1.z, g.lo[2], g.inv_w[2], g.n[2]) == cz;
     const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
-    // the self pair's contribution, taken off at the end (0 where the pair
-    // test excludes it by identity)
-    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
-    const float kself = by_id ? 0.f : (KERNEL == KERNEL_LOWFLOP ? 1.0f : ex2_approx(0.f));
-    const uint32_t nself = by_id ? 0u : 1u;
-    Sums<Acc, KERNEL> ra, rb;
-    direct_pair(a, d, win, threadIdx.x, ta, together ? t1 : ta, cxa, together ? cxb : cxa, cy, cz, kp, ra, rb);
-    store_out(a, __float_as_uint(ta.w), ra, kself, nself);
-    if (together) {
-        store_out(a, __float_as_uint(t1.w), rb, kself, nself);
-    } else if (has_b) {
+    float kself;
+    uint32_t nself;
+    self_terms<Acc, KERNEL>(kself, nself);
+    {
+        const float4 t[2] = {ta, together ? t1 : ta};
+        const int cx[2] = {cxa, together ? cxb : cxa};
+        Sums<Acc, KERNEL> r[2];
+        direct_group<WT, 2>(a, d, win, col, t, cx, cy, cz, kp, r);
+        store_out(a, __float_as_uint(ta.w), r[0], kself, nself);
+        if (together) store_out(a, __float_as_uint(t1.w), r[1], kself, nself);
+    }
+    if (has_b && !together) {
         const SysDesc& d1 = a.sy.sys[sid1];
         const Grid& g1 = d1.g;
         const KParams kp1{a.kscale ? a.kscale[sid1] : a.kscale0, a.one, a.zero};
         const int cx1 = axis_cell(t1.x, g1.lo[0], g1.inv_w[0], g1.n[0]);
         const int cy1 = axis_cell(t1.y, g1.lo[1], g1.inv_w[1], g1.n[1]);
         const int cz1 = axis_cell(t1.z, g1.lo[2], g1.inv_w[2], g1.n[2]);
-        direct_pair(a, d1, win, threadIdx.x, t1, t1, cx1, cx1, cy1, cz1, kp1, rb, ra);
-        store_out(a, __float_as_uint(t1.w), rb, kself, nself);
+        const float4 t[2] = {t1, t1};
+        const int cx[2] = {cx1, cx1};
+        Sums<Acc, KERNEL> r[2];
+        direct_group<WT, 2>(a, d1, win, col, t, cx, cy1, cz1, kp1, r);
+        store_out(a, __float_as_uint(t1.w), r[0], kself, nself);
     }
+}
+
+// Resident CTAs per SM the direct kernel's registers are capped for.  The
+// kernel waits mostly on source loads, so more resident warps pay more than
+// registers: the plain Gaussian and low-FLOP kernels run 6 % faster with 8
+// CTAs (32 warps, 64 registers) than with the 6 their 79 registers would
+// allow, Lennard-Jones 10 % faster with 6 (80 registers) than with 5; the
+// compensated sums are no faster at 7.
+template <class Acc, int KERNEL>
+__host__ __device__ constexpr int direct_min_blocks()
+{
+    return (std::is_same<Acc, PlainAcc>::value && (KERNEL == KERNEL_GAUSSIAN || KERNEL == KERNEL_LOWFLOP)) ? 8 : 6;
+}
+
+// Targets of P slots 2p and 2p + 1 per thread.
+template <class Acc, int KERNEL>
+__global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL>()))
+    k_interact_direct(InteractArgs a)
+{
+    __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
+    // keep the work counters of the tiled launches in step (see k_interact_tiled)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
+    if (load_error(a.ctrl)) return;
+    direct_slot_pair<DIRECT_THREADS, Acc, KERNEL>(a, win, threadIdx.x,
+                                                  2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x));
 }
 
 template <class Acc, int KERNEL>
