@@ -1241,10 +1241,12 @@ __device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_
 }
 
 // The 9 x-windows of one target as ranges of P indices (see target_windows;
-// here the lookups read global memory).
+// here the lookups read global memory), merged into the union windows
+// [ulo, uhi) of a group of targets: a non-empty window widens its row's
+// union, an empty one leaves it as it is.
 __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, const SysDesc& d, const float4& t,
-                                                      int cx, int cy, int cz, uint32_t (&j)[9],
-                                                      uint32_t (&je)[9])
+                                                      int cx, int cy, int cz, uint32_t (&ulo)[9],
+                                                      uint32_t (&uhi)[9])
 {
     const Faces f = faces_of(d, t.y, t.z, cy, cz);
     const float rcm2 = d.rc2 * 1.00002f;
@@ -1259,8 +1261,6 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
         const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
         const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
         const float tw = rcm2 - fmaf(ey, ey, ez * ez);
-        j[rr] = 0u;
-        je[rr] = 0u;
         if (by < 0 || by >= ny || bz < 0 || bz >= nz || !(tw > 0.f)) continue;
         const float tt = fmaxf(tw, 1e-30f);
         const float w = tt * rsqrtf(tt) + slack;
@@ -1268,8 +1268,12 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
         const uint32_t rb = d.cell_base + (uint32_t)nx * row, pad = ROW_PADS * (d.row_base + row);
         const int b0 = sub_bin(t.x - w, xlo, invs, 0, lo, hi);
         const int b1 = sub_bin(t.x + w, xlo, invs, 0, lo, hi) + 1;
-        j[rr] = sub_bin_start(a, rb, b0, false) + pad;
-        je[rr] = sub_bin_start(a, rb, b1, true) + pad;
+        const uint32_t j = sub_bin_start(a, rb, b0, false) + pad;
+        const uint32_t je = sub_bin_start(a, rb, b1, true) + pad;
+        if (je > j) {
+            ulo[rr] = min(ulo[rr], j);
+            uhi[rr] = max(uhi[rr], je);
+        }
     }
 }
 
@@ -1299,16 +1303,7 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
             uhi[rr] = 0u;
         }
 #pragma unroll
-        for (int k = 0; k < G; ++k) {
-            uint32_t j[9], je[9];
-            target_windows_direct(a, d, t[k], cx[k], cy, cz, j, je);
-#pragma unroll
-            for (int rr = 0; rr < 9; ++rr)
-                if (je[rr] > j[rr]) {
-                    ulo[rr] = min(ulo[rr], j[rr]);
-                    uhi[rr] = max(uhi[rr], je[rr]);
-                }
-        }
+        for (int k = 0; k < G; ++k) target_windows_direct(a, d, t[k], cx[k], cy, cz, ulo, uhi);
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr)
             if (uhi[rr] > ulo[rr]) {
