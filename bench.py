@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
+    p.add_argument("--max-slots", type=int, default=8, help="serving study: slots per capacity bucket")
     return p.parse_args()
 
 
@@ -637,7 +638,7 @@ def study_serving(args):
         # results of every 500th job are kept; the others land in slot buffers
         jobs.append(make_job(k, x, y, z, sp.lo, sp.hi, sp.rc, sp.h, outputs=k % 500 == 0))
     t_gen = time.perf_counter() - t0
-    srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=8)
+    srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=args.max_slots)
     res = {"study": "serving", "jobs": len(jobs), "particles": sum(j.n for j in jobs),
            "generation_s": t_gen}
     try:

@@ -193,6 +193,23 @@ pi_status pi_submit_host(pi_ctx* ctx, const pi_box* box, float r_c, const float*
                          const float* hz, int64_t n, float h, float* hS, float* hVx, float* hVy,
                          float* hVz, uint32_t* hnbr, int out_order, pi_stream stream);
 
+/* pi_submit_host with host arrays that may lie in blocks, so that the step
+ * makes as few as one host-to-device and one device-to-host copy instead of
+ * up to eight.  in_stride = 0: x, y, z are separate arrays (three copies);
+ * in_stride > 0: they lie in one block, hy = hx + in_stride and hz = hx +
+ * 2*in_stride (checked), and travel as one copy of 2*in_stride + n entries,
+ * the gaps included.  out_stride likewise for S, Vx, Vy, Vz and, unless
+ * NULL, the counts: hVx = hS + out_stride, ..., hnbr = (uint32_t*)(hS +
+ * 4*out_stride).  A block must be one host allocation covering the copied
+ * range.  A non-zero stride is a multiple of 4 with n <= stride <= n_max +
+ * 4 rounded up to a multiple of 4.  Otherwise as pi_submit_host.
+ * Errors: PI_ERR_INVALID_ARG (a stride outside these limits or arrays not at
+ * their stride) and those of pi_submit_host. */
+pi_status pi_submit_host_strided(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
+                                 const float* hz, int64_t in_stride, int64_t n, float h, float* hS, float* hVx,
+                                 float* hVy, float* hVz, uint32_t* hnbr, int64_t out_stride, int out_order,
+                                 pi_stream stream);
+
 /* ---- Batches: many independent systems per context --------------------
  *
  * A batch context holds num_systems independent systems, each with its own
@@ -319,6 +336,82 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
  * Errors: PI_ERR_INVALID_ARG, PI_ERR_CAPACITY, PI_ERR_CUDA. */
 pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, uint32_t* offsets,
                                  uint32_t* result, pi_stream stream);
+
+/* ---- Serving: a request loop over device-resident slots ---------------
+ *
+ * Continuous batching on one GPU, as a native host loop.  A server owns
+ * "slots": single-system contexts, each with its own stream, completion
+ * event and pinned scratch block.  A job runs on one slot as one
+ * pi_submit_host_strided call (re-target to the job's box and cutoff, copy
+ * in, bin, interact, copy out) -- the kernels a lone pi_bin + pi_interact
+ * would run, so a job's results do not depend on the jobs beside it.  Slots
+ * come in capacity buckets; a job waits in the queue of the smallest bucket
+ * whose capacity holds both its particles and its grid's cells, and may also
+ * take a free slot of a larger bucket.  When every slot that fits a job is
+ * busy, the server makes a new one while the bucket's slot limit, the HBM
+ * budget and the device's free memory allow (memory-based admission);
+ * otherwise the job waits.  Completion is polled with cudaEventQuery.
+ */
+typedef struct pi_server pi_server;
+
+enum { PI_SERVER_MAX_BUCKETS = 16 };
+
+/* One request (host memory; pinned memory makes the copies asynchronous). */
+typedef struct {
+    const float* x;      /* positions: n entries each; with in_stride > 0,   */
+    const float* y;      /* y and z are x + in_stride and x + 2*in_stride    */
+    const float* z;      /* (one block, one copy) and these two are ignored  */
+    int64_t in_stride;   /* 0 or a stride as in pi_submit_host_strided       */
+    int64_t n;           /* particles, >= 0                                  */
+    pi_box box;          /* the job's box and cutoff (any grid that fits a   */
+    float r_c;           /* bucket)                                          */
+    float h;             /* kernel length, > 0                               */
+    float* S;            /* outputs, n entries each, in input order; all    */
+    float* Vx;           /* four NULL: the results go to the slot's scratch  */
+    float* Vy;           /* block, which the slot's next job overwrites      */
+    float* Vz;
+    uint32_t* nbr;       /* neighbour counts, or NULL                        */
+    int64_t out_stride;  /* 0 or a stride as in pi_submit_host_strided       */
+    double arrival;      /* seconds after the start of pi_server_run         */
+    double t_start;      /* written: when the job was enqueued on a slot     */
+    double t_done;       /* written: when its completion was seen            */
+    int64_t slot_capacity; /* written: capacity of the slot that ran it      */
+} pi_job;
+
+/* Device memory one slot of the given particle capacity is charged against
+ * the HBM budget: capacity * 144 bytes + 1 MiB (the context, up to one cell
+ * per particle, and its staging buffers). */
+int64_t pi_server_slot_bytes(int64_t capacity);
+
+/* Creates a server on the current device.  capacity: num_buckets (1 ..
+ * PI_SERVER_MAX_BUCKETS) distinct particle capacities (each also the cell
+ * capacity of its slots), 1 .. 2^30; initial_slots: slots made at once per
+ * bucket (NULL: none; fewer if the budget runs out); max_slots_per_bucket
+ * >= 1; hbm_budget: bytes the slots may be charged (<= 0: half of the
+ * device's free memory).  Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM,
+ * PI_ERR_CUDA. */
+pi_status pi_server_create(int32_t num_buckets, const int64_t* capacity, const int32_t* initial_slots,
+                           int32_t max_slots_per_bucket, int64_t hbm_budget, pi_server** out);
+
+/* Serves num_jobs jobs, blocking until all are complete: a job is admitted
+ * once `arrival` seconds have passed since the call started and a slot that
+ * fits it is free (oldest arrival first).  Writes each job's t_start,
+ * t_done and slot_capacity, and the time from the start to the last
+ * completion into *makespan_s (may be NULL).  Every job is checked first:
+ * PI_ERR_INVALID_ARG for a bad job, PI_ERR_CAPACITY for one that fits no
+ * bucket (nothing runs then).  Afterwards the device status of every slot
+ * is collected as in pi_sync_status.  The host arrays of a job must stay
+ * valid until the call returns. */
+pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* makespan_s);
+
+/* Buckets (num_buckets; capacity and slots as arrays of that length, any
+ * pointer may be NULL) and the bytes charged to the HBM budget. */
+pi_status pi_server_info(const pi_server* srv, int32_t* num_buckets, int64_t* capacity, int32_t* slots,
+                         int64_t* hbm_used);
+
+/* Destroys the server and its slots (waits for their streams).  NULL is
+ * accepted. */
+pi_status pi_server_destroy(pi_server* srv);
 
 /* Number of kernels this context has launched since pi_create (host counter). */
 pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count);

@@ -48,6 +48,20 @@ class PiBox(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
 
 
+class PiJob(ctypes.Structure):
+    """``pi_job`` of include/pi.h: one serving request."""
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("in_stride", ctypes.c_int64), ("n", ctypes.c_int64), ("box", PiBox),
+                ("r_c", ctypes.c_float), ("h", ctypes.c_float),
+                ("S", ctypes.c_void_p), ("Vx", ctypes.c_void_p), ("Vy", ctypes.c_void_p),
+                ("Vz", ctypes.c_void_p), ("nbr", ctypes.c_void_p), ("out_stride", ctypes.c_int64),
+                ("arrival", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("slot_capacity", ctypes.c_int64)]
+
+
+PI_SERVER_MAX_BUCKETS = 16
+
+
 class PiError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -85,6 +99,13 @@ def load():
         "pi_interact": ([P, f32, P, P, P, P, P, i32, P], i32),
         "pi_run_host": ([P, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
         "pi_submit_host": ([P, ctypes.POINTER(PiBox), f32, P, P, P, i64, f32, P, P, P, P, P, i32, P], i32),
+        "pi_submit_host_strided": ([P, ctypes.POINTER(PiBox), f32, P, P, P, i64, i64, f32, P, P, P, P, P, i64,
+                                    i32, P], i32),
+        "pi_server_slot_bytes": ([i64], i64),
+        "pi_server_create": ([i32, P, P, i32, i64, ctypes.POINTER(P)], i32),
+        "pi_server_run": ([P, ctypes.POINTER(PiJob), i64, ctypes.POINTER(ctypes.c_double)], i32),
+        "pi_server_info": ([P, P, P, P, P], i32),
+        "pi_server_destroy": ([P], i32),
         "pi_grid": ([P, P], i32),
         "pi_binned": ([P] + [ctypes.POINTER(P)] * 6, i32),
         "pi_copy_binned": ([P, P, P, P, P, P, P, P], i32),
@@ -224,6 +245,52 @@ def pi_submit_host(ctx, lo, hi, r_c: float, x, y, z, n: int, h: float, S, Vx, Vy
     _check(load().pi_submit_host(ctx, ctypes.byref(box), float(r_c), _ptr(x), _ptr(y), _ptr(z), int(n),
                                  float(h), _ptr(S), _ptr(Vx), _ptr(Vy), _ptr(Vz), _ptr(nbr),
                                  int(out_order), _stream(stream)), "pi_submit_host")
+
+
+def pi_submit_host_strided(ctx, lo, hi, r_c: float, x, y, z, in_stride: int, n: int, h: float, S, Vx, Vy, Vz,
+                           nbr=None, out_stride: int = 0, out_order: int = PI_ORDER_ORIGINAL, stream=None) -> None:
+    """pi_submit_host with host arrays that may lie in blocks (one copy per
+    block); see include/pi.h."""
+    box = PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi))
+    _check(load().pi_submit_host_strided(ctx, ctypes.byref(box), float(r_c), _ptr(x), _ptr(y), _ptr(z),
+                                         int(in_stride), int(n), float(h), _ptr(S), _ptr(Vx), _ptr(Vy),
+                                         _ptr(Vz), _ptr(nbr), int(out_stride), int(out_order), _stream(stream)),
+           "pi_submit_host_strided")
+
+
+def pi_server_slot_bytes(capacity: int) -> int:
+    return int(load().pi_server_slot_bytes(int(capacity)))
+
+
+def pi_server_create(capacities, initial_slots=None, max_slots_per_bucket: int = 8, hbm_budget: int = 0):
+    k = len(capacities)
+    caps = (ctypes.c_int64 * k)(*[int(c) for c in capacities])
+    init = (ctypes.c_int32 * k)(*[int(c) for c in initial_slots]) if initial_slots is not None else None
+    out = ctypes.c_void_p()
+    _check(load().pi_server_create(int(k), caps, init, int(max_slots_per_bucket), int(hbm_budget),
+                                   ctypes.byref(out)), "pi_server_create")
+    return out
+
+
+def pi_server_run(srv, jobs) -> float:
+    """Serves a ctypes array of PiJob; returns the makespan in seconds."""
+    mk = ctypes.c_double()
+    _check(load().pi_server_run(srv, jobs, len(jobs), ctypes.byref(mk)), "pi_server_run")
+    return mk.value
+
+
+def pi_server_info(srv):
+    """(capacities, slots per bucket, bytes charged to the HBM budget)."""
+    nb = ctypes.c_int32()
+    caps = (ctypes.c_int64 * PI_SERVER_MAX_BUCKETS)()
+    slots = (ctypes.c_int32 * PI_SERVER_MAX_BUCKETS)()
+    used = ctypes.c_int64()
+    _check(load().pi_server_info(srv, ctypes.byref(nb), caps, slots, ctypes.byref(used)), "pi_server_info")
+    return list(caps[: nb.value]), list(slots[: nb.value]), used.value
+
+
+def pi_server_destroy(srv) -> None:
+    _check(load().pi_server_destroy(srv), "pi_server_destroy")
 
 
 def pi_grid(ctx):

@@ -63,15 +63,8 @@ struct pi_ctx {
     float4* P;
 
     // host-buffer path (allocated on first use)
-    void* io;
-    float* io_x;
-    float* io_y;
-    float* io_z;
-    float* io_S;
-    float* io_Vx;
-    float* io_Vy;
-    float* io_Vz;
-    uint32_t* io_nbr;
+    float* io;    // host-transfer staging: 3 input and 5 output arrays of io_n entries
+    size_t io_n;
 
     int64_t n;                      // particles of the last pi_bin (all systems)
     std::vector<uint32_t> pbase_h;  // [S+1] particle bases of the last pi_bin
@@ -729,50 +722,75 @@ pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)
     return PI_OK;
 }
 
+// Entries per staging array of a context (its particle capacity, rounded).
+static size_t io_entries(const pi_ctx* ctx)
+{
+    return ((size_t)ctx->n_max_total + 4 + 3) & ~(size_t)3;
+}
+
 // Device staging buffers of the host-memory entry points (allocated on the
-// first call: n_max entries for x, y, z, S, Vx, Vy, Vz, nbr).
+// first call: io_entries entries for each of x, y, z, S, Vx, Vy, Vz, nbr).
 static pi_status ensure_io(pi_ctx* ctx)
 {
     if (ctx->io) return PI_OK;
-    const size_t nm = (size_t)ctx->n_max_total + 4;
+    const size_t nm = io_entries(ctx);
     PI_TRY(cudaMalloc(&ctx->io, nm * 8 * sizeof(float)));
-    float* f = (float*)ctx->io;
-    ctx->io_x = f;
-    ctx->io_y = f + nm;
-    ctx->io_z = f + 2 * nm;
-    ctx->io_S = f + 3 * nm;
-    ctx->io_Vx = f + 4 * nm;
-    ctx->io_Vy = f + 5 * nm;
-    ctx->io_Vz = f + 6 * nm;
-    ctx->io_nbr = (uint32_t*)(f + 7 * nm);
+    ctx->io_n = nm;
     return PI_OK;
 }
 
-// The asynchronous body of pi_run_host / pi_submit_host.
-static pi_status host_step(pi_ctx* ctx, const float* hx, const float* hy, const float* hz, int64_t n,
-                           float h, float* hS, float* hVx, float* hVy, float* hVz, uint32_t* hnbr,
-                           int out_order, pi_stream stream)
+// The asynchronous body of pi_run_host / pi_submit_host /
+// pi_submit_host_strided.  in_stride / out_stride: 0 for separate host
+// arrays (one copy each), else the stride (elements) of host arrays that
+// lie in one block (one copy per block, the gaps included); the device
+// staging arrays take the same stride.
+static pi_status host_step(pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
+                           size_t in_stride, int64_t n, float h, float* hS, float* hVx, float* hVy,
+                           float* hVz, uint32_t* hnbr, size_t out_stride, int out_order, pi_stream stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)n * sizeof(float);
+    const size_t bytes = (size_t)n * sizeof(float), nm = ctx->io_n;
+    float* dx = ctx->io;
+    const size_t si = in_stride ? in_stride : nm;
     if (n > 0) {
-        PI_TRY(cudaMemcpyAsync(ctx->io_x, hx, bytes, cudaMemcpyHostToDevice, s));
-        PI_TRY(cudaMemcpyAsync(ctx->io_y, hy, bytes, cudaMemcpyHostToDevice, s));
-        PI_TRY(cudaMemcpyAsync(ctx->io_z, hz, bytes, cudaMemcpyHostToDevice, s));
+        if (in_stride) {
+            PI_TRY(cudaMemcpyAsync(dx, hx, (2 * si + (size_t)n) * sizeof(float), cudaMemcpyHostToDevice, s));
+        } else {
+            PI_TRY(cudaMemcpyAsync(dx, hx, bytes, cudaMemcpyHostToDevice, s));
+            PI_TRY(cudaMemcpyAsync(dx + nm, hy, bytes, cudaMemcpyHostToDevice, s));
+            PI_TRY(cudaMemcpyAsync(dx + 2 * nm, hz, bytes, cudaMemcpyHostToDevice, s));
+        }
     }
-    pi_status st = pi_bin(ctx, ctx->io_x, ctx->io_y, ctx->io_z, n, stream);
+    pi_status st = pi_bin(ctx, dx, dx + si, dx + 2 * si, n, stream);
     if (st != PI_OK) return st;
-    st = pi_interact(ctx, h, ctx->io_S, ctx->io_Vx, ctx->io_Vy, ctx->io_Vz,
-                     hnbr ? ctx->io_nbr : nullptr, out_order, stream);
+    float* d0 = ctx->io + 3 * nm;
+    const size_t so = out_stride ? out_stride : nm;
+    st = pi_interact(ctx, h, d0, d0 + so, d0 + 2 * so, d0 + 3 * so, hnbr ? (uint32_t*)(d0 + 4 * so) : nullptr,
+                     out_order, stream);
     if (st != PI_OK) return st;
     if (n > 0) {
-        PI_TRY(cudaMemcpyAsync(hS, ctx->io_S, bytes, cudaMemcpyDeviceToHost, s));
-        PI_TRY(cudaMemcpyAsync(hVx, ctx->io_Vx, bytes, cudaMemcpyDeviceToHost, s));
-        PI_TRY(cudaMemcpyAsync(hVy, ctx->io_Vy, bytes, cudaMemcpyDeviceToHost, s));
-        PI_TRY(cudaMemcpyAsync(hVz, ctx->io_Vz, bytes, cudaMemcpyDeviceToHost, s));
-        if (hnbr) PI_TRY(cudaMemcpyAsync(hnbr, ctx->io_nbr, bytes, cudaMemcpyDeviceToHost, s));
+        if (out_stride) {
+            const size_t k = hnbr ? 5 : 4;
+            PI_TRY(cudaMemcpyAsync(hS, d0, ((k - 1) * so + (size_t)n) * sizeof(float), cudaMemcpyDeviceToHost, s));
+        } else {
+            PI_TRY(cudaMemcpyAsync(hS, d0, bytes, cudaMemcpyDeviceToHost, s));
+            PI_TRY(cudaMemcpyAsync(hVx, d0 + nm, bytes, cudaMemcpyDeviceToHost, s));
+            PI_TRY(cudaMemcpyAsync(hVy, d0 + 2 * nm, bytes, cudaMemcpyDeviceToHost, s));
+            PI_TRY(cudaMemcpyAsync(hVz, d0 + 3 * nm, bytes, cudaMemcpyDeviceToHost, s));
+            if (hnbr) PI_TRY(cudaMemcpyAsync(hnbr, d0 + 4 * nm, bytes, cudaMemcpyDeviceToHost, s));
+        }
     }
     return PI_OK;
+}
+
+// Re-targets a single-system context to another box and cutoff unless it
+// already has them.
+static pi_status retarget(pi_ctx* ctx, const pi_box* box, float r_c, pi_stream stream)
+{
+    const pi_box& cur = ctx->boxes[0];
+    bool same = r_c == ctx->rc[0];
+    for (int d = 0; d < 3; ++d) same = same && box->lo[d] == cur.lo[d] && box->hi[d] == cur.hi[d];
+    return same ? PI_OK : pi_reconfigure(ctx, box, r_c, stream);
 }
 
 static pi_status host_args_ok(const pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
@@ -796,7 +814,7 @@ pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_run_host: set device");
     if ((st = ensure_io(ctx)) != PI_OK) return st;
-    st = host_step(ctx, hx, hy, hz, n, h, hS, hVx, hVy, hVz, hnbr, out_order, stream);
+    st = host_step(ctx, hx, hy, hz, 0, n, h, hS, hVx, hVy, hVz, hnbr, 0, out_order, stream);
     if (st != PI_OK) return st;
     return pi_sync_status(ctx, stream, nullptr);
 }
@@ -811,11 +829,32 @@ pi_status pi_submit_host(pi_ctx* ctx, const pi_box* box, float r_c, const float*
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_submit_host: set device");
     if ((st = ensure_io(ctx)) != PI_OK) return st;
-    const pi_box& cur = ctx->boxes[0];
-    bool same = r_c == ctx->rc[0];
-    for (int d = 0; d < 3; ++d) same = same && box->lo[d] == cur.lo[d] && box->hi[d] == cur.hi[d];
-    if (!same && (st = pi_reconfigure(ctx, box, r_c, stream)) != PI_OK) return st;
-    return host_step(ctx, hx, hy, hz, n, h, hS, hVx, hVy, hVz, hnbr, out_order, stream);
+    if ((st = retarget(ctx, box, r_c, stream)) != PI_OK) return st;
+    return host_step(ctx, hx, hy, hz, 0, n, h, hS, hVx, hVy, hVz, hnbr, 0, out_order, stream);
+}
+
+pi_status pi_submit_host_strided(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
+                                 const float* hz, int64_t in_stride, int64_t n, float h, float* hS, float* hVx,
+                                 float* hVy, float* hVz, uint32_t* hnbr, int64_t out_stride, int out_order,
+                                 pi_stream stream)
+{
+    if (!ctx || !box) return PI_ERR_INVALID_ARG;
+    const uint64_t cap = io_entries(ctx);
+    auto stride_ok = [&](int64_t d) { return d == 0 || (d >= n && d % 4 == 0 && (uint64_t)d <= cap); };
+    if (n < 0 || !stride_ok(in_stride) || !stride_ok(out_stride)) return PI_ERR_INVALID_ARG;
+    // arrays of a block must sit at the stride they claim
+    if (in_stride && (hy != hx + in_stride || hz != hx + 2 * in_stride)) return PI_ERR_INVALID_ARG;
+    if (out_stride && (hVx != hS + out_stride || hVy != hS + 2 * out_stride || hVz != hS + 3 * out_stride ||
+                       (hnbr && (const void*)hnbr != (const void*)(hS + 4 * out_stride))))
+        return PI_ERR_INVALID_ARG;
+    pi_status st = host_args_ok(ctx, hx, hy, hz, n, hS, hVx, hVy, hVz);
+    if (st != PI_OK) return st;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_submit_host_strided: set device");
+    if ((st = ensure_io(ctx)) != PI_OK) return st;
+    if ((st = retarget(ctx, box, r_c, stream)) != PI_OK) return st;
+    return host_step(ctx, hx, hy, hz, (size_t)in_stride, n, h, hS, hVx, hVy, hVz, hnbr, (size_t)out_stride,
+                     out_order, stream);
 }
 
 }  // extern "C"

@@ -1,12 +1,13 @@
 """Continuous-batching server for cutoff-interaction jobs on one GPU.
 
 Jobs (host positions, box, cutoff, kernel width) arrive over time.  The
-server keeps device-resident contexts ("slots"), each with its own CUDA
-stream and device staging buffers; a job is enqueued on a free slot with one
-call, ``pi_submit_host``, which re-targets the slot's grid to the job's box
-and cutoff (no allocation), copies the positions in, bins, interacts and
-copies the results out.  A job's grid thus lives on the device only while it
-runs, and the next job reuses it.
+request loop itself is native (``pi_server_run`` in the C library): it
+keeps device-resident contexts ("slots"), each with its own CUDA stream,
+completion event and pinned scratch block, and enqueues a job on a free slot
+with one ``pi_submit_host_strided`` call, which re-targets the slot's grid
+to the job's box and cutoff (no allocation), copies the positions in, bins,
+interacts and copies the results out.  A job's grid thus lives on the
+device only while it runs, and the next job reuses it.
 
 Admission is continuous: whenever a slot is free, the oldest waiting job
 that fits it is started at once, so the work of several jobs overlaps on the
@@ -18,27 +19,29 @@ a new slot is created (memory-based admission); otherwise the job waits.
 Completion is polled through CUDA events.
 
 Every job runs exactly the kernels a lone ``pi_bin`` + ``pi_interact``
-would run, on its own slot, so its results do not depend on the mix.
+would run, on its own slot, so its results do not depend on the mix.  This
+module builds the job records and reports the statistics.
 """
 from __future__ import annotations
 
+import ctypes
 import time
-from collections import deque
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 
 import numpy as np
 
 from . import binding as B
-from .workloads import rc_for_cells
 
 
 @dataclass
 class Job:
-    """One request.  Inputs are pinned host tensors (x, y, z); the outputs
-    (S, Vx, Vy, Vz, nbr) are pinned host tensors filled by the server, or
-    None: the results then land in the slot's own host buffers, which the
-    next job on that slot overwrites (for callers that consume a result as
-    soon as the job completes)."""
+    """One request.  Inputs are pinned host tensors (x, y, z; with
+    in_stride > 0 they are views of one block, y = x + in_stride and z = x +
+    2 in_stride); the outputs (S, Vx, Vy, Vz, nbr) are pinned host tensors
+    filled by the server (views of one block when out_stride > 0), or None:
+    the results then land in the slot's scratch block, which the slot's next
+    job overwrites (for callers that consume a result as soon as the job
+    completes)."""
     jid: int
     n: int
     lo: tuple
@@ -57,6 +60,9 @@ class Job:
     t_start: float = 0.0
     t_done: float = 0.0
     cells: int = 0
+    in_stride: int = 0
+    out_stride: int = 0
+    blocks: list = field(default_factory=list)  # keeps the pinned blocks alive
 
 
 def job_cells(lo, hi, rc) -> int:
@@ -67,108 +73,61 @@ def job_cells(lo, hi, rc) -> int:
     return c
 
 
+def _stride(n: int) -> int:
+    return max(4, (int(n) + 3) // 4 * 4)
+
+
 def make_job(jid, x, y, z, lo, hi, rc, h, arrival=0.0, outputs=True):
-    """A job from host positions (numpy arrays, copied to pinned memory, or
-    pinned torch tensors, used as they are); ``outputs``: allocate the job's
-    own pinned result buffers."""
+    """A job from host positions: numpy arrays are copied into one pinned
+    block (one host-to-device copy per job); pinned torch tensors are used
+    as they are.  ``outputs``: allocate the job's own pinned result block."""
     import torch
 
     n = len(x)
-
-    def pin(a):
-        if isinstance(a, torch.Tensor):
-            return a
-        return torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
-
-    job = Job(jid=jid, n=n, lo=tuple(lo), hi=tuple(hi), rc=float(rc), h=float(h), x=pin(x),
-              y=pin(y), z=pin(z), arrival=float(arrival), cells=job_cells(lo, hi, rc))
+    d = _stride(n)
+    job = Job(jid=jid, n=n, lo=tuple(lo), hi=tuple(hi), rc=float(rc), h=float(h), x=None, y=None, z=None,
+              arrival=float(arrival), cells=job_cells(lo, hi, rc))
+    if isinstance(x, torch.Tensor):
+        job.x, job.y, job.z = x, y, z
+    else:
+        blk = torch.empty(3 * d).pin_memory()
+        for k, a in enumerate((x, y, z)):
+            blk[k * d: k * d + n] = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+        job.x, job.y, job.z = blk[0:n], blk[d:d + n], blk[2 * d:2 * d + n]
+        job.in_stride = d
+        job.blocks.append(blk)
     if outputs:
-        out = [torch.empty(max(n, 1)).pin_memory() for _ in range(4)]
-        job.S, job.Vx, job.Vy, job.Vz = out
-        job.nbr = torch.empty(max(n, 1), dtype=torch.int32).pin_memory()
+        out = torch.empty(5 * d).pin_memory()
+        job.S, job.Vx, job.Vy, job.Vz = (out[k * d: k * d + n] for k in range(4))
+        job.nbr = out[4 * d: 4 * d + n].view(torch.int32)
+        job.out_stride = d
+        job.blocks.append(out)
     return job
 
 
-def slot_bytes(n_cap: int, c_cap: int) -> int:
-    """Device memory of one slot: the context arena (72 bytes per particle,
-    about 28 per cell) plus its host-transfer staging buffers (32 bytes per
-    particle); an upper estimate."""
-    return int(n_cap) * (80 + 32) + int(c_cap) * 32 + (1 << 20)
-
-
-class Slot:
-    def __init__(self, n_cap: int, c_cap: int, device, bucket: int):
-        import torch
-
-        self.n_cap, self.c_cap, self.bucket = int(n_cap), int(c_cap), int(bucket)
-        # a unit box with k^3 >= c_cap cells sizes the grid capacity
-        k = int(np.ceil(c_cap ** (1.0 / 3.0) - 1e-9))
-        self.ctx = B.pi_create((0, 0, 0), (1, 1, 1), rc_for_cells(k), self.n_cap)
-        self.stream = torch.cuda.Stream(device=device)
-        # host results of jobs without their own buffers
-        self.hout = [torch.empty(self.n_cap).pin_memory() for _ in range(4)]
-        self.hnb = torch.empty(self.n_cap, dtype=torch.int32).pin_memory()
-        self.event = torch.cuda.Event()
-        self.job: Job | None = None
-        # allocate the staging buffers now, outside the request loop
-        z = torch.zeros(1).pin_memory()
-        B.pi_submit_host(self.ctx, (0, 0, 0), (1, 1, 1), rc_for_cells(k), z, z, z, 0, 0.5,
-                         *self.hout, self.hnb, B.PI_ORDER_ORIGINAL, self.stream)
-        self.stream.synchronize()
-
-    def start(self, job: Job, now: float):
-        job.t_start = now
-        own = job.S is not None
-        outs = (job.S, job.Vx, job.Vy, job.Vz) if own else self.hout
-        B.pi_submit_host(self.ctx, job.lo, job.hi, job.rc, job.x, job.y, job.z, job.n, job.h, *outs,
-                         job.nbr if own else self.hnb, B.PI_ORDER_ORIGINAL, self.stream)
-        self.event.record(self.stream)
-        self.job = job
-
-    def destroy(self):
-        B.pi_destroy(self.ctx)
+def slot_bytes(n_cap: int, c_cap: int | None = None) -> int:
+    """Device memory one slot of particle capacity n_cap is charged against
+    the server's HBM budget (cell capacity = particle capacity)."""
+    return B.pi_server_slot_bytes(n_cap)
 
 
 class Server:
-    """Continuous-batching server.  ``buckets``: (particle capacity, initial
-    slots) per bucket, cell capacity = particle capacity; ``hbm_budget``:
-    bytes the slots may occupy (default: half of the free device memory)."""
+    """Continuous-batching server over the native request loop.
+    ``buckets``: (particle capacity, initial slots) per bucket, cell capacity
+    = particle capacity; ``hbm_budget``: bytes the slots may occupy (default:
+    half of the free device memory)."""
 
     def __init__(self, buckets=((65536, 2), (262144, 2), (1048576, 1)), hbm_budget=None,
                  max_slots_per_bucket=8, device=0):
         import torch
 
         self.device = torch.device("cuda", device)
-        free, _ = torch.cuda.mem_get_info(self.device)
-        self.budget = int(hbm_budget if hbm_budget is not None else free // 2)
-        self.used = 0
-        self.caps = sorted(int(b[0]) for b in buckets)
-        self.max_per_bucket = int(max_slots_per_bucket)
-        self.slots = {c: [] for c in self.caps}
-        self.free = {c: [] for c in self.caps}
-        for cap, k in buckets:
-            for _ in range(k):
-                s = self._grow(int(cap))
-                if s is not None:
-                    self.free[s.bucket].append(s)
-
-    def _grow(self, cap: int) -> Slot | None:
-        """New slot of a bucket if it fits the bucket's limit, the HBM budget
-        and the device's free memory (checked in that order)."""
-        import torch
-
-        if len(self.slots[cap]) >= self.max_per_bucket:
-            return None
-        need = slot_bytes(cap, cap)
-        if self.used + need > self.budget:
-            return None
-        free, _ = torch.cuda.mem_get_info(self.device)
-        if need > free:
-            return None
-        s = Slot(cap, cap, self.device, cap)
-        self.slots[cap].append(s)
-        self.used += need
-        return s
+        caps = [int(b[0]) for b in buckets]
+        init = [int(b[1]) for b in buckets]
+        with torch.cuda.device(self.device):
+            self.srv = B.pi_server_create(caps, init, max_slots_per_bucket,
+                                          0 if hbm_budget is None else int(hbm_budget))
+        self.caps = sorted(caps)
 
     def bucket_of(self, job: Job) -> int | None:
         """Smallest bucket whose slots fit the job, None if none does."""
@@ -180,86 +139,41 @@ class Server:
     def fits(self, job: Job) -> bool:
         return self.bucket_of(job) is not None
 
-    def _admit(self, queues, busy, now):
-        """Starts waiting jobs while slots are free or can be created: for
-        each bucket from the largest down, its free slots take the oldest
-        job among the queues of that bucket and the smaller ones."""
-        for bi in range(len(self.caps) - 1, -1, -1):
-            cap = self.caps[bi]
-            while True:
-                # oldest head among the queues this bucket can serve
-                best = None
-                for bj in range(bi + 1):
-                    q = queues[self.caps[bj]]
-                    if q and (best is None or q[0].arrival < queues[best][0].arrival):
-                        best = self.caps[bj]
-                if best is None:
-                    break
-                if not self.free[cap]:
-                    s = self._grow(cap)
-                    if s is None:
-                        break
-                    self.free[cap].append(s)
-                slot = self.free[cap].pop()
-                slot.start(queues[best].popleft(), now)
-                busy.append(slot)
-
-    def run(self, jobs, clock=time.perf_counter):
+    def run(self, jobs):
         """Serves ``jobs`` (each with an ``arrival`` offset in seconds from
         the start).  Returns statistics; every job gets its outputs, start
         and completion times (seconds from the start)."""
+        import torch
+
         for j in jobs:
             if self.bucket_of(j) is None:
                 raise ValueError(f"job {j.jid} fits no slot bucket")
-        pending = deque(sorted(jobs, key=lambda j: j.arrival))
-        queues = {c: deque() for c in self.caps}
-        busy: list[Slot] = []
-        done = 0
-        total = len(pending)
-        t0 = clock()
-        while done < total:
-            now = clock() - t0
-            arrived = False
-            while pending and pending[0].arrival <= now:
-                j = pending.popleft()
-                queues[self.bucket_of(j)].append(j)
-                arrived = True
-            # completions
-            freed = False
-            still = []
-            for s in busy:
-                if s.event.query():
-                    s.job.t_done = clock() - t0
-                    s.job = None
-                    self.free[s.bucket].append(s)
-                    done += 1
-                    freed = True
-                else:
-                    still.append(s)
-            busy = still
-            if arrived or freed:
-                self._admit(queues, busy, clock() - t0)
-            if not busy and pending and not any(queues.values()):
-                wait = pending[0].arrival - (clock() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.001))
-        makespan = clock() - t0
-        for s in (s for lst in self.slots.values() for s in lst):
-            st, _ = B.pi_sync_status(s.ctx, s.stream, raise_on_error=False)
-            if st != B.PI_OK:
-                raise B.PiError(st, "serving")
+        arr = (B.PiJob * len(jobs))()
+        for r, j in zip(arr, jobs):
+            r.x, r.y, r.z = B._ptr(j.x), B._ptr(j.y), B._ptr(j.z)
+            r.in_stride, r.n = int(j.in_stride), int(j.n)
+            r.box = B.PiBox((ctypes.c_float * 3)(*j.lo), (ctypes.c_float * 3)(*j.hi))
+            r.r_c, r.h = float(j.rc), float(j.h)
+            if j.S is not None:
+                r.S, r.Vx, r.Vy, r.Vz = B._ptr(j.S), B._ptr(j.Vx), B._ptr(j.Vy), B._ptr(j.Vz)
+                r.nbr = B._ptr(j.nbr)
+                r.out_stride = int(j.out_stride)
+            r.arrival = float(j.arrival)
+        with torch.cuda.device(self.device):
+            makespan = B.pi_server_run(self.srv, arr)
+        for r, j in zip(arr, jobs):
+            j.t_start, j.t_done = r.t_start, r.t_done
+        caps, slots, used = B.pi_server_info(self.srv)
         lat = np.array([j.t_done - j.arrival for j in jobs])
-        return {"jobs": total, "makespan_s": makespan, "jobs_per_s": total / makespan,
+        return {"jobs": len(jobs), "makespan_s": makespan, "jobs_per_s": len(jobs) / makespan,
                 "particles_per_s": sum(j.n for j in jobs) / makespan,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "mean_ms": 1e3 * float(lat.mean()),
-                "slots": {c: len(v) for c, v in self.slots.items()},
-                "hbm_used_bytes": self.used}
+                "slots": dict(zip(caps, slots)),
+                "hbm_used_bytes": used}
 
     def close(self):
-        for lst in self.slots.values():
-            for s in lst:
-                s.destroy()
-        self.slots = {c: [] for c in self.caps}
-        self.free = {c: [] for c in self.caps}
+        if self.srv is not None:
+            B.pi_server_destroy(self.srv)
+            self.srv = None
