@@ -150,11 +150,13 @@ class Server:
                 raise ValueError(f"job {j.jid} fits no slot bucket")
         arr = (B.PiJob * len(jobs))()
         for r, j in zip(arr, jobs):
-            r.x, r.y, r.z = B._ptr(j.x), B._ptr(j.y), B._ptr(j.z)
-            r.in_stride, r.n = int(j.in_stride), int(j.n)
+            r.n = int(j.n)
+            if j.n > 0:  # (an empty job copies nothing: no addresses)
+                r.x, r.y, r.z = B._ptr(j.x), B._ptr(j.y), B._ptr(j.z)
+                r.in_stride = int(j.in_stride)
             r.box = B.PiBox((ctypes.c_float * 3)(*j.lo), (ctypes.c_float * 3)(*j.hi))
             r.r_c, r.h = float(j.rc), float(j.h)
-            if j.S is not None:
+            if j.S is not None and j.n > 0:
                 r.S, r.Vx, r.Vy, r.Vz = B._ptr(j.S), B._ptr(j.Vx), B._ptr(j.Vy), B._ptr(j.Vz)
                 r.nbr = B._ptr(j.nbr)
                 r.out_stride = int(j.out_stride)

@@ -120,3 +120,53 @@ def test_submit_host_checks_the_grid_capacity():
         assert np.array_equal(nb.numpy().view(np.uint32)[b.perm], r.nbr)
     finally:
         B.pi_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 1000, 4099])
+def test_strided_host_step_equals_separate_arrays(n):
+    """One block each way (one copy in, one out) gives bit for bit the
+    results of separate arrays; bad strides and arrays off their stride are
+    rejected before anything is enqueued."""
+    torch = pytest.importorskip("torch")
+    w = W.scaled(W.SMALL, max(n, 1))
+    x, y, z = (a[:n] for a in w.positions())
+    cap = 4100
+    ctx = B.pi_create(w.lo, w.hi, w.rc, cap)
+    try:
+        d = max(4, (n + 3) // 4 * 4)
+        blk = torch.zeros(3 * d).pin_memory()
+        for k, a in enumerate((x, y, z)):
+            blk[k * d:k * d + n] = torch.from_numpy(a)
+        outb = torch.full((5 * d,), float("nan")).pin_memory()
+        # addresses inside the blocks (slices of no elements may not carry one)
+        ib, ob = blk.data_ptr(), outb.data_ptr()
+
+        def at(base, s, k):
+            return base + 4 * s * k
+
+        B.pi_submit_host_strided(ctx, w.lo, w.hi, w.rc, at(ib, d, 0), at(ib, d, 1), at(ib, d, 2), d, n, w.h,
+                                 *(at(ob, d, k) for k in range(5)), d)
+        B.pi_sync_status(ctx)
+        o = [outb[k * d:k * d + n] for k in range(4)] + [outb[4 * d:4 * d + n].view(torch.int32)]
+        sep = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (x, y, z)]
+        ref = [torch.empty(max(n, 1)).pin_memory() for _ in range(4)]
+        rnb = torch.empty(max(n, 1), dtype=torch.int32).pin_memory()
+        B.pi_run_host(ctx, *sep, n, w.h, *ref, rnb)
+        for a, b in zip(o, ref + [rnb]):
+            assert np.array_equal(a.numpy().view(np.uint32), b[:n].numpy().view(np.uint32))
+        bad = [(d + 2, d + 2),                       # not a multiple of 4
+               (d, (cap + 4 + 3) // 4 * 4 + 4)]      # beyond the staging arrays
+        if n > 4:
+            bad.append((n - 1 - (n - 1) % 4, d))     # below n
+        for si, so in bad:
+            with pytest.raises(B.PiError) as e:
+                B.pi_submit_host_strided(ctx, w.lo, w.hi, w.rc, at(ib, si, 0), at(ib, si, 1), at(ib, si, 2), si,
+                                         n, w.h, *(at(ob, so, k) for k in range(5)), so)
+            assert e.value.status == B.PI_ERR_INVALID_ARG
+        # y not at x + stride
+        with pytest.raises(B.PiError) as e:
+            B.pi_submit_host_strided(ctx, w.lo, w.hi, w.rc, at(ib, d, 0), at(ib, d, 2), at(ib, d, 2), d, n, w.h,
+                                     *(at(ob, d, k) for k in range(5)), d)
+        assert e.value.status == B.PI_ERR_INVALID_ARG
+    finally:
+        B.pi_destroy(ctx)
