@@ -38,10 +38,14 @@ __global__ void k_zero(ZeroArgs<NB> z)
     for (size_t k = i; k < (size_t)z.nb; k += stride) z.pbase[k] = z.vals[k];
 }
 
-// a1 + a2.  Each lane owns a group of 4 consecutive particles, loaded as one
-// float4 per component when the arrays are 16-byte aligned.  The system of
-// each particle comes from the particle bases; its cell is offset by the
-// system's first cell.
+// Particles per lane of k_hist (a multiple of 4: float4 loads and stores).
+constexpr int HIST_PER_LANE = 4;
+
+// a1 + a2.  Each lane owns a group of HIST_PER_LANE consecutive particles,
+// loaded as float4s per component when the arrays are 16-byte aligned, so
+// that all of its atomics are in flight together.  The system of each
+// particle comes from the particle bases; its cell is offset by the system's
+// first cell.
 __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               const float* __restrict__ y,
                                               const float* __restrict__ z, uint32_t n, Systems sy,
@@ -50,28 +54,32 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               uint32_t* __restrict__ rank_out,
                                               Ctrl* __restrict__ ctrl, int vec)
 {
+    constexpr int HP = HIST_PER_LANE, HV = HP / 4;
     const unsigned lane = threadIdx.x & 31u;
-    const uint32_t groups = (n + 3u) / 4u;
+    const uint32_t groups = (n + HP - 1u) / HP;
     const uint32_t stride = gridDim.x * blockDim.x;
     bool all_ok = true;
     for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < groups; g0 += stride) {
         const uint32_t grp = g0 + lane;
-        const uint32_t i0 = grp * 4u;
-        float px[4], py[4], pz[4];
-        bool valid[4];
-        const bool full = (grp < groups) && (i0 + 4u <= n);
+        const uint32_t i0 = grp * HP;
+        float px[HP], py[HP], pz[HP];
+        bool valid[HP];
+        const bool full = (grp < groups) && (i0 + HP <= n);
         if (full && vec) {
-            float4 a = __ldcs(reinterpret_cast<const float4*>(x) + grp);
-            float4 b = __ldcs(reinterpret_cast<const float4*>(y) + grp);
-            float4 c = __ldcs(reinterpret_cast<const float4*>(z) + grp);
-            px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
-            py[0] = b.x; py[1] = b.y; py[2] = b.z; py[3] = b.w;
-            pz[0] = c.x; pz[1] = c.y; pz[2] = c.z; pz[3] = c.w;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) valid[j] = true;
+            for (int v = 0; v < HV; ++v) {
+                const float4 a = __ldcs(reinterpret_cast<const float4*>(x) + grp * HV + v);
+                const float4 b = __ldcs(reinterpret_cast<const float4*>(y) + grp * HV + v);
+                const float4 c = __ldcs(reinterpret_cast<const float4*>(z) + grp * HV + v);
+                px[4 * v] = a.x; px[4 * v + 1] = a.y; px[4 * v + 2] = a.z; px[4 * v + 3] = a.w;
+                py[4 * v] = b.x; py[4 * v + 1] = b.y; py[4 * v + 2] = b.z; py[4 * v + 3] = b.w;
+                pz[4 * v] = c.x; pz[4 * v + 1] = c.y; pz[4 * v + 2] = c.z; pz[4 * v + 3] = c.w;
+            }
+#pragma unroll
+            for (int j = 0; j < HP; ++j) valid[j] = true;
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < HP; ++j) {
                 const uint32_t i = i0 + j;
                 valid[j] = (grp < groups) && (i < n);
                 px[j] = valid[j] ? x[i] : 0.f;
@@ -80,12 +88,12 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
             }
         }
         int s = (sy.S == 1 || grp >= groups) ? 0 : find_system(sy.pbase, sy.S, i0);
-        // all four cells, then all four atomics: the atomics of one lane are
-        // in flight together.  Particles come in no spatial order, so a warp
-        // almost never holds two of one cell: no warp aggregation.
-        uint32_t cell[4], rank[4];
+        // all cells, then all atomics: the atomics of one lane are in flight
+        // together.  Particles come in no spatial order, so a warp almost
+        // never holds two of one cell: no warp aggregation.
+        uint32_t cell[HP], rank[HP];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < HP; ++j) {
             if (sy.S > 1 && valid[j])
                 while (s + 1 < sy.S && i0 + j >= __ldg(sy.pbase + s + 1)) ++s;
             const SysDesc& d = sy.sys[s];
@@ -94,13 +102,18 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
             all_ok &= ok | !valid[j];
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rank[j] = valid[j] ? atomicAdd(&counts[cell[j]], 1u) : 0u;
+        for (int j = 0; j < HP; ++j) rank[j] = valid[j] ? atomicAdd(&counts[cell[j]], 1u) : 0u;
         if (full) {
-            reinterpret_cast<uint4*>(cell_out)[grp] = make_uint4(cell[0], cell[1], cell[2], cell[3]);
-            reinterpret_cast<uint4*>(rank_out)[grp] = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+#pragma unroll
+            for (int v = 0; v < HV; ++v) {
+                reinterpret_cast<uint4*>(cell_out)[grp * HV + v] =
+                    make_uint4(cell[4 * v], cell[4 * v + 1], cell[4 * v + 2], cell[4 * v + 3]);
+                reinterpret_cast<uint4*>(rank_out)[grp * HV + v] =
+                    make_uint4(rank[4 * v], rank[4 * v + 1], rank[4 * v + 2], rank[4 * v + 3]);
+            }
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < HP; ++j)
                 if (valid[j]) {
                     cell_out[i0 + j] = cell[j];
                     rank_out[i0 + j] = rank[j];
@@ -353,12 +366,12 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
                 pz[j] = valid[j] ? z[i] : 0.f;
             }
         }
-        uint32_t lo[4], hi[4];
+        // rank < count holds by the atomic's semantics, so the slot lies in
+        // the cell's range; the test against n only keeps a corrupted rank
+        // from writing outside the records
+        uint32_t lo[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            lo[j] = valid[j] ? offsets[c[j]] : 0u;
-            hi[j] = valid[j] ? offsets[c[j] + 1] : 0u;
-        }
+        for (int j = 0; j < 4; ++j) lo[j] = valid[j] ? offsets[c[j]] : 0u;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!valid[j]) continue;
@@ -366,7 +379,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
             const SysDesc& d = sy.sys[sid];
             const uint2 t = sub_bin_thermometer(px[j], c[j] - d.cell_base, d.g);
             const uint32_t slot = lo[j] + r[j];
-            if (slot < hi[j]) store_rec(rec + slot, px[j], i0 + j, t.x, t.y, py[j], pz[j], c[j]);
+            if (slot < n) store_rec(rec + slot, px[j], i0 + j, t.x, t.y, py[j], pz[j], c[j]);
             else bad = true;
         }
     }
@@ -503,7 +516,7 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
                         Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
-    const uint64_t groups = ((uint64_t)n + 3) / 4;
+    const uint64_t groups = ((uint64_t)n + HIST_PER_LANE - 1) / HIST_PER_LANE;
     // exactly the resident CTAs (grid-stride loop): no partial last wave
     k_hist<<<grid_for(groups, 256, num_sms, resident_per_sm(k_hist, 0)), 256, 0, s>>>(x, y, z, n, sy, counts, cell, rank,
                                                              ctrl, vec);
