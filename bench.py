@@ -314,6 +314,16 @@ def run_ours(args):
     dev_time_max, pairs_all = replicas.aggregate(dev_time, pairs, dev)
     value = replicas.job_rate(pairs_all, K, dev_time_max)
 
+    # the paper's protocol: the mean of 200 back-to-back asynchronous
+    # interaction calls (no L2 flush between them)
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record(s)
+    for _ in range(200):
+        B.pi_interact(ctx, w.h, S, Vx, Vy, Vz, nb, B.PI_ORDER_SORTED, s)
+    eb1.record(s)
+    eb1.synchronize()
+    back_to_back = 1e3 * eb0.elapsed_time(eb1) / 200
+
     # ---- end to end through the host-buffer entry points (pinned memory)
     e2e = None
     if args.e2e_steps > 0:
@@ -418,18 +428,33 @@ def run_ours(args):
 
         oracle.build()
         # whole oracle steps on the same particles, repeated for about 10 s
-        reps, t_cpu, cpu_pairs = 0, 0.0, 0
-        while reps == 0 or t_cpu < 10.0:
+        reps, t_bin_cpu, t_int_cpu, cpu_pairs = 0, 0.0, 0.0, 0
+        while reps == 0 or t_bin_cpu + t_int_cpu < 10.0:
             t0 = time.perf_counter()
             b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
+            t1 = time.perf_counter()
             r = oracle.interact(b, w.rc, w.h)
-            t_cpu += time.perf_counter() - t0
+            t_bin_cpu += t1 - t0
+            t_int_cpu += time.perf_counter() - t1
             cpu_pairs += int(r.nbr.sum())
             reps += 1
-        cpu = {"value": cpu_pairs / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
+        t_cpu = t_bin_cpu + t_int_cpu
+        cores = oracle.num_threads()
+        # and one step on a single core
+        oracle.set_num_threads(1)
+        try:
+            t0 = time.perf_counter()
+            b = oracle.bin_particles(x, y, z, w.lo, w.hi, w.rc)
+            r1 = oracle.interact(b, w.rc, w.h)
+            t_one = time.perf_counter() - t0
+        finally:
+            oracle.set_num_threads(cores)
+        cpu = {"value": cpu_pairs / t_cpu, "unit": UNIT, "cores": cores,
                "kind": "oracle",
                "sample": f"{reps} full steps (bin + interact) of the {w.name} workload, "
-                         f"{n} particles each, FP64 oracle, {t_cpu:.1f} s in all"}
+                         f"{n} particles each, FP64 oracle, {t_cpu:.1f} s in all",
+               "bin_s_per_step": t_bin_cpu / reps, "interact_s_per_step": t_int_cpu / reps,
+               "single_core": {"value": int(r1.nbr.sum()) / t_one, "unit": UNIT, "s_per_step": t_one}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -439,7 +464,9 @@ def run_ours(args):
         "full_step_particles_per_s": ws * n * K / dev_time_max,
         "pairs_per_step": pairs, "max_per_cell": mpc2,
         "interact_pairs_per_s": pairs / mean_int, "bin_us": 1e6 * mean_bin,
-        "interact_us": 1e6 * mean_int,
+        "interact_us": 1e6 * mean_int, "bin_us_median": 1e6 * statistics.median(t_bin),
+        "interact_us_median": 1e6 * statistics.median(t_int),
+        "interact_us_back_to_back": back_to_back,
         "tile": tile, "tile_ms": tile_ms,
         "roofline": roofline, "roofline_binning": binning, "peak_source": peak_kind,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
