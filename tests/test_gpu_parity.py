@@ -8,6 +8,8 @@ of every kernel to the full benchmark workloads, in the launch configuration
 the benchmark times.
 """
 import numpy as np
+
+import oracle
 import pytest
 
 from paper_2406_16091_gb300 import binding as B
@@ -179,6 +181,23 @@ def test_full_size_workloads(name):
     check_interaction(g, r)
     # each within-cutoff pair is seen from both sides
     assert int(g["nbr"].astype(np.int64).sum()) % 2 == 0
+
+
+def test_full_size_precision_and_comparator_rows():
+    """At full size in the bench's launch configuration: the compensated
+    sums on the 4.2 M clustered workload (the precision row) and the
+    Lennard-Jones comparator on the 2 M scale workload match the oracle, and
+    the compensated error is no larger than the plain one."""
+    w = W.WORKLOADS["clustered"]
+    x, y, z, lo, hi, rc, h = _case(w)
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    plain = check_interaction(run_gpu(x, y, z, lo, hi, rc, h, binned=False), r)
+    kahan = check_interaction(run_gpu(x, y, z, lo, hi, rc, h, precision=B.PI_PREC_KAHAN, binned=False), r)
+    assert kahan["S"] <= plain["S"]
+    w = W.WORKLOADS["scale"]
+    x, y, z, lo, hi, rc, h = _case(w)
+    b, r = oracle_run(x, y, z, lo, hi, rc, h, oracle.LJ)
+    check_interaction(run_gpu(x, y, z, lo, hi, rc, h, kernel=B.PI_KERNEL_LJ, binned=False), r)
 
 
 # ---- failure paths: no fault, the status comes back and the context recovers ----
