@@ -17,28 +17,34 @@
 // cell and X-row indices are global over the concatenated systems.
 //
 // Kernels:
-//   k_interact_ppnl   Alg. 1 (Par-Part-NoLoop): one thread per particle,
-//                     sources read straight from global memory.  Kept as the
-//                     comparator the paper measures its speedups against.
-//   k_interact_tiled  reads P, the x-ordered copy written by binning: the
-//                     sorted particles with every cell ordered by x, as float4
-//                     (x, y, z, stable slot); every X-row of P is sorted by x
-//                     as a whole.  Work items are segments of an X-row of
-//                     target cells, handed out dynamically from one queue
-//                     over all systems, and processed in chunks of
-//                     consecutive cells.  The 9 neighbour rows (y +- 1,
-//                     z +- 1) of a chunk are contiguous ranges of P, each
-//                     staged into shared memory with one cp.async.bulk copy
-//                     (Sec. 5.2 loads pencils along X; here
-//                     the whole 3x3 bundle of pencils is loaded at once
-//                     because the sorted order makes each one contiguous).
-//                     Each thread holds one target in registers and, per
-//                     neighbour row, scans only the x-window
-//                     [x_i - w_r, x_i + w_r], w_r = sqrt(rc^2 - d_yz^2), where
-//                     d_yz is the target's distance to the row in y and z:
-//                     sources outside it cannot pass the pair test.  Pairs
-//                     of candidates are evaluated with packed f32x2
-//                     arithmetic.
+//   k_interact_ppnl    Alg. 1 (Par-Part-NoLoop): one thread per particle,
+//                      sources read straight from global memory.  Kept as
+//                      the comparator the paper measures its speedups
+//                      against.
+// The others read P, the x-ordered copy written by binning: the sorted
+// particles as float4 (x, y, z, stable slot), every X-row of cells sorted by
+// x as a whole and followed by ROW_PADS sentinel slots.  A target scans, per
+// neighbour row (y +- 1, z +- 1), only the x-window [x_i - w_r, x_i + w_r],
+// w_r = sqrt(rc^2 - d_yz^2) with d_yz its distance to the row in y and z
+// (sources outside it cannot pass the pair test), found from per-cell
+// x-sub-bin starts; each thread takes two x-adjacent targets and evaluates
+// every source against both with packed f32x2 arithmetic.
+//   k_interact_direct  (default) one thread per target pair, windows from
+//                      global memory, sources read through L1; one flattened
+//                      loop over all windows.  Every kernel K and both
+//                      precision modes.
+//   k_interact_tiled   work items are segments of an X-row of target cells,
+//                      handed out dynamically from one queue over all
+//                      systems and processed in chunks of consecutive cells;
+//                      the 9 neighbour rows of a chunk are contiguous ranges
+//                      of P, each staged into shared memory with one
+//                      cp.async.bulk copy (Sec. 5.2 loads pencils along X;
+//                      here the whole 3x3 bundle is loaded at once because
+//                      the sorted order makes each one contiguous).
+//   k_interact_ws      the same chunks with a producer warp that stages them
+//                      for consumer warps (warp specialisation).
+// All of them sum each target's terms in the order of its own windows, so
+// their outputs are bitwise equal.
 #include <type_traits>
 
 #include "pi_internal.cuh"
