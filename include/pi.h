@@ -401,7 +401,8 @@ pi_status pi_server_create(int32_t num_buckets, const int64_t* capacity, const i
  * PI_ERR_INVALID_ARG for a bad job, PI_ERR_CAPACITY for one that fits no
  * bucket (nothing runs then).  Afterwards the device status of every slot
  * is collected as in pi_sync_status.  The host arrays of a job must stay
- * valid until the call returns. */
+ * valid until the call returns.  The calling thread polls while jobs run
+ * (it sleeps only when nothing is running or queued). */
 pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* makespan_s);
 
 /* Buckets (num_buckets; capacity and slots as arrays of that length, any
