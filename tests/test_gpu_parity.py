@@ -126,6 +126,25 @@ def test_lattice_on_cell_faces():
         check_interaction(g, r)
 
 
+@pytest.mark.parametrize("box,rc,n", [
+    (((0, 0, 0), (1, 1, 1)), 1.5, 600),            # one cell: every pair a candidate
+    (((0, 0, 0), (1, 1, 1)), 0.5, 800),            # 2 x 2 x 2 cells, all at a boundary
+    (((0, 0, 0), (4, 0.3, 0.3)), 0.31, 700),       # cells only along X (rows of 12 cells)
+    (((0, 0, 0), (0.3, 0.3, 4)), 0.31, 700),       # one cell per X-row, a stack along Z
+    (((0, 0, 0), (0.3, 4, 0.3)), 0.31, 700),       # one cell per X-row, a stack along Y
+])
+def test_degenerate_grids(box, rc, n):
+    """Grids with one cell per axis or per row: windows clip to the single
+    row, every X-row is one cell followed by its sentinel slots."""
+    lo, hi = box
+    x, y, z = W.uniform(n, 31 + n, lo, hi)
+    b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2)
+    for algo, tile in VARIANTS:
+        g = run_gpu(x, y, z, lo, hi, rc, rc / 2, algo=algo, tile=tile)
+        check_binning(g, b)
+        check_interaction(g, r)
+
+
 def test_coincident_particles():
     x = np.full(50, 0.3, np.float32)
     y = np.full(50, 0.6, np.float32)
