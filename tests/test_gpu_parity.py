@@ -145,6 +145,41 @@ def test_degenerate_grids(box, rc, n):
         check_interaction(g, r)
 
 
+def _random_case(seed):
+    """A seeded random configuration: box offset and extents, cutoff,
+    particle count (empty and ragged included), layout and kernel width."""
+    rng = np.random.default_rng(seed)
+    lo = tuple(float(v) for v in rng.uniform(-3, 3, 3).astype(np.float32))
+    ext = rng.uniform(0.2, 3.0, 3)
+    hi = tuple(float(np.float32(l + e)) for l, e in zip(lo, ext))
+    cells = rng.integers(1, 24, 3)
+    rc = float(np.float32(min(e / c for e, c in zip(ext, cells)) * rng.uniform(0.6, 1.0)))
+    n = int(rng.choice([0, 1, 33, 500, 3000, 12000, 30000, 60000]))
+    if n >= 500 and rng.random() < 0.5:
+        x, y, z = W.clustered(n, 500 + seed)
+        x, y, z = (np.float32(l) + np.float32(e) * a for l, e, a in zip(lo, ext, (x, y, z)))
+        x, y, z = (np.minimum(a.astype(np.float32), np.nextafter(np.float32(h), np.float32(l))).astype(np.float32)
+                   for a, l, h in zip((x, y, z), lo, hi))
+    else:
+        x, y, z = W.uniform(n, 500 + seed, lo, hi)
+    h = float(rc * rng.uniform(0.3, 1.2))
+    return x, y, z, lo, hi, rc, h
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_configurations(seed):
+    """Seeded random boxes, cutoffs, sizes and layouts through the direct
+    kernel (both precision modes), a staged shape and Alg. 1."""
+    x, y, z, lo, hi, rc, h = _random_case(seed)
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    for algo, tile, prec in ((B.PI_ALGO_TILED, 5, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 5, B.PI_PREC_KAHAN),
+                             (B.PI_ALGO_TILED, 2, B.PI_PREC_FP32), (B.PI_ALGO_PPNL, None, B.PI_PREC_FP32)):
+        g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile, precision=prec, n_max=max(len(x), 1))
+        check_binning(g, b)
+        if len(x):
+            check_interaction(g, r)
+
+
 def test_coincident_particles():
     x = np.full(50, 0.3, np.float32)
     y = np.full(50, 0.6, np.float32)
