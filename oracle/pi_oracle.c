@@ -21,7 +21,7 @@
  *   Alg. 5, Sec. 5.2: neighbour cells are clipped at the box faces
  *     (Max(0, .) / Min(limit, .)), i.e. the box is not periodic.
  *
- * Readings where the paper is silent (each is also listed in the design doc):
+ * Readings where the paper is silent:
  *   - K is the Gaussian exp(-r^2/h^2) by default; outputs S_i = sum K and
  *     V_i = sum (p_j - p_i) K (the paper's Lennard-Jones constants are not
  *     fixed by its text).  The other kernels, for the comparisons of
