@@ -216,7 +216,7 @@ def run_reference(args):
 
 
 def workload_config(w, args):
-    return {"workload": f"{w.name}: {w.note}, uniform in [0,1)^3 (seeded), non-periodic, "
+    return {"workload": f"{w.name}: {w.note}, {w.layout} in [0,1)^3 (seeded), non-periodic, "
                         f"r_c={w.rc:.9g}, Gaussian K with h=r_c/2, outputs S, V and neighbour count",
             "n_particles": w.n, "cells": [w.cells_per_axis()] * 3, "r_c": w.rc, "h": w.h,
             "layout": w.layout, "algo": args.algo, "precision": args.precision,
