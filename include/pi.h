@@ -91,9 +91,10 @@ enum {
      * (one producer warp stages chunks of up to 2432 particles into 2
      * buffers for 4 or 8 consumer warps); 5 for the direct form (no
      * staging: one thread per target pair reads its sources from global
-     * memory through L1; the Gaussian kernel in FP32 only, the others run
-     * shape 2).  Default 5.  pi_autotune sets it
-     * from measurements.  Results do not depend on it. */
+     * memory through L1; every kernel K and both precision modes).  With a
+     * kernel other than the Gaussian, shapes 0 - 4 all run shape 2's
+     * one-target form.  Default 5.  pi_autotune sets it from measurements.
+     * Results do not depend on it. */
     PI_OPT_TILE = 6
 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
