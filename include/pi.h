@@ -69,13 +69,15 @@ enum {
 
 /* Keys of pi_set_option(). */
 enum {
-    /* Interaction algorithm.  PI_ALGO_TILED (default) stages neighbour X-rows
-     * of cells in shared memory; PI_ALGO_PPNL is Alg. 1 of the paper
-     * (Par-Part-NoLoop: one thread per particle, sources read from global
-     * memory), kept as the in-library comparator. */
+    /* Interaction algorithm.  PI_ALGO_TILED (default): per-target x-windows
+     * over the x-sorted neighbour X-rows, in the shape PI_OPT_TILE selects;
+     * PI_ALGO_PPNL is Alg. 1 of the paper (Par-Part-NoLoop: one thread per
+     * particle, the 27-cell stencil read from global memory), kept as the
+     * in-library comparator. */
     PI_OPT_ALGO = 1,
     /* Accumulation: PI_PREC_FP32 (default) plain FP32 sums; PI_PREC_KAHAN
-     * compensated FP32 sums per particle and output. */
+     * compensated FP32 sums per particle and output (a Kahan step per
+     * accepted pair; pairs that fail the test are skipped). */
     PI_OPT_PRECISION = 2,
     /* Upper bound, in nanoseconds, of every device-side wait (default 1e9). */
     PI_OPT_WAIT_LIMIT_NS = 3,
