@@ -405,7 +405,8 @@ pi_status pi_server_create(int32_t num_buckets, const int64_t* capacity, const i
  * bucket (nothing runs then).  Afterwards the device status of every slot
  * is collected as in pi_sync_status.  The host arrays of a job must stay
  * valid until the call returns.  The calling thread polls while jobs run
- * (it sleeps only when nothing is running or queued). */
+ * (it sleeps only when nothing is running or queued).  Like a context, a
+ * server is used by one host thread at a time. */
 pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* makespan_s);
 
 /* Buckets (num_buckets; capacity and slots as arrays of that length, any
