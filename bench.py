@@ -422,9 +422,12 @@ def run_ours(args):
     bin_bytes = 72 * n + 12 * C
     mean_bin = statistics.fmean(t_bin)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    bin_traffic = recorded_traffic("binning", source_hash([os.path.join(src, "pi_bin.cu"),
+                                                          os.path.join(src, "pi_internal.cuh")]))
     binning = {"bound": "hbm", "achieved": bin_bytes / mean_bin / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": bin_bytes / mean_bin / 1e9 / hbm_peak,
                "algorithmic_bytes": bin_bytes, "mean_us": 1e6 * mean_bin,
+               "traffic": bin_traffic["dram_bytes_per_launch"] if bin_traffic else None,
                "kernels": ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"]}
 
     cpu = None
