@@ -254,6 +254,19 @@ def test_full_size_precision_and_comparator_rows():
     check_interaction(run_gpu(x, y, z, lo, hi, rc, h, kernel=B.PI_KERNEL_LJ, binned=False), r)
 
 
+def test_large_system_64m_particles():
+    """2^26 particles on a 203^3 grid (8 per cell, 8.4 M cells, about 5 GB on
+    the device): particle indices, offsets and P slots past 2^26, every
+    output against the oracle."""
+    w = W.scaled(W.SCALE, 1 << 26)
+    assert w.cells_per_axis() == 203
+    x, y, z, lo, hi, rc, h = _case(w)
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    g = run_gpu(x, y, z, lo, hi, rc, h)
+    check_binning(g, b)
+    check_interaction(g, r)
+
+
 # ---- failure paths: no fault, the status comes back and the context recovers ----
 
 def test_out_of_box_reported_then_recovers():
