@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--flush-mb", type=int, default=512)
     p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
                    help="tile shape of the tiled interaction (auto: pi_autotune during warm-up)")
-    p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep"],
+    p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep", "sizes"],
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
     p.add_argument("--max-slots", type=int, default=8, help="serving study: slots per capacity bucket")
@@ -771,8 +771,47 @@ def study_sweep(args):
     print(json.dumps({"study": "sweep", "rows": rows}), flush=True)
 
 
+def study_sizes(args):
+    """One full step (bin + interact) at 8 particles per cell from 32 K to
+    2^28 particles (the largest about 20 GB on the device): throughput in N,
+    medians of CUDA events with the L2 flushed before every step."""
+    torch, B = _torch_setup()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, device=dev)
+    s = torch.cuda.current_stream()
+    rows = []
+    for n in (1 << 15, 1 << 18, 1 << 21, 1 << 24, 1 << 26, 1 << 28):
+        w = W.scaled(W.SCALE, n)
+        x, y, z = w.positions()
+        ctx = B.pi_create(w.lo, w.hi, w.rc, n)
+        try:
+            tx, ty, tz = (torch.from_numpy(a).to(dev) for a in (x, y, z))
+            out = [torch.empty(n, device=dev) for _ in range(4)]
+            nb = torch.empty(n, dtype=torch.int32, device=dev)
+            B.pi_bin(ctx, tx, ty, tz, n, s)
+            B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+            B.pi_sync_status(ctx, s)
+            pairs = int(nb.to(torch.int64).sum().item())
+            reps = 20 if n <= (1 << 24) else 5
+            bin_ms, _ = _time_events(torch, lambda: B.pi_bin(ctx, tx, ty, tz, n, s), reps, flush)
+            step_ms, _ = _time_events(torch, lambda: (B.pi_bin(ctx, tx, ty, tz, n, s),
+                                                      B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)),
+                                      reps, flush)
+            B.pi_sync_status(ctx, s)
+            rows.append({"n": n, "cells_per_axis": w.cells_per_axis(), "pairs": pairs,
+                         "step_ms": step_ms, "bin_ms": bin_ms,
+                         "pairs_per_s": pairs / (step_ms * 1e-3),
+                         "particles_per_s": n / (step_ms * 1e-3)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del tx, ty, tz, out, nb
+        finally:
+            B.pi_destroy(ctx)
+        torch.cuda.empty_cache()
+    print(json.dumps({"study": "sizes", "rows": rows, "l2": "flushed before every timed step"}), flush=True)
+
+
 STUDIES = {"precision": study_precision, "batched": study_batched, "serving": study_serving,
-           "sweep": study_sweep}
+           "sweep": study_sweep, "sizes": study_sizes}
 
 def main():
     args = parse()
