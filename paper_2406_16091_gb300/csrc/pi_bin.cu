@@ -398,8 +398,9 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 //     and followed by ROW_PADS sentinel slots (written here too);
 //   - (the member of x-rank 0 only) xbins[c]: byte b - 1 (b = 1 .. XSUB - 1)
 //     = members whose x-sub-bin is < b, the sum of the members' thermometers
-//     (see Rec); byte 7 = 1 when the cell has more than 255 members, bytes
-//     0..6 then 0 (every sub-bin starts at the cell).
+//     (see Rec); byte 7 holds flags: XBIN_COARSE when the cell has more
+//     than 255 members (bytes 0..6 then 0: every sub-bin starts at the
+//     cell), XBIN_DENSE when it has more than DENSE_CELL.
 __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, uint32_t n,
                                                    Systems sy, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ perm,
@@ -453,7 +454,11 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         // the first member in x order writes the cell's sub-bin starts; the
         // byte sums are exact up to 255 members, larger cells are flagged
         static_assert(XSUB == 8, "xbins packs 7 sub-bin starts and a flag into 8 bytes");
-        if (xr == 0) xbins[c] = (s1 - s0 > 255u) ? make_uint2(0u, 1u << 24) : make_uint2(lt_lo, lt_hi);
+        if (xr == 0) {
+            const uint32_t m = s1 - s0;
+            xbins[c] = m > 255u ? make_uint2(0u, XBIN_COARSE << 24)
+                                : make_uint2(lt_lo, lt_hi | (m > DENSE_CELL ? XBIN_DENSE << 24 : 0u));
+        }
     }
     if (bad) atomicOr(&ctrl->error, ERR_CAPACITY);
 }

@@ -511,7 +511,7 @@ __device__ __forceinline__ void build_table(const InteractArgs& a, const SysDesc
             ent[0] = (E)start[i];
             continue;
         }
-        if (w[i].y >> 24) atomicOr(coarse_mask, 1u << rr);
+        if ((w[i].y >> 24) & XBIN_COARSE) atomicOr(coarse_mask, 1u << rr);
         E v[XSUB];
         v[0] = (E)start[i];
 #pragma unroll
@@ -1232,16 +1232,33 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
 
 constexpr int DIRECT_THREADS = 128;
 
+// First index in [lo, hi) of P whose x is >= v (strict: > v); hi if none.
+__device__ __noinline__ uint32_t x_bound(const float4* P, uint32_t lo, uint32_t hi, float v, bool strict)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const float xm = __ldg(&P[mid].x);
+        const bool left = strict ? !(xm > v) : (xm < v);
+        lo = left ? mid + 1u : lo;
+        hi = left ? hi : mid;
+    }
+    return lo;
+}
+
 // First index of P whose sub-bin in the row starting at cell `rb` is >= b
 // (b counted from the row's first cell); `upper`: round a sub-bin of a cell
 // without sub-bin starts up to the cell's end instead of down to its start.
-__device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_t rb, int b, bool upper)
+// `dense` is set when the lookup read the sub-bin word of a cell with more
+// than DENSE_CELL members (left unchanged otherwise).
+__device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_t rb, int b, bool upper,
+                                                  bool& dense)
 {
     const uint32_t k = (uint32_t)(b >> 3), sub = (uint32_t)(b & 7);
     const uint32_t start = __ldg(a.offsets + rb + k);
     if (sub == 0) return start;
     const uint2 w = __ldg(a.xbins + rb + k);
-    if (w.y >> 24) return upper ? __ldg(a.offsets + rb + k + 1) : start;
+    dense = (w.y >> 24) != 0u;
+    if ((w.y >> 24) & XBIN_COARSE) return upper ? __ldg(a.offsets + rb + k + 1) : start;
     const uint32_t word = sub <= 4 ? w.x : w.y;
     return start + ((word >> (8 * ((sub - 1) & 3))) & 255u);
 }
@@ -1250,6 +1267,7 @@ __device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_
 // here the lookups read global memory), merged into the union windows
 // [ulo, uhi) of a group of targets: a non-empty window widens its row's
 // union, an empty one leaves it as it is.
+template <bool DENSE>
 __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, const SysDesc& d, const float4& t,
                                                       int cx, int cy, int cz, uint32_t (&ulo)[9],
                                                       uint32_t (&uhi)[9])
@@ -1272,10 +1290,24 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
         const float w = tt * rsqrtf(tt) + slack;
         const uint32_t row = (uint32_t)by + (uint32_t)ny * (uint32_t)bz;
         const uint32_t rb = d.cell_base + (uint32_t)nx * row, pad = ROW_PADS * (d.row_base + row);
-        const int b0 = sub_bin(t.x - w, xlo, invs, 0, lo, hi);
-        const int b1 = sub_bin(t.x + w, xlo, invs, 0, lo, hi) + 1;
-        const uint32_t j = sub_bin_start(a, rb, b0, false) + pad;
-        const uint32_t je = sub_bin_start(a, rb, b1, true) + pad;
+        const float xl = t.x - w, xu = t.x + w;
+        const int b0 = sub_bin(xl, xlo, invs, 0, lo, hi);
+        const int b1 = sub_bin(xu, xlo, invs, 0, lo, hi) + 1;
+        bool dl = false, du = false;
+        uint32_t j = sub_bin_start(a, rb, b0, false, dl) + pad;
+        uint32_t je = sub_bin_start(a, rb, b1, true, du) + pad;
+        // a bound inside a dense cell (b0's, or b1's when b1 is not the
+        // cell's first sub-bin): the exact bound from a binary search of the
+        // cell's x-sorted members.  Every source within the cutoff stays in
+        // the window, so the sums do not change; only fewer zeros are added.
+        if (DENSE && dl) {
+            const uint32_t k = (uint32_t)(b0 >> 3);
+            j = x_bound(a.P, __ldg(a.offsets + rb + k) + pad, __ldg(a.offsets + rb + k + 1) + pad, xl, false);
+        }
+        if (DENSE && du) {
+            const uint32_t k = (uint32_t)(b1 >> 3);
+            je = x_bound(a.P, __ldg(a.offsets + rb + k) + pad, __ldg(a.offsets + rb + k + 1) + pad, xu, true);
+        }
         if (je > j) {
             ulo[rr] = min(ulo[rr], j);
             uhi[rr] = max(uhi[rr], je);
@@ -1294,7 +1326,7 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
 // (the same row outside the windows, or the row's sentinel slots) -- add
 // exact zeros, so each target's sums are those of the sequential loop over
 // its own windows.
-template <int WT, int G, class Acc, int KERNEL>
+template <int WT, int G, bool DENSE, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
                                              unsigned col, const float4 (&t)[G], const int (&cx)[G], int cy,
                                              int cz, const KParams& kp, Sums<Acc, KERNEL> (&r)[G])
@@ -1309,7 +1341,7 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
             uhi[rr] = 0u;
         }
 #pragma unroll
-        for (int k = 0; k < G; ++k) target_windows_direct(a, d, t[k], cx[k], cy, cz, ulo, uhi);
+        for (int k = 0; k < G; ++k) target_windows_direct<DENSE>(a, d, t[k], cx[k], cy, cz, ulo, uhi);
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr)
             if (uhi[rr] > ulo[rr]) {
@@ -1360,7 +1392,7 @@ __device__ __forceinline__ void self_terms(float& kself, uint32_t& nself)
 }
 
 // Slots ka and ka + 1 of P (either may be a sentinel or past the end).
-template <int WT, class Acc, int KERNEL>
+template <int WT, bool DENSE, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t (*win)[WT], unsigned col,
                                                  uint32_t ka)
 {
@@ -1396,7 +1428,7 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
         const float4 t[2] = {ta, together ? t1 : ta};
         const int cx[2] = {cxa, together ? cxb : cxa};
         Sums<Acc, KERNEL> r[2];
-        direct_group<WT, 2>(a, d, win, col, t, cx, cy, cz, kp, r);
+        direct_group<WT, 2, DENSE>(a, d, win, col, t, cx, cy, cz, kp, r);
         store_out(a, __float_as_uint(ta.w), r[0], kself, nself);
         if (together) store_out(a, __float_as_uint(t1.w), r[1], kself, nself);
     }
@@ -1410,9 +1442,18 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
         const float4 t[2] = {t1, t1};
         const int cx[2] = {cx1, cx1};
         Sums<Acc, KERNEL> r[2];
-        direct_group<WT, 2>(a, d1, win, col, t, cx, cy1, cz1, kp1, r);
+        direct_group<WT, 2, DENSE>(a, d1, win, col, t, cx, cy1, cz1, kp1, r);
         store_out(a, __float_as_uint(t1.w), r[0], kself, nself);
     }
+}
+
+// The slot pair with exact window bounds in dense cells, out of line so that
+// the common path keeps its code and registers.
+template <class Acc, int KERNEL>
+__device__ __noinline__ void direct_slot_pair_dense(const InteractArgs& a, uint32_t (*win)[DIRECT_THREADS],
+                                                    unsigned col, uint32_t ka)
+{
+    direct_slot_pair<DIRECT_THREADS, true, Acc, KERNEL>(a, win, col, ka);
 }
 
 // Resident CTAs per SM the direct kernel's registers are capped for.  The
@@ -1435,9 +1476,17 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL
     __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
     // keep the work counters of the tiled launches in step (see k_interact_tiled)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
-    if (load_error(a.ctrl)) return;
-    direct_slot_pair<DIRECT_THREADS, Acc, KERNEL>(a, win, threadIdx.x,
-                                                  2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x));
+    // both control words in flight together
+    const uint32_t err = load_error(a.ctrl);
+    const uint32_t mpc = *((volatile const uint32_t*)&a.ctrl->max_per_cell);
+    if (err) return;
+    // grids with dense cells take the exact window bounds in them (a
+    // separate copy of the path, so the common one keeps its registers)
+    const uint32_t k0 = 2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
+    if (mpc > DENSE_CELL)
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0);
+    else
+        direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL>(a, win, threadIdx.x, k0);
 }
 
 template <class Acc, int KERNEL>

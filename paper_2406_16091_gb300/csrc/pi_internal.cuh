@@ -112,6 +112,14 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // cell starts, and the tiled interaction uses them to find x-windows.
 constexpr int XSUB = 8;
 
+// Flags in the top byte of a cell's sub-bin word (xbins[c].y >> 24):
+// XBIN_COARSE, more than 255 members (the byte counts would overflow, so
+// every sub-bin starts at the cell); XBIN_DENSE, more than DENSE_CELL
+// members (the sub-bin starts are valid, but an interaction may prefer
+// exact window bounds from a binary search of the x-sorted members).
+constexpr uint32_t XBIN_COARSE = 1u, XBIN_DENSE = 2u;
+constexpr uint32_t DENSE_CELL = 255;
+
 // Cell index of a position (Sec. 2: "compute its cell index using its
 // physical position").  FP32, round-to-nearest subtract and multiply, floor,
 // clamp; X fastest so that an X-row of cells is contiguous after sorting.

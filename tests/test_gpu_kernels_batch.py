@@ -34,6 +34,40 @@ def test_kernel_parity(path, kern, precision):
     check_interaction(g, r)
 
 
+def _dense_cluster():
+    """Background plus one tight cluster: cells of several hundred members,
+    so the direct kernel takes exact window bounds in them."""
+    rng = np.random.default_rng(3)
+    bg = rng.random((20000, 3)).astype(np.float32)
+    cl = (0.5 + 0.004 * rng.standard_normal((6000, 3))).astype(np.float32)
+    p = np.concatenate([bg, cl])
+    return p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), (0, 0, 0), (1, 1, 1), 1.0 / 64
+
+
+@pytest.mark.parametrize("kern", KERNELS)
+@pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
+def test_dense_cells_exact_windows_bitwise_equal(kern, precision):
+    """Cells above 255 members: the direct kernel's binary-searched window
+    bounds (tighter than whole cells) give the staged path's sums bit for
+    bit, and both match the oracle."""
+    gk, ok = kern
+    x, y, z, lo, hi, rc = _dense_cluster()
+    b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2, ok)
+    assert b.max_per_cell > 255
+    res = {t: run_gpu(x, y, z, lo, hi, rc, rc / 2, precision=precision, kernel=gk, tile=t, binned=False)
+           for t in (2, 5)}
+    for k in ("S", "Vx", "Vy", "Vz", "nbr"):
+        assert np.array_equal(res[2][k].view(np.uint32), res[5][k].view(np.uint32)), k
+    # Plain FP32 sums of up to m terms carry the sequential-summation bound
+    # (m + 1) 2^-24 of sum|terms| (one rounding per term and per add); with
+    # several hundred neighbours of the Lennard-Jones kernel's wide range that
+    # bound, not 1e-5, is what FP32 can promise.  The compensated sums keep
+    # 1e-5 at any count.
+    m = int(r.nbr.max())
+    tol = TOL if precision == B.PI_PREC_KAHAN else max(TOL, 1.1 * (m + 2) * 2.0 ** -24)
+    check_interaction(res[5], r, tol=tol)
+
+
 @pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
 def test_staged_and_direct_paths_bitwise_equal(kern, precision):
