@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--flush-mb", type=int, default=512)
-    p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
+    p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6"],
                    help="tile shape of the tiled interaction (auto: pi_autotune during warm-up)")
     p.add_argument("--study", choices=["none", "precision", "batched", "serving", "sweep", "sizes"],
                    default="none", help="run one of the extra studies instead of the main line")
@@ -404,7 +404,8 @@ def run_ours(args):
     if args.algo != "tiled":
         kname = "k_interact_ppnl"
     else:
-        kname = {3: "k_interact_ws", 4: "k_interact_ws", 5: "k_interact_direct"}.get(tile, "k_interact_tiled")
+        kname = {3: "k_interact_ws", 4: "k_interact_ws", 5: "k_interact_direct",
+                 6: "k_interact_direct4"}.get(tile, "k_interact_tiled")
     traffic = recorded_traffic(kname, source_hash([os.path.join(src, "pi_interact.cu"),
                                                    os.path.join(src, "pi_internal.cuh")]))
     roofline = {

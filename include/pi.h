@@ -93,7 +93,9 @@ enum {
      * (one producer warp stages chunks of up to 2432 particles into 2
      * buffers for 4 or 8 consumer warps); 5 for the direct form (no
      * staging: one thread per target pair reads its sources from global
-     * memory through L1; every kernel K and both precision modes).  With a
+     * memory through L1; every kernel K and both precision modes); 6 for the
+     * direct form with four targets per thread (fewer source reads per
+     * evaluation, more evaluations: faster at high occupancy).  With a
      * kernel other than the Gaussian, shapes 0 - 4 all run shape 2's
      * one-target form.  Default 5.  pi_autotune sets it from measurements.
      * Results do not depend on it. */
@@ -249,10 +251,10 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
 /* Autotuner of the interaction for the data of the last pi_bin /
  * pi_batch_bin: runs the interaction (arguments as pi_batch_interact, h one
  * entry per system) once untimed and `reps` times timed (1 <= reps <= 100)
- * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..5) and then
+ * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..6) and then
  * with PI_ALGO_PPNL, keeps the candidate with the smallest median time for
  * later calls (setting PI_OPT_ALGO and PI_OPT_TILE), and returns its index in
- * *chosen (0..5 = tile shape, 6 = PI_ALGO_PPNL) and the medians in ms[7]
+ * *chosen (0..6 = tile shape, 7 = PI_ALGO_PPNL) and the medians in ms[8]
  * (milliseconds; either pointer may be NULL).  The choice changes only the
  * speed: every tile shape sums each target's terms in the same order, so
  * their outputs are identical; PPNL's agree with them within the stated

@@ -32,7 +32,7 @@ PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
-PI_NUM_TILES = 6  # tile shapes of PI_OPT_TILE (see include/pi.h)
+PI_NUM_TILES = 7  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_AUTOTUNE_PPNL = PI_NUM_TILES  # pi_autotune's index of PI_ALGO_PPNL
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1
@@ -323,7 +323,7 @@ def pi_scan_counts_noalloc(counts, C: int, offsets, result=None, stream=None) ->
 def pi_autotune(ctx, h, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTED, reps: int = 3,
                 stream=None):
     """Times every tile shape and PI_ALGO_PPNL on the binned data, keeps the
-    fastest.  Returns (chosen index: shape 0..5 or PI_AUTOTUNE_PPNL,
+    fastest.  Returns (chosen index: shape 0..6 or PI_AUTOTUNE_PPNL,
     [median ms per candidate])."""
     arr = (ctypes.c_float * len(h))(*[float(v) for v in h])
     chosen = ctypes.c_int32()

@@ -1489,6 +1489,79 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL
         direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL>(a, win, threadIdx.x, k0);
 }
 
+// Resident CTAs per SM the four-target direct kernel's registers are capped
+// for (the plain kernels: 5, about 100 registers; the others uncapped).
+template <class Acc, int KERNEL>
+__host__ __device__ constexpr int direct4_min_blocks()
+{
+    return (std::is_same<Acc, PlainAcc>::value && (KERNEL == KERNEL_GAUSSIAN || KERNEL == KERNEL_LOWFLOP)) ? 5 : 1;
+}
+
+// Four targets per thread: P slots 4p .. 4p + 3.  Each source read feeds
+// four targets (two packed pairs), so the L1 reads per evaluation halve
+// while the union of four windows adds evaluations -- the better trade at
+// high occupancy (32 per cell), the worse at low.  Four slots lie in one
+// X-row of one system unless some are sentinels (every row ends in
+// ROW_PADS of them), which repeat a real target and store nothing.  Grids
+// with dense cells take the slot pairs' dense path.
+template <class Acc, int KERNEL>
+__global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNEL>()))
+    k_interact_direct4(InteractArgs a)
+{
+    __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
+    // keep the work counters of the tiled launches in step (see k_interact_tiled)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
+    const uint32_t err = load_error(a.ctrl);
+    const uint32_t mpc = *((volatile const uint32_t*)&a.ctrl->max_per_cell);
+    if (err) return;
+    const uint32_t k0 = 4u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
+    if (k0 >= a.np) return;
+    if (mpc > DENSE_CELL) {
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0);
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0 + 2u);
+        return;
+    }
+    constexpr uint32_t NONE = 0xffffffffu;
+    float4 t[4];
+    bool v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        t[k] = k0 + k < a.np ? __ldg(a.P + k0 + k) : make_float4(0.f, 0.f, 0.f, __uint_as_float(NONE));
+        v[k] = __float_as_uint(t[k].w) != NONE;
+    }
+    if (!(v[0] || v[1] || v[2] || v[3])) return;
+    const float4 tf = v[0] ? t[0] : (v[1] ? t[1] : (v[2] ? t[2] : t[3]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (!v[k]) t[k] = tf;
+    // the system of the targets: from a stable slot (= sorted index)
+    const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.pbase, a.sy.S, __float_as_uint(tf.w));
+    const SysDesc& d = a.sy.sys[sid];
+    const Grid& g = d.g;
+    int cx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cx[k] = axis_cell(t[k].x, g.lo[0], g.inv_w[0], g.n[0]);
+    const int cy = axis_cell(tf.y, g.lo[1], g.inv_w[1], g.n[1]);
+    const int cz = axis_cell(tf.z, g.lo[2], g.inv_w[2], g.n[2]);
+    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
+    float kself;
+    uint32_t nself;
+    self_terms<Acc, KERNEL>(kself, nself);
+    Sums<Acc, KERNEL> r[4];
+    direct_group<DIRECT_THREADS, 4, false>(a, d, win, threadIdx.x, t, cx, cy, cz, kp, r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (v[k]) store_out(a, __float_as_uint(t[k].w), r[k], kself, nself);
+}
+
+template <class Acc, int KERNEL>
+void launch_direct4_one(const InteractArgs& a, cudaStream_t s)
+{
+    const uint64_t quads = ((uint64_t)a.np + 3) / 4;
+    k_interact_direct4<Acc, KERNEL>
+        <<<(unsigned)((quads + DIRECT_THREADS - 1) / DIRECT_THREADS), DIRECT_THREADS, 0, s>>>(a);
+}
+
 template <class Acc, int KERNEL>
 void launch_direct_one(const InteractArgs& a, cudaStream_t s)
 {
@@ -1526,24 +1599,27 @@ template <class Acc>
 cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
                              cudaStream_t s)
 {
-    // the comparator kernels run on the direct kernel or the 128-thread shape
-    if (a.kernel != KERNEL_GAUSSIAN && tile != 5) tile = 2;
+    // the comparator kernels run on the direct kernels or the 128-thread shape
+    if (a.kernel != KERNEL_GAUSSIAN && tile != 5 && tile != 6) tile = 2;
     uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
     if (grid > a.work) grid = a.work;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
-    const bool direct = tile == 5;
     switch (a.kernel) {
         case KERNEL_LJ:
-            direct ? launch_direct_one<Acc, KERNEL_LJ>(a, s) : launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s);
+            tile == 5   ? launch_direct_one<Acc, KERNEL_LJ>(a, s)
+            : tile == 6 ? launch_direct4_one<Acc, KERNEL_LJ>(a, s)
+                        : launch_tiled_one<TileL, Acc, KERNEL_LJ>(a, g, s);
             break;
         case KERNEL_LOWFLOP:
-            direct ? launch_direct_one<Acc, KERNEL_LOWFLOP>(a, s)
-                   : launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s);
+            tile == 5   ? launch_direct_one<Acc, KERNEL_LOWFLOP>(a, s)
+            : tile == 6 ? launch_direct4_one<Acc, KERNEL_LOWFLOP>(a, s)
+                        : launch_tiled_one<TileL, Acc, KERNEL_LOWFLOP>(a, g, s);
             break;
         case KERNEL_HIGHFLOP:
-            direct ? launch_direct_one<Acc, KERNEL_HIGHFLOP>(a, s)
-                   : launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s);
+            tile == 5   ? launch_direct_one<Acc, KERNEL_HIGHFLOP>(a, s)
+            : tile == 6 ? launch_direct4_one<Acc, KERNEL_HIGHFLOP>(a, s)
+                        : launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s);
             break;
         default:
             switch (tile) {
@@ -1552,6 +1628,7 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
                 case 2: launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 4: launch_ws_one<Ws8, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
                 case 5: launch_direct_one<Acc, KERNEL_GAUSSIAN>(a, s); break;
+                case 6: launch_direct4_one<Acc, KERNEL_GAUSSIAN>(a, s); break;
                 default: launch_ws_one<Ws4, Acc, KERNEL_GAUSSIAN>(a, g, s); break;
             }
             break;
@@ -1598,7 +1675,8 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
     if ((e = occupancy_of<TileL, Acc>(&per_sm[2])) != cudaSuccess) return e;
     if ((e = ws_occupancy_of<Ws4, Acc>(&per_sm[3])) != cudaSuccess) return e;
     if ((e = ws_occupancy_of<Ws8, Acc>(&per_sm[4])) != cudaSuccess) return e;
-    per_sm[5] = 1;  // the direct kernel launches one thread per target pair
+    per_sm[5] = 1;  // the direct kernels launch one thread per two or four targets
+    per_sm[6] = 1;
     // the comparator kernels run with the 128-thread shape: allow its shared memory
     constexpr int bytes = (int)sizeof(Smem<TileL>);
     if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_LJ>,
@@ -1613,7 +1691,7 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
 
 cudaError_t tiled_occupancy(bool kahan, int* per_sm)
 {
-    static_assert(NUM_TILES == 6, "one occupancy entry per tile shape");
+    static_assert(NUM_TILES == 7, "one occupancy entry per tile shape");
     return kahan ? tiled_occupancy_acc<KahanAcc>(per_sm) : tiled_occupancy_acc<PlainAcc>(per_sm);
 }
 

@@ -249,8 +249,9 @@ cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms,
                                  int* launches);
 // tile: 0, 1, 2 = one CTA per chunk with 32, 64, 128 threads (two targets
 // each); 3, 4 = warp-specialised, 4 or 8 consumer warps; 5 = direct (no
-// staging, sources through L1); per_sm[tile] = resident CTAs.
-constexpr int NUM_TILES = 6;
+// staging, sources through L1, two targets per thread); 6 = direct with
+// four targets per thread; per_sm[tile] = resident CTAs.
+constexpr int NUM_TILES = 7;
 constexpr int DEFAULT_TILE = 5;
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
                                   int tile, cudaStream_t s, int* launches);

@@ -17,10 +17,10 @@ KERNELS = [(B.PI_KERNEL_LJ, oracle.LJ), (B.PI_KERNEL_LOWFLOP, oracle.LOWFLOP),
 
 # (algorithm, tile shape): the staged one-target shape, the direct kernel
 # (two targets per thread, packed), Alg. 1
-PATHS = [(B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 5), (B.PI_ALGO_PPNL, None)]
+PATHS = [(B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 5), (B.PI_ALGO_TILED, 6), (B.PI_ALGO_PPNL, None)]
 
 
-@pytest.mark.parametrize("path", PATHS, ids=["staged", "direct", "ppnl"])
+@pytest.mark.parametrize("path", PATHS, ids=["staged", "direct", "direct4", "ppnl"])
 @pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("precision", [B.PI_PREC_FP32, B.PI_PREC_KAHAN])
 def test_kernel_parity(path, kern, precision):
@@ -55,9 +55,10 @@ def test_dense_cells_exact_windows_bitwise_equal(kern, precision):
     b, r = oracle_run(x, y, z, lo, hi, rc, rc / 2, ok)
     assert b.max_per_cell > 255
     res = {t: run_gpu(x, y, z, lo, hi, rc, rc / 2, precision=precision, kernel=gk, tile=t, binned=False)
-           for t in (2, 5)}
-    for k in ("S", "Vx", "Vy", "Vz", "nbr"):
-        assert np.array_equal(res[2][k].view(np.uint32), res[5][k].view(np.uint32)), k
+           for t in (2, 5, 6)}
+    for t in (5, 6):
+        for k in ("S", "Vx", "Vy", "Vz", "nbr"):
+            assert np.array_equal(res[2][k].view(np.uint32), res[t][k].view(np.uint32)), (t, k)
     # Plain FP32 sums of up to m terms carry the sequential-summation bound
     # (m + 1) 2^-24 of sum|terms| (one rounding per term and per add); with
     # several hundred neighbours of the Lennard-Jones kernel's wide range that
@@ -82,8 +83,8 @@ def test_staged_and_direct_paths_bitwise_equal(kern, precision):
     x, y, z = w.positions()
     _, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h, ok)
     res = {t: run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, precision=precision, kernel=gk, tile=t, binned=False)
-           for t in (0, 2, 3, 5)}
-    for t in (0, 3, 5):
+           for t in (0, 2, 3, 5, 6)}
+    for t in (0, 3, 5, 6):
         for k in ("S", "Vx", "Vy", "Vz", "nbr"):
             assert np.array_equal(res[2][k].view(np.uint32), res[t][k].view(np.uint32)), (t, k)
     check_interaction(res[5], r)

@@ -23,8 +23,8 @@ ALGOS = [B.PI_ALGO_TILED, B.PI_ALGO_PPNL]
 # (algorithm, tile shape): the one-CTA-per-chunk shapes of 32 and 128
 # threads, both warp-specialised shapes, the direct form, and Alg. 1
 VARIANTS = [(B.PI_ALGO_TILED, 0), (B.PI_ALGO_TILED, 2), (B.PI_ALGO_TILED, 3), (B.PI_ALGO_TILED, 4),
-            (B.PI_ALGO_TILED, 5), (B.PI_ALGO_PPNL, None)]
-VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "direct", "ppnl"]
+            (B.PI_ALGO_TILED, 5), (B.PI_ALGO_TILED, 6), (B.PI_ALGO_PPNL, None)]
+VARIANT_IDS = ["tile0", "tile2", "ws4", "ws8", "direct", "direct4", "ppnl"]
 
 
 def _case(w):
@@ -173,7 +173,8 @@ def test_random_configurations(seed):
     x, y, z, lo, hi, rc, h = _random_case(seed)
     b, r = oracle_run(x, y, z, lo, hi, rc, h)
     for algo, tile, prec in ((B.PI_ALGO_TILED, 5, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 5, B.PI_PREC_KAHAN),
-                             (B.PI_ALGO_TILED, 2, B.PI_PREC_FP32), (B.PI_ALGO_PPNL, None, B.PI_PREC_FP32)):
+                             (B.PI_ALGO_TILED, 6, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 2, B.PI_PREC_FP32),
+                             (B.PI_ALGO_PPNL, None, B.PI_PREC_FP32)):
         g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile, precision=prec, n_max=max(len(x), 1))
         check_binning(g, b)
         if len(x):
