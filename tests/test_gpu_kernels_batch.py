@@ -119,9 +119,11 @@ def _systems(seed=5):
     return out
 
 
-@pytest.mark.parametrize("algo", [B.PI_ALGO_TILED, B.PI_ALGO_PPNL])
+@pytest.mark.parametrize("algo", [(B.PI_ALGO_TILED, None), (B.PI_ALGO_TILED, 6), (B.PI_ALGO_TILED, 2),
+                                  (B.PI_ALGO_PPNL, None)], ids=["direct", "direct4", "staged", "ppnl"])
 @pytest.mark.parametrize("order", [B.PI_ORDER_SORTED, B.PI_ORDER_ORIGINAL])
 def test_batch_matches_each_system_alone(algo, order):
+    algo, tile = algo
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
     systems = _systems()
@@ -131,6 +133,8 @@ def test_batch_matches_each_system_alone(algo, order):
                             [n + 5 for n in ns])
     try:
         B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
+        if tile is not None:
+            B.pi_set_option(ctx, B.PI_OPT_TILE, tile)
         S_, C, _ = B.pi_batch_info(ctx)
         assert S_ == len(systems)
         cat = lambda k: torch.from_numpy(np.concatenate([s[k] for s in systems]).astype(np.float32)).to(dev)
