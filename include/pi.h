@@ -97,10 +97,12 @@ enum {
      * direct form with four targets per thread (fewer source reads per
      * evaluation, more evaluations: faster at high occupancy).  With a
      * kernel other than the Gaussian, shapes 0 - 4 all run shape 2's
-     * one-target form.  Default 5.  pi_autotune sets it from measurements.
-     * Results do not depend on it. */
+     * one-target form.  Default PI_TILE_AUTO: shape 5, or 6 when the last
+     * pi_bin put 16 or more particles per cell on average.  pi_autotune
+     * sets a shape from measurements.  Results do not depend on it. */
     PI_OPT_TILE = 6
 };
+enum { PI_TILE_AUTO = -1 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
 enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
 

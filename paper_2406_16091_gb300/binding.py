@@ -34,6 +34,7 @@ PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
 PI_NUM_TILES = 7  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_AUTOTUNE_PPNL = PI_NUM_TILES  # pi_autotune's index of PI_ALGO_PPNL
+PI_TILE_AUTO = -1  # PI_OPT_TILE default: shape by mean occupancy
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1
 PI_KERNEL_LOWFLOP = 2

@@ -76,7 +76,7 @@ struct pi_ctx {
     int algo;
     int precision;
     int kernel;
-    int tile;                       // tile shape of the tiled kernel (0 .. NUM_TILES - 1)
+    int tile;                       // tile shape of the tiled kernel (0 .. NUM_TILES - 1, or PI_TILE_AUTO)
     uint64_t wait_limit_ns;
     int withhold_scan;
 };
@@ -261,7 +261,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->algo = PI_ALGO_TILED;
     c->precision = PI_PREC_FP32;
     c->kernel = PI_KERNEL_GAUSSIAN;
-    c->tile = pi::DEFAULT_TILE;
+    c->tile = PI_TILE_AUTO;
     c->wait_limit_ns = 1000000000ull;
 
     cudaError_t e = cudaGetDevice(&c->device);
@@ -477,7 +477,7 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
             ctx->withhold_scan = (int)value;
             return PI_OK;
         case PI_OPT_TILE:
-            if (value < 0 || value >= pi::NUM_TILES) return PI_ERR_INVALID_ARG;
+            if (value < PI_TILE_AUTO || value >= pi::NUM_TILES) return PI_ERR_INVALID_ARG;
             ctx->tile = (int)value;
             return PI_OK;
         case PI_OPT_KERNEL:
@@ -616,8 +616,12 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     if (ctx->algo == PI_ALGO_PPNL) {
         e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, st, &launched);
     } else {
-        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0],
-                                      ctx->tile, st, &launched);
+        // PI_TILE_AUTO: two targets per thread, four from 16 particles per
+        // cell on average (where the four-target shape is measured faster)
+        const int tile = ctx->tile >= 0 ? ctx->tile
+                                        : (ctx->n >= 16 * ctx->C ? pi::HIGH_OCCUPANCY_TILE : pi::DEFAULT_TILE);
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], tile, st,
+                                      &launched);
         ctx->tiled_seq += 1;
     }
     ctx->launches += (uint64_t)launched;
