@@ -344,45 +344,58 @@ def run_ours(args):
             blocking = {"value": replicas.job_rate(e2e_pairs_all, args.e2e_steps, t_e2e), "unit": UNIT,
                         "ms_per_step": 1e3 * t_e2e / args.e2e_steps, "steps": args.e2e_steps,
                         "api": "pi_run_host (pinned host buffers), one blocking call per step"}
-            # (2) pipelined: steps alternate between two contexts on two streams
-            # with pi_submit_host, so one step's copies overlap the other's kernels
-            ctx2 = B.pi_create(w.lo, w.hi, w.rc, n)
-            B.pi_set_option(ctx2, B.PI_OPT_ALGO, B.PI_ALGO_TILED if args.algo == "tiled" else B.PI_ALGO_PPNL)
-            B.pi_set_option(ctx2, B.PI_OPT_PRECISION,
-                            B.PI_PREC_FP32 if args.precision == "fp32" else B.PI_PREC_KAHAN)
-            if args.algo == "tiled":
-                B.pi_set_option(ctx2, B.PI_OPT_TILE, tile)
-            ctxs = [ctx, ctx2]
-            streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-            houts = [hout, [torch.empty(n).pin_memory() for _ in range(4)]]
-            hnbs = [hnb, torch.empty(n, dtype=torch.int32).pin_memory()]
+            # (2) pipelined: steps rotate over PIPE contexts on their own streams
+            # through pi_submit_host_strided (positions in one pinned block, one
+            # copy in; outputs into one pinned block, one copy out), so one
+            # step's copies and latency-bound binning overlap the others'
+            # kernels.  Every step copies its positions in and its outputs out.
+            PIPE = 4
+            d = (n + 3) // 4 * 4
+            hin = torch.empty(3 * d).pin_memory()
+            for k, a_ in enumerate((x, y, z)):
+                hin[k * d:k * d + n] = torch.from_numpy(a_)
+            ib = hin.data_ptr()
+            ctxs = [ctx] + [B.pi_create(w.lo, w.hi, w.rc, n) for _ in range(PIPE - 1)]
+            for c in ctxs[1:]:
+                B.pi_set_option(c, B.PI_OPT_ALGO, B.PI_ALGO_TILED if args.algo == "tiled" else B.PI_ALGO_PPNL)
+                B.pi_set_option(c, B.PI_OPT_PRECISION,
+                                B.PI_PREC_FP32 if args.precision == "fp32" else B.PI_PREC_KAHAN)
+                if args.algo == "tiled":
+                    B.pi_set_option(c, B.PI_OPT_TILE, tile)
+            streams = [torch.cuda.Stream(dev) for _ in range(PIPE)]
+            houts = [torch.empty(5 * d).pin_memory() for _ in range(PIPE)]
 
             def submit(k):
-                c = k & 1
-                B.pi_submit_host(ctxs[c], w.lo, w.hi, w.rc, hx, hy, hz, n, w.h, *houts[c], hnbs[c],
-                                 B.PI_ORDER_SORTED, streams[c])
+                c = k % PIPE
+                ob = houts[c].data_ptr()
+                B.pi_submit_host_strided(ctxs[c], w.lo, w.hi, w.rc, ib, ib + 4 * d, ib + 8 * d, d, n, w.h,
+                                         *(ob + 4 * d * j for j in range(5)), d, B.PI_ORDER_SORTED,
+                                         streams[c])
 
-            for k in range(4):
+            for k in range(2 * PIPE):
                 submit(k)
             torch.cuda.synchronize()
-            K2 = max(2, args.e2e_steps)
+            K2 = max(PIPE, args.e2e_steps)
             t0 = time.perf_counter()
             for k in range(K2):
                 submit(k)
             torch.cuda.synchronize()
             t_pipe = time.perf_counter() - t0
-            for c in range(2):
+            for c in range(PIPE):
                 B.pi_sync_status(ctxs[c], streams[c])
-            pipe_pairs = int(hnbs[1].numpy().astype(np.int64).sum())
-            assert pipe_pairs == e2e_pairs, "the two contexts disagree on the pair count"
+            nbr_last = houts[(K2 - 1) % PIPE][4 * d:4 * d + n].view(torch.int32)
+            pipe_pairs = int(nbr_last.numpy().astype(np.int64).sum())
+            assert pipe_pairs == e2e_pairs, "the contexts disagree on the pair count"
             t_pipe, pipe_pairs_all = replicas.aggregate(t_pipe, pipe_pairs, dev)
             e2e = {"value": replicas.job_rate(pipe_pairs_all, K2, t_pipe), "unit": UNIT,
                    "h2d_bytes_per_step": 3 * 4 * n, "d2h_bytes_per_step": 5 * 4 * n,
-                   "ms_per_step": 1e3 * t_pipe / K2, "steps": K2,
-                   "api": "pi_submit_host (pinned host buffers), steps alternating between two contexts "
-                          "on two streams; every step copies its positions in and its outputs out",
+                   "ms_per_step": 1e3 * t_pipe / K2, "steps": K2, "steps_in_flight": PIPE,
+                   "api": f"pi_submit_host_strided (pinned host blocks), steps rotating over {PIPE} "
+                          "contexts on their own streams; every step copies its positions in and its "
+                          "outputs out",
                    "blocking": blocking}
-            B.pi_destroy(ctx2)
+            for c in ctxs[1:]:
+                B.pi_destroy(c)
     except Exception as exc:  # the line is still printed
         print(f"bench: end-to-end measurement failed: {exc!r}", file=sys.stderr)
         e2e = {"error": repr(exc)}
