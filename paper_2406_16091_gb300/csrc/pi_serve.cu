@@ -302,7 +302,12 @@ pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* 
                     jobs[k].t_start = now();
                     jobs[k].slot_capacity = s->cap;
                     s->job = k;
-                    if ((err = start(srv, s, jobs[k])) != PI_OK) break;
+                    if ((err = start(srv, s, jobs[k])) != PI_OK) {
+                        // the slot stays usable for later runs; the run ends
+                        s->job = -1;
+                        srv->free[(size_t)b].push_back(s);
+                        break;
+                    }
                     busy.push_back(s);
                 }
             }
@@ -324,6 +329,11 @@ pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* 
             const pi_status st = pi_sync_status(s->ctx, s->stream, nullptr);
             if (err == PI_OK && st != PI_OK) err = st;
         }
+    // after an error, slots still marked busy are drained: free them again
+    for (Slot* s : busy) {
+        s->job = -1;
+        srv->free[(size_t)s->bucket].push_back(s);
+    }
     return err;
 }
 
