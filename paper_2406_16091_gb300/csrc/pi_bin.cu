@@ -29,6 +29,7 @@ constexpr unsigned FULL = 0xffffffffu;
 template <int NB>
 __global__ void k_zero(ZeroArgs<NB> z)
 {
+    pdl_trigger();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     uint4* p4 = reinterpret_cast<uint4*>(z.p);
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                                               Ctrl* __restrict__ ctrl, int vec)
 {
     constexpr int HP = HIST_PER_LANE, HV = HP / 4;
+    pdl_trigger();
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t groups = (n + HP - 1u) / HP;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -87,6 +89,9 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
                 pz[j] = valid[j] ? z[i] : 0.f;
             }
         }
+        // the positions are the caller's input, written before k_zero started;
+        // the particle bases and the counts are k_zero's
+        pdl_wait();
         int s = (sy.S == 1 || grp >= groups) ? 0 : find_system(sy.pbase, sy.S, i0);
         // all cells, then all atomics: the atomics of one lane are in flight
         // together.  Particles come in no spatial order, so a warp almost
@@ -168,6 +173,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
     __shared__ uint32_t s_prefix;
 
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl->ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
@@ -324,6 +331,8 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
                                                  Rec* __restrict__ rec, Ctrl* __restrict__ ctrl,
                                                  int vec)
 {
+    pdl_trigger();
+    pdl_wait();
     if (load_error(ctrl)) return;
     bool bad = false;
     const uint32_t groups = (n + 3u) / 4u;
@@ -409,6 +418,8 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
                                                    uint2* __restrict__ xbins,
                                                    Ctrl* __restrict__ ctrl)
 {
+    pdl_trigger();
+    pdl_wait();
     if (load_error(ctrl)) return;
     bool bad = false;
     const uint32_t C = __ldg(sy.cbase + sy.S);
@@ -523,9 +534,8 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + HIST_PER_LANE - 1) / HIST_PER_LANE;
     // exactly the resident CTAs (grid-stride loop): no partial last wave
-    k_hist<<<grid_for(groups, 256, num_sms, resident_per_sm(k_hist, 0)), 256, 0, s>>>(x, y, z, n, sy, counts, cell, rank,
-                                                             ctrl, vec);
-    return cudaGetLastError();
+    return launch_dependent(k_hist, dim3(grid_for(groups, 256, num_sms, resident_per_sm(k_hist, 0))), dim3(256), 0, s,
+                            x, y, z, n, sy, counts, cell, rank, ctrl, vec);
 }
 
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
@@ -533,9 +543,8 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         uint64_t wait_limit_ns, int withhold_first, cudaStream_t s)
 {
     const uint64_t tiles = ((uint64_t)C + 1 + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, C, offsets, status, ctrl, epoch,
-                                                    wait_limit_ns, withhold_first);
-    return cudaGetLastError();
+    return launch_dependent(k_scan, dim3((unsigned)tiles), dim3(SCAN_THREADS), 0, s, counts, C, offsets, status,
+                            ctrl, epoch, wait_limit_ns, withhold_first);
 }
 
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
@@ -544,18 +553,16 @@ cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const flo
 {
     const int vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z)) & 15u) == 0;
     const uint64_t groups = ((uint64_t)n + 3) / 4;
-    k_scatter<<<grid_for(groups, 256, num_sms, resident_per_sm(k_scatter, 1)), 256, 0, s>>>(cell, rank, x, y, z, n, sy, offsets,
-                                                                                         rec, ctrl, vec);
-    return cudaGetLastError();
+    return launch_dependent(k_scatter, dim3(grid_for(groups, 256, num_sms, resident_per_sm(k_scatter, 1))), dim3(256),
+                            0, s, cell, rank, x, y, z, n, sy, offsets, rec, ctrl, vec);
 }
 
 cudaError_t launch_stabilise(const Rec* rec, uint32_t n, const Systems& sy, const uint32_t* offsets,
                              uint32_t* perm, float* sx, float* sy_out, float* sz, float4* P,
                              uint2* xbins, Ctrl* ctrl, int num_sms, cudaStream_t s)
 {
-    k_stabilise<<<grid_for(n, 256, num_sms, resident_per_sm(k_stabilise, 2)), 256, 0, s>>>(rec, n, sy, offsets, perm, sx, sy_out, sz,
-                                                             P, xbins, ctrl);
-    return cudaGetLastError();
+    return launch_dependent(k_stabilise, dim3(grid_for(n, 256, num_sms, resident_per_sm(k_stabilise, 2))), dim3(256),
+                            0, s, rec, n, sy, offsets, perm, sx, sy_out, sz, P, xbins, ctrl);
 }
 
 namespace {

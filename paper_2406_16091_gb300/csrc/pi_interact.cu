@@ -1474,6 +1474,8 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL
     k_interact_direct(InteractArgs a)
 {
     __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
+    pdl_trigger();
+    pdl_wait();  // the binning (or the previous interaction) has completed
     // keep the work counters of the tiled launches in step (see k_interact_tiled)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     // both control words in flight together
@@ -1509,6 +1511,8 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     k_interact_direct4(InteractArgs a)
 {
     __shared__ uint32_t win[20][DIRECT_THREADS];  // 9 windows (lo, hi) + one spare read after the last
+    pdl_trigger();
+    pdl_wait();  // the binning (or the previous interaction) has completed
     // keep the work counters of the tiled launches in step (see k_interact_tiled)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     const uint32_t err = load_error(a.ctrl);
@@ -1558,16 +1562,20 @@ template <class Acc, int KERNEL>
 void launch_direct4_one(const InteractArgs& a, cudaStream_t s)
 {
     const uint64_t quads = ((uint64_t)a.np + 3) / 4;
-    k_interact_direct4<Acc, KERNEL>
-        <<<(unsigned)((quads + DIRECT_THREADS - 1) / DIRECT_THREADS), DIRECT_THREADS, 0, s>>>(a);
+    // an error is left for cudaGetLastError
+    (void)launch_dependent(k_interact_direct4<Acc, KERNEL>,
+                           dim3((unsigned)((quads + DIRECT_THREADS - 1) / DIRECT_THREADS)), dim3(DIRECT_THREADS), 0,
+                           s, a);
 }
 
 template <class Acc, int KERNEL>
 void launch_direct_one(const InteractArgs& a, cudaStream_t s)
 {
     const uint64_t pairs = ((uint64_t)a.np + 1) / 2;
-    k_interact_direct<Acc, KERNEL>
-        <<<(unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS), DIRECT_THREADS, 0, s>>>(a);
+    // an error is left for cudaGetLastError
+    (void)launch_dependent(k_interact_direct<Acc, KERNEL>,
+                           dim3((unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS)), dim3(DIRECT_THREADS), 0,
+                           s, a);
 }
 
 template <class Acc>

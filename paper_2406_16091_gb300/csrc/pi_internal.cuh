@@ -154,6 +154,32 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Programmatic dependent launch.  A kernel started by launch_dependent may
+// begin while the kernel before it in the stream is still running (once
+// every block of that kernel has called pdl_trigger or exited); pdl_wait
+// then blocks until that kernel has completed and its writes are visible.
+// Whatever a kernel reads or writes of the step's state comes after its
+// pdl_wait.  For a kernel launched the ordinary way both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dependent(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // One particle in provisional (unstable) slot order: position, input index,
 // cell, and its x-sub-bin as a thermometer (byte b - 1 is 1 when the
 // sub-bin is < b, b = 1 .. XSUB - 1; t_lo holds bytes 0..3, t_hi bytes
