@@ -44,7 +44,9 @@
 //   k_interact_ws      the same chunks with a producer warp that stages them
 //                      for consumer warps (warp specialisation).
 // All of them sum each target's terms in the order of its own windows, so
-// their outputs are bitwise equal.
+// their outputs are bitwise equal.  Every one is a programmatic dependent
+// launch: it may start while the binning's last kernel (or the previous
+// interaction) drains, and waits for it before reading anything of the step.
 #include <type_traits>
 
 #include "pi_internal.cuh"
@@ -179,6 +181,8 @@ __device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot,
 template <class Acc, int KERNEL>
 __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
 {
+    pdl_trigger();
+    pdl_wait();
     if (load_error(a.ctrl)) return;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n) return;
@@ -864,6 +868,8 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
 
+    pdl_trigger();
+    pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -1194,6 +1200,8 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WsSmem<T>& sm = *reinterpret_cast<WsSmem<T>*>(smem_raw);
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    pdl_trigger();
+    pdl_wait();
     if (tid == 0) {
         if (blockIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
         sm.failed = load_error(a.ctrl) != 0u;
@@ -1581,26 +1589,27 @@ void launch_direct_one(const InteractArgs& a, cudaStream_t s)
 template <class Acc>
 cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((a.n + 127) / 128);
+    const dim3 blocks((unsigned)((a.n + 127) / 128)), threads(128);
     switch (a.kernel) {
-        case KERNEL_LJ: k_interact_ppnl<Acc, KERNEL_LJ><<<blocks, 128, 0, s>>>(a); break;
-        case KERNEL_LOWFLOP: k_interact_ppnl<Acc, KERNEL_LOWFLOP><<<blocks, 128, 0, s>>>(a); break;
-        case KERNEL_HIGHFLOP: k_interact_ppnl<Acc, KERNEL_HIGHFLOP><<<blocks, 128, 0, s>>>(a); break;
-        default: k_interact_ppnl<Acc, KERNEL_GAUSSIAN><<<blocks, 128, 0, s>>>(a); break;
+        case KERNEL_LJ: return launch_dependent(k_interact_ppnl<Acc, KERNEL_LJ>, blocks, threads, 0, s, a);
+        case KERNEL_LOWFLOP: return launch_dependent(k_interact_ppnl<Acc, KERNEL_LOWFLOP>, blocks, threads, 0, s, a);
+        case KERNEL_HIGHFLOP: return launch_dependent(k_interact_ppnl<Acc, KERNEL_HIGHFLOP>, blocks, threads, 0, s, a);
+        default: return launch_dependent(k_interact_ppnl<Acc, KERNEL_GAUSSIAN>, blocks, threads, 0, s, a);
     }
-    return cudaGetLastError();
 }
 
 template <class T, class Acc, int KERNEL>
 void launch_tiled_one(const InteractArgs& a, unsigned grid, cudaStream_t s)
 {
-    k_interact_tiled<T, Acc, KERNEL><<<grid, T::NT, sizeof(Smem<T>), s>>>(a);
+    // an error is left for cudaGetLastError
+    (void)launch_dependent(k_interact_tiled<T, Acc, KERNEL>, dim3(grid), dim3(T::NT), sizeof(Smem<T>), s, a);
 }
 
 template <class T, class Acc, int KERNEL>
 void launch_ws_one(const InteractArgs& a, unsigned grid, cudaStream_t s)
 {
-    k_interact_ws<T, Acc, KERNEL><<<grid, T::THREADS, sizeof(WsSmem<T>), s>>>(a);
+    // an error is left for cudaGetLastError
+    (void)launch_dependent(k_interact_ws<T, Acc, KERNEL>, dim3(grid), dim3(T::THREADS), sizeof(WsSmem<T>), s, a);
 }
 
 template <class Acc>
