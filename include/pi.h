@@ -97,9 +97,11 @@ enum {
      * direct form with four targets per thread (fewer source reads per
      * evaluation, more evaluations: faster at high occupancy).  With a
      * kernel other than the Gaussian, shapes 0 - 4 all run shape 2's
-     * one-target form.  Default PI_TILE_AUTO: shape 5, or 6 when the last
-     * pi_bin put 16 or more particles per cell on average.  pi_autotune
-     * sets a shape from measurements.  Results do not depend on it. */
+     * one-target form.  Default PI_TILE_AUTO: shape 6 for the plain
+     * (PI_PREC_FP32) Gaussian and low-FLOP kernels when the last pi_bin put
+     * 8 or more particles per cell on average, shape 5 otherwise.
+     * pi_autotune sets a shape from measurements.  Results do not depend on
+     * it. */
     PI_OPT_TILE = 6
 };
 enum { PI_TILE_AUTO = -1 };

@@ -616,10 +616,15 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     if (ctx->algo == PI_ALGO_PPNL) {
         e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, st, &launched);
     } else {
-        // PI_TILE_AUTO: two targets per thread, four from 16 particles per
-        // cell on average (where the four-target shape is measured faster)
+        // PI_TILE_AUTO: four targets per thread for the plain Gaussian and
+        // low-FLOP sums from 8 particles per cell on average (measured
+        // faster from there on, slower below), two otherwise: the
+        // four-target Lennard-Jones and 168-FLOP forms (measured slower at 8
+        // per cell) and the compensated sums keep all their registers and
+        // run fewer warps
+        const bool packed = !kahan && (ctx->kernel == PI_KERNEL_GAUSSIAN || ctx->kernel == PI_KERNEL_LOWFLOP);
         const int tile = ctx->tile >= 0 ? ctx->tile
-                                        : (ctx->n >= 16 * ctx->C ? pi::HIGH_OCCUPANCY_TILE : pi::DEFAULT_TILE);
+                         : (packed && ctx->n >= 8 * ctx->C ? pi::HIGH_OCCUPANCY_TILE : pi::DEFAULT_TILE);
         e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], tile, st,
                                       &launched);
         ctx->tiled_seq += 1;

@@ -1271,34 +1271,53 @@ __device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_
     return start + ((word >> (8 * ((sub - 1) & 3))) & 255u);
 }
 
-// The 9 x-windows of one target as ranges of P indices (see target_windows;
-// here the lookups read global memory), merged into the union windows
-// [ulo, uhi) of a group of targets: a non-empty window widens its row's
-// union, an empty one leaves it as it is.
-template <bool DENSE>
-__device__ __forceinline__ void target_windows_direct(const InteractArgs& a, const SysDesc& d, const float4& t,
-                                                      int cx, int cy, int cz, uint32_t (&ulo)[9],
-                                                      uint32_t (&uhi)[9])
+// The x-windows of a group of G targets of one X-row (see target_windows;
+// here the lookups read global memory), one range [ulo, uhi) of P indices
+// per neighbour row, left unchanged for a row where the range is empty.
+// The union is taken in x before the lookups: the smallest x - w_r and the
+// largest x + w_r over the targets that have the row, clamped to the cells
+// next to the group's, give one sub-bin range and two lookups per row
+// instead of two per target.  Sub-bins and their starts are monotone in x,
+// so the range holds every target's own window; what else it may hold (the
+// sub-bins between two disjoint windows) is outside every target's cutoff
+// and adds exact zeros.
+template <bool DENSE, int G>
+__device__ __forceinline__ void group_windows_direct(const InteractArgs& a, const SysDesc& d, const float4 (&t)[G],
+                                                     const int (&cx)[G], int cy, int cz, uint32_t (&ulo)[9],
+                                                     uint32_t (&uhi)[9])
 {
-    const Faces f = faces_of(d, t.y, t.z, cy, cz);
+    Faces f[G];
+    int cmin = cx[0], cmax = cx[0];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        f[k] = faces_of(d, t[k].y, t[k].z, cy, cz);
+        cmin = min(cmin, cx[k]);
+        cmax = max(cmax, cx[k]);
+    }
     const float rcm2 = d.rc2 * 1.00002f;
     const float xlo = d.g.lo[0], slack = d.slack, invs = d.g.inv_w[0] * (float)XSUB;
     const int nx = d.g.n[0], ny = d.g.n[1], nz = d.g.n[2];
-    const int lo = XSUB * max(cx - 1, 0);
-    const int hi = XSUB * (min(cx + 1, nx - 1) + 1) - 1;
+    const int lo = XSUB * max(cmin - 1, 0);
+    const int hi = XSUB * (min(cmax + 1, nx - 1) + 1) - 1;
 #pragma unroll
     for (int rr = 0; rr < 9; ++rr) {
         const int dy = rr % 3 - 1, dz = rr / 3 - 1;
         const int by = cy + dy, bz = cz + dz;
-        const float ey = dy < 0 ? f.y_lo : (dy > 0 ? f.y_hi : 0.f);
-        const float ez = dz < 0 ? f.z_lo : (dz > 0 ? f.z_hi : 0.f);
-        const float tw = rcm2 - fmaf(ey, ey, ez * ez);
-        if (by < 0 || by >= ny || bz < 0 || bz >= nz || !(tw > 0.f)) continue;
-        const float tt = fmaxf(tw, 1e-30f);
-        const float w = tt * rsqrtf(tt) + slack;
+        if (by < 0 || by >= ny || bz < 0 || bz >= nz) continue;
+        float xl = INFINITY, xu = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const float ey = dy < 0 ? f[k].y_lo : (dy > 0 ? f[k].y_hi : 0.f);
+            const float ez = dz < 0 ? f[k].z_lo : (dz > 0 ? f[k].z_hi : 0.f);
+            const float tw = rcm2 - fmaf(ey, ey, ez * ez);
+            const float tt = fmaxf(tw, 1e-30f);
+            const float w = tt * rsqrtf(tt) + slack;
+            xl = tw > 0.f ? fminf(xl, t[k].x - w) : xl;
+            xu = tw > 0.f ? fmaxf(xu, t[k].x + w) : xu;
+        }
+        if (!(xl <= xu)) continue;  // no target of the group reaches the row
         const uint32_t row = (uint32_t)by + (uint32_t)ny * (uint32_t)bz;
         const uint32_t rb = d.cell_base + (uint32_t)nx * row, pad = ROW_PADS * (d.row_base + row);
-        const float xl = t.x - w, xu = t.x + w;
         const int b0 = sub_bin(xl, xlo, invs, 0, lo, hi);
         const int b1 = sub_bin(xu, xlo, invs, 0, lo, hi) + 1;
         bool dl = false, du = false;
@@ -1317,8 +1336,8 @@ __device__ __forceinline__ void target_windows_direct(const InteractArgs& a, con
             je = x_bound(a.P, __ldg(a.offsets + rb + k) + pad, __ldg(a.offsets + rb + k + 1) + pad, xu, true);
         }
         if (je > j) {
-            ulo[rr] = min(ulo[rr], j);
-            uhi[rr] = max(uhi[rr], je);
+            ulo[rr] = j;
+            uhi[rr] = je;
         }
     }
 }
@@ -1348,8 +1367,7 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
             ulo[rr] = 0xffffffffu;
             uhi[rr] = 0u;
         }
-#pragma unroll
-        for (int k = 0; k < G; ++k) target_windows_direct<DENSE>(a, d, t[k], cx[k], cy, cz, ulo, uhi);
+        group_windows_direct<DENSE, G>(a, d, t, cx, cy, cz, ulo, uhi);
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr)
             if (uhi[rr] > ulo[rr]) {

@@ -278,8 +278,8 @@ cudaError_t launch_interact_ppnl(const InteractArgs& a, bool kahan, int num_sms,
 // staging, sources through L1, two targets per thread); 6 = direct with
 // four targets per thread; per_sm[tile] = resident CTAs.
 constexpr int NUM_TILES = 7;
-constexpr int DEFAULT_TILE = 5;         // PI_TILE_AUTO below 16 particles per cell on average
-constexpr int HIGH_OCCUPANCY_TILE = 6;  // PI_TILE_AUTO from 16 per cell
+constexpr int DEFAULT_TILE = 5;         // PI_TILE_AUTO below 8 particles per cell, or not the packed sums
+constexpr int HIGH_OCCUPANCY_TILE = 6;  // PI_TILE_AUTO: plain Gaussian / low-FLOP sums from 8 per cell
 cudaError_t launch_interact_tiled(const InteractArgs& a, bool kahan, int num_sms, const int* per_sm,
                                   int tile, cudaStream_t s, int* launches);
 // Resident CTAs per SM of each tile shape of the tiled kernel (per_sm[NUM_TILES]).
