@@ -99,7 +99,8 @@ enum {
      * kernel other than the Gaussian, shapes 0 - 4 all run shape 2's
      * one-target form.  Default PI_TILE_AUTO: shape 6 for the plain
      * (PI_PREC_FP32) Gaussian and low-FLOP kernels when the last pi_bin put
-     * 8 or more particles per cell on average, shape 5 otherwise.
+     * 8 or more particles per cell on average and enough particles for one
+     * full wave of shape 6 (4 x 640 per SM), shape 5 otherwise.
      * pi_autotune sets a shape from measurements.  Results do not depend on
      * it. */
     PI_OPT_TILE = 6

@@ -618,13 +618,19 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     } else {
         // PI_TILE_AUTO: four targets per thread for the plain Gaussian and
         // low-FLOP sums from 8 particles per cell on average (measured
-        // faster from there on, slower below), two otherwise: the
+        // faster from there on, slower below) when the four-target grid
+        // fills at least one wave of the GPU (5 CTAs of 128 threads per SM);
+        // two otherwise: a smaller grid leaves SMs idle and each thread twice
+        // the work (measured 2x slower at 32,768 particles), and the
         // four-target Lennard-Jones and 168-FLOP forms (measured slower at 8
         // per cell) and the compensated sums keep all their registers and
         // run fewer warps
+        constexpr int64_t QUAD_THREADS_PER_SM = 5 * 128;
         const bool packed = !kahan && (ctx->kernel == PI_KERNEL_GAUSSIAN || ctx->kernel == PI_KERNEL_LOWFLOP);
+        const bool full_wave = ctx->n / 4 >= (int64_t)ctx->num_sms * QUAD_THREADS_PER_SM;
         const int tile = ctx->tile >= 0 ? ctx->tile
-                         : (packed && ctx->n >= 8 * ctx->C ? pi::HIGH_OCCUPANCY_TILE : pi::DEFAULT_TILE);
+                         : (packed && full_wave && ctx->n >= 8 * ctx->C ? pi::HIGH_OCCUPANCY_TILE
+                                                                         : pi::DEFAULT_TILE);
         e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], tile, st,
                                       &launched);
         ctx->tiled_seq += 1;
