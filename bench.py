@@ -61,7 +61,26 @@ def parse():
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
     p.add_argument("--max-slots", type=int, default=8, help="serving study: slots per capacity bucket")
+    p.add_argument("--no-extras", action="store_true",
+                   help="leave out the batched, serving and per-configuration records of the line")
+    p.add_argument("--serving-jobs", type=int, default=1000,
+                   help="jobs of the line's serving record (Poisson arrivals at 80 %% of capacity)")
     return p.parse_args()
+
+
+def binning_bytes(n, C):
+    """Algorithmic bytes of binning a1-a4: per particle 12 read + 4 cell +
+    4 rank written (a1/a2), 8 read (cell, rank) + 12 read (x, y, z) + 4 perm
+    + 12 sorted positions written (a4); per cell 4 (count clear) + 4 read +
+    4 written (a3)."""
+    return 48 * n + 12 * C
+
+
+def binning_bytes_with_p(n, C):
+    """binning_bytes plus what this library's binning also writes for the
+    interaction: the 16-byte x-ordered P record per particle, and its 8-byte
+    per-cell sub-bin word (reported beside the algorithmic figure)."""
+    return 48 * n + 16 * n + 12 * C + 8 * C
 
 
 def measured_peaks():
@@ -447,16 +466,36 @@ def run_ours(args):
     if clocks:
         roofline["frac_at_median_clock"] = achieved / (alu_peak * clocks["sm_mhz"] / sm_max)
     C = w.cells_per_axis() ** 3
-    bin_bytes = 72 * n + 12 * C
+    bin_bytes = binning_bytes(n, C)
     mean_bin = statistics.fmean(t_bin)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bin_traffic = recorded_traffic("binning", source_hash([os.path.join(src, "pi_bin.cu"),
                                                           os.path.join(src, "pi_internal.cuh")]))
+    bin_dram = bin_traffic["dram_bytes_per_launch"] if bin_traffic else None
     binning = {"bound": "hbm", "achieved": bin_bytes / mean_bin / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": bin_bytes / mean_bin / 1e9 / hbm_peak,
-               "algorithmic_bytes": bin_bytes, "mean_us": 1e6 * mean_bin,
-               "traffic": bin_traffic["dram_bytes_per_launch"] if bin_traffic else None,
+               "algorithmic_bytes": bin_bytes,
+               "algorithmic_bytes_formula": "48 N + 12 C (a1-a4 per particle and per cell)",
+               "bytes_with_P_record": binning_bytes_with_p(n, C), "mean_us": 1e6 * mean_bin,
+               "traffic": bin_dram,
+               "traffic_over_algorithmic": bin_dram / bin_bytes if bin_dram else None,
                "kernels": ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"]}
+
+    # the other parts of the metric and the other configurations, measured
+    # after the timed region: batched systems, served jobs, per configuration
+    extras = {}
+    if not args.no_extras and ws == 1:
+        for key, fn in (("per_config", lambda: per_config_records(torch, B, args.flush_mb, alu_peak)),
+                        ("batched", lambda: batched_record(torch, B, args.flush_mb, 10, 5)),
+                        ("serving", lambda: serving_record(torch, B, args.serving_jobs, args.max_slots,
+                                                           loads=(0.8,)))):
+            t0 = time.perf_counter()
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # the line is still printed
+                print(f"bench: {key} record failed: {exc!r}", file=sys.stderr)
+                extras[key] = {"error": repr(exc)}
+            extras[key]["wall_s"] = time.perf_counter() - t0
 
     cpu = None
     try:
@@ -511,6 +550,7 @@ def run_ours(args):
         "roofline": roofline, "roofline_binning": binning, "peak_source": peak_kind,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "timed_region_wall_s": wall,
+        **extras,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -605,11 +645,10 @@ def study_precision(args):
     print(json.dumps(res), flush=True)
 
 
-def study_batched(args):
+def batched_record(torch, B, flush_mb, reps_batch=20, reps_plain=10):
     """The batched workload: 256 uneven systems in one context (one launch per
     kernel, graph-captured, tile shape autotuned) against one context and one
     launch set per system, at the same accuracy (bitwise-equal outputs)."""
-    torch, B = _torch_setup()
     dev = torch.device("cuda", 0)
     systems = W.batched_systems()
     ns = [sy.n for sy in systems]
@@ -619,7 +658,7 @@ def study_batched(args):
     tx, ty, tz = cat(0), cat(1), cat(2)
     hs = [sy.h for sy in systems]
     s = torch.cuda.current_stream()
-    flush = torch.empty(args.flush_mb * (1 << 20) // 4, device=dev)
+    flush = torch.empty(flush_mb * (1 << 20) // 4, device=dev)
     # --- batched
     ctx = B.pi_batch_create([(sy.lo, sy.hi) for sy in systems], [sy.rc for sy in systems], ns)
     out = [torch.empty(N, device=dev) for _ in range(4)]
@@ -634,7 +673,7 @@ def study_batched(args):
     for _ in range(3):
         step_batch()
     pairs = int(nb.to(torch.int64).sum().item())
-    ms_batch, _ = _time_events(torch, step_batch, 20, flush)
+    ms_batch, _ = _time_events(torch, step_batch, reps_batch, flush)
     g = torch.cuda.CUDAGraph()
     cs = torch.cuda.Stream()
     cs.wait_stream(s)
@@ -646,7 +685,7 @@ def study_batched(args):
         with torch.cuda.graph(g, stream=cs):
             step_batch_cs()
     s.wait_stream(cs)
-    ms_graph, _ = _time_events(torch, g.replay, 20, flush)
+    ms_graph, _ = _time_events(torch, g.replay, reps_batch, flush)
     B.pi_sync_status(ctx, s)
     batch_out = [o.clone() for o in out] + [nb.clone()]
     # --- one context per system, launched one after the other
@@ -661,7 +700,7 @@ def study_batched(args):
 
     for _ in range(3):
         step_plain()
-    ms_plain, _ = _time_events(torch, step_plain, 10, flush)
+    ms_plain, _ = _time_events(torch, step_plain, reps_plain, flush)
     g2 = torch.cuda.CUDAGraph()
     with torch.cuda.stream(cs):
         step_plain(cs)
@@ -669,7 +708,7 @@ def study_batched(args):
         with torch.cuda.graph(g2, stream=cs):
             step_plain(cs)
     s.wait_stream(cs)
-    ms_plain_graph, _ = _time_events(torch, g2.replay, 10, flush)
+    ms_plain_graph, _ = _time_events(torch, g2.replay, reps_plain, flush)
     torch.cuda.synchronize()
     same = all(torch.equal(a.view(torch.int32), b.view(torch.int32))
                for a, b in zip(batch_out, [o for o in out] + [nb]))
@@ -686,17 +725,23 @@ def study_batched(args):
            "speedup_vs_plain_graph": ms_plain_graph / ms_graph,
            "outputs_bitwise_equal": bool(same),
            "l2": "flushed before every timed step"}
-    print(json.dumps(res), flush=True)
+    return res
 
 
-def study_serving(args):
+def study_batched(args):
+    torch, B = _torch_setup()
+    print(json.dumps(batched_record(torch, B, args.flush_mb)), flush=True)
+
+
+def serving_record(torch, B, n_jobs, max_slots, loads=(0.5, 0.8, 0.95)):
     """The serving workload: jobs of N log-uniform in [1k, 1M], occupancy in
     {2, 4, 8, 16}, half uniform and half clustered.  First the capacity (all
-    jobs queued at once), then Poisson arrivals at 50 %, 80 % and 95 % of it."""
-    torch, B = _torch_setup()
+    jobs queued at once), then the same jobs one after another as blocking
+    pi_run_host calls (the plain per-system loop), then Poisson arrivals at
+    the given fractions of the capacity."""
     from paper_2406_16091_gb300.serving import Server, make_job
 
-    specs = W.serving_jobs(args.jobs)
+    specs = W.serving_jobs(n_jobs)
     t0 = time.perf_counter()
     pool = {k: [torch.from_numpy(a).pin_memory() for a in v] for k, v in W.serving_pool().items()}
     jobs = []
@@ -705,7 +750,7 @@ def study_serving(args):
         # results of every 500th job are kept; the others land in slot buffers
         jobs.append(make_job(k, x, y, z, sp.lo, sp.hi, sp.rc, sp.h, outputs=k % 500 == 0))
     t_gen = time.perf_counter() - t0
-    srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=args.max_slots)
+    srv = Server(buckets=((65536, 4), (262144, 4), (1048576, 2)), max_slots_per_bucket=max_slots)
     res = {"study": "serving", "jobs": len(jobs), "particles": sum(j.n for j in jobs),
            "generation_s": t_gen}
     try:
@@ -739,7 +784,7 @@ def study_serving(args):
                                    "makespan_s": t_plain}
         res["speedup_vs_plain"] = cap["jobs_per_s"] / res["plain_sequential"]["jobs_per_s"]
         rng = np.random.default_rng(1005)
-        for frac in (0.5, 0.8, 0.95):
+        for frac in loads:
             rate = frac * cap["jobs_per_s"]
             t = np.cumsum(rng.exponential(1.0 / rate, len(jobs)))
             for j, a in zip(jobs, t):
@@ -747,7 +792,56 @@ def study_serving(args):
             res[f"load_{int(frac * 100)}"] = srv.run(jobs)
     finally:
         srv.close()
-    print(json.dumps(res), flush=True)
+    return res
+
+
+def study_serving(args):
+    torch, B = _torch_setup()
+    print(json.dumps(serving_record(torch, B, args.jobs, args.max_slots)), flush=True)
+
+
+def per_config_records(torch, B, flush_mb, alu_peak, names=("scale_ppc1", "scale_ppc2", "scale_ppc4",
+                                                              "scale_ppc16", "scale_ppc32", "clustered"),
+                       reps=20):
+    """The other single-GPU configurations: per workload one full step and the
+    interaction alone (medians of CUDA events, L2 flushed before each), with
+    the shape pi_autotune picks, the within-cutoff pairs per second and the
+    interaction's fraction of the FP32 peak on useful FLOP."""
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(flush_mb * (1 << 20) // 4, device=dev)
+    s = torch.cuda.current_stream()
+    rows = {}
+    for name in names:
+        w = W.WORKLOADS[name]
+        x, y, z = w.positions()
+        ctx = B.pi_create(w.lo, w.hi, w.rc, w.n)
+        try:
+            t = [torch.from_numpy(a).to(dev) for a in (x, y, z)]
+            out = [torch.empty(w.n, device=dev) for _ in range(4)]
+            nb = torch.empty(w.n, dtype=torch.int32, device=dev)
+            B.pi_bin(ctx, *t, w.n, s)
+            chosen, _ = B.pi_autotune(ctx, [w.h], *out, nb, B.PI_ORDER_SORTED, 3, s)
+            B.pi_sync_status(ctx, s)
+            pairs = int(nb.to(torch.int64).sum().item())
+            inter = lambda: B.pi_interact(ctx, w.h, *out, nb, B.PI_ORDER_SORTED, s)
+            step = lambda: (B.pi_bin(ctx, *t, w.n, s), inter())
+            step()
+            int_ms, _ = _time_events(torch, inter, reps, flush)
+            step_ms, _ = _time_events(torch, step, reps, flush)
+            _, mpc = B.pi_sync_status(ctx, s)
+            rows[name] = {"n": w.n, "cells_per_axis": w.cells_per_axis(), "layout": w.layout,
+                          "max_per_cell": mpc, "pairs": pairs,
+                          "shape": "ppnl" if chosen == B.PI_AUTOTUNE_PPNL else f"tile{chosen}",
+                          "step_ms": step_ms, "interact_ms": int_ms,
+                          "pairs_per_s": pairs / (step_ms * 1e-3),
+                          "interact_pairs_per_s": pairs / (int_ms * 1e-3),
+                          "full_step_particles_per_s": w.n / (step_ms * 1e-3),
+                          "interact_frac_of_fp32_peak": FLOP_PER_PAIR * pairs / (int_ms * 1e-3) / 1e12 / alu_peak}
+            del t, out, nb
+        finally:
+            B.pi_destroy(ctx)
+    return {"rows": rows, "timing": f"medians of {reps} CUDA-event timings, L2 flushed before each",
+            "frac_basis": "17 FLOP per within-cutoff ordered pair over the derived FP32 peak"}
 
 
 def study_sweep(args):

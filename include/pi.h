@@ -138,12 +138,13 @@ pi_status pi_create(const pi_box* box, float r_c, int64_t n_max, pi_ctx** out);
  * unchanged.  The new constants are written by a launch on `stream`, so work
  * enqueued on that stream afterwards sees them; the context must be binned
  * again before pi_interact.  Used to keep device-resident contexts for jobs
- * of varying shape (serving).  Errors: PI_ERR_INVALID_ARG (also for a batch
+ * of varying shape (serving).  The grid follows pi_create's rule (Sec. 3:
+ * cells at least r_c wide).  Errors: PI_ERR_INVALID_ARG (also for a batch
  * context), PI_ERR_CAPACITY, PI_ERR_CUDA. */
 pi_status pi_reconfigure(pi_ctx* ctx, const pi_box* box, float r_c, pi_stream stream);
 
 /* Frees the context and its device buffers (synchronises the device first).
- * NULL is accepted. */
+ * NULL is accepted.  No passage of the paper: library housekeeping. */
 pi_status pi_destroy(pi_ctx* ctx);
 
 /* Binning (Sec. 2, Fig. 1).  x, y, z: device arrays of n FP32 positions
@@ -169,52 +170,66 @@ pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, in
  *   V[i]   = sum_j d_ij K_ij   (Vx, Vy, Vz).
  * S, Vx, Vy, Vz: device FP32 arrays of n entries (caller-owned, written).
  * nbr: device uint32 array of n entries, or NULL to skip the counts.
- * h > 0 and finite.  out_order: PI_ORDER_SORTED or PI_ORDER_ORIGINAL.
+ * Every path excludes the self pair by identity (j != i of Sec. 2), so a
+ * distinct particle at the same position counts, with K = 1 and a zero
+ * vector term.
+ * h > 0 and finite, with a finite FP32 kernel scale: -log2(e)/h^2 for the
+ * Gaussian (h above about 6.5e-20), h^2 finite and non-zero for the
+ * Lennard-Jones kernels; otherwise PI_ERR_INVALID_ARG.  Terms are FP32: a
+ * Gaussian term below 2^-126 (the smallest normal FP32 number, reached
+ * where (r/h)^2 > 87) is flushed to zero, so each output carries at most
+ * that much per neighbour (|d_ij| times that for V) beyond its relative
+ * error.  out_order: PI_ORDER_SORTED or PI_ORDER_ORIGINAL.
  * Output arrays must not alias each other or the inputs of pi_bin.
  * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
 pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
                       uint32_t* nbr, int out_order, pi_stream stream);
 
-/* End-to-end step through host memory: copies n positions from the host
- * arrays hx, hy, hz into context-owned device buffers, runs pi_bin and
- * pi_interact, copies the outputs back into the host arrays hS, hVx, hVy,
- * hVz (and hnbr unless NULL), then synchronises `stream` and returns the
- * step's status (device-side errors included).  Pinned host memory gives
- * asynchronous copies; pageable memory works too.  The device staging
- * buffers are allocated on the first call (n_max entries).
- * Errors: those of pi_bin, pi_interact and pi_sync_status, PI_ERR_NOMEM. */
+/* End-to-end step through host memory (one step of Sec. 2's method: the
+ * binning of pi_bin and the interaction of pi_interact): copies n positions
+ * from the host arrays hx, hy, hz into context-owned device buffers, runs
+ * pi_bin and pi_interact, copies the outputs back into the host arrays hS,
+ * hVx, hVy, hVz (and hnbr unless NULL), then synchronises `stream` and
+ * returns the step's status (device-side errors included).  Pinned host
+ * memory gives asynchronous copies; pageable memory works too.  The device
+ * staging buffers are allocated on the first call (n_max entries).  Errors:
+ * those of pi_bin, pi_interact and pi_sync_status, PI_ERR_NOMEM.
+ */
 pi_status pi_run_host(pi_ctx* ctx, const float* hx, const float* hy, const float* hz,
                       int64_t n, float h, float* hS, float* hVx, float* hVy, float* hVz,
                       uint32_t* hnbr, int out_order, pi_stream stream);
 
-/* One job of a request loop, enqueued without waiting: re-targets the
- * context to (box, r_c) when they differ from its current ones (as
- * pi_reconfigure: the new grid must fit the context), copies the n host
- * positions into the context's device staging buffers, runs pi_bin and
- * pi_interact, and copies the outputs back into the host arrays -- all on
- * `stream`, in that order, nothing synchronised.  The host arrays must stay
- * valid and untouched until the stream reaches this point (record an event
- * after the call); pinned memory makes the copies asynchronous.  The staging
- * buffers are allocated on the first pi_run_host / pi_submit_host call of a
- * context (a warm-up call keeps that out of a request loop).  Device-side
- * errors surface in pi_sync_status.  Errors returned at once: those of
- * pi_reconfigure, pi_bin and pi_interact, PI_ERR_NOMEM. */
+/* One job of a request loop (one step of Sec. 2's method on the job's own box
+ * and cutoff), enqueued without waiting: re-targets the context to (box, r_c)
+ * when they differ from its current ones (as pi_reconfigure: the new grid
+ * must fit the context), copies the n host positions into the context's
+ * device staging buffers, runs pi_bin and pi_interact, and copies the outputs
+ * back into the host arrays -- all on `stream`, in that order, nothing
+ * synchronised.  The host arrays must stay valid and untouched until the
+ * stream reaches this point (record an event after the call); pinned memory
+ * makes the copies asynchronous.  The staging buffers are allocated on the
+ * first pi_run_host / pi_submit_host call of a context (a warm-up call keeps
+ * that out of a request loop).  Device-side errors surface in pi_sync_status.
+ * Errors returned at once: those of pi_reconfigure, pi_bin and pi_interact,
+ * PI_ERR_NOMEM.
+ */
 pi_status pi_submit_host(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
                          const float* hz, int64_t n, float h, float* hS, float* hVx, float* hVy,
                          float* hVz, uint32_t* hnbr, int out_order, pi_stream stream);
 
-/* pi_submit_host with host arrays that may lie in blocks, so that the step
- * makes as few as one host-to-device and one device-to-host copy instead of
- * up to eight.  in_stride = 0: x, y, z are separate arrays (three copies);
- * in_stride > 0: they lie in one block, hy = hx + in_stride and hz = hx +
- * 2*in_stride (checked), and travel as one copy of 2*in_stride + n entries,
- * the gaps included.  out_stride likewise for S, Vx, Vy, Vz and, unless
- * NULL, the counts: hVx = hS + out_stride, ..., hnbr = (uint32_t*)(hS +
- * 4*out_stride).  A block must be one host allocation covering the copied
- * range.  A non-zero stride is a multiple of 4 with n <= stride <= n_max +
- * 4 rounded up to a multiple of 4.  Otherwise as pi_submit_host.
- * Errors: PI_ERR_INVALID_ARG (a stride outside these limits or arrays not at
- * their stride) and those of pi_submit_host. */
+/* pi_submit_host (Sec. 2's step, as above) with host arrays that may lie in
+ * blocks, so that the step makes as few as one host-to-device and one
+ * device-to-host copy instead of up to eight.  in_stride = 0: x, y, z are separate
+ * arrays (three copies); in_stride > 0: they lie in one block, hy = hx +
+ * in_stride and hz = hx + 2*in_stride (checked), and travel as one copy of
+ * 2*in_stride + n entries, the gaps included.  out_stride likewise for S, Vx,
+ * Vy, Vz and, unless NULL, the counts: hVx = hS + out_stride, ..., hnbr =
+ * (uint32_t*)(hS + 4*out_stride).  A block must be one host allocation
+ * covering the copied range.  A non-zero stride is a multiple of 4 with n <=
+ * stride <= n_max + 4 rounded up to a multiple of 4.  Otherwise as
+ * pi_submit_host.  Errors: PI_ERR_INVALID_ARG (a stride outside these limits
+ * or arrays not at their stride) and those of pi_submit_host.
+ */
 pi_status pi_submit_host_strided(pi_ctx* ctx, const pi_box* box, float r_c, const float* hx, const float* hy,
                                  const float* hz, int64_t in_stride, int64_t n, float h, float* hS, float* hVx,
                                  float* hVy, float* hVz, uint32_t* hnbr, int64_t out_stride, int out_order,
@@ -234,27 +249,31 @@ pi_status pi_submit_host_strided(pi_ctx* ctx, const pi_box* box, float r_c, cons
  */
 
 /* Creates a batch context on the current device.  boxes, r_c and n_max are
- * host arrays of num_systems entries (1 <= num_systems <= 2048), each
- * checked as in pi_create; the total of the cells stays below 2^31 and the
- * total of n_max below 2^31 - 64.
- * Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA. */
+ * host arrays of num_systems entries (1 <= num_systems <= 2048), each checked
+ * as in pi_create (Sec. 3's grid per system); the total of the cells stays
+ * below 2^31 and the total of n_max below 2^31 - 64.  Errors:
+ * PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA.
+ */
 pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float* r_c,
                           const int64_t* n_max, pi_ctx** out);
 
-/* Binning of every system (as pi_bin).  x, y, z: device arrays of the
- * concatenated positions; n: host array of num_systems counts, 0 <= n[s] <=
- * n_max[s].  Errors: as pi_bin. */
+/* Binning of every system (as pi_bin: Sec. 2, Fig. 1).  x, y, z: device
+ * arrays of the concatenated positions; n: host array of num_systems counts,
+ * 0 <= n[s] <= n_max[s].  Errors: as pi_bin.
+ */
 pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float* z,
                        const int64_t* n, pi_stream stream);
 
-/* Interaction of every system (as pi_interact).  h: host array of
- * num_systems kernel lengths, each > 0 and finite.  Outputs are device
- * arrays of the concatenated particles.  Errors: as pi_interact. */
+/* Interaction of every system (as pi_interact: Sec. 2, Sec. 3).  h: host
+ * array of num_systems kernel lengths, each as in pi_interact.  Outputs are
+ * device arrays of the concatenated particles.  Errors: as pi_interact.
+ */
 pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                             uint32_t* nbr, int out_order, pi_stream stream);
 
 /* Autotuner of the interaction for the data of the last pi_bin /
- * pi_batch_bin: runs the interaction (arguments as pi_batch_interact, h one
+ * pi_batch_bin (Sec. 5 sizes its launches from M_C and the shared memory;
+ * here the candidates are measured instead): runs the interaction (arguments as pi_batch_interact, h one
  * entry per system) once untimed and `reps` times timed (1 <= reps <= 100)
  * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..6) and then
  * with PI_ALGO_PPNL, keeps the candidate with the smallest median time for
@@ -271,27 +290,34 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
                       pi_stream stream);
 
 /* Number of systems, total cells and total particle capacity (host outputs,
- * any may be NULL). */
+ * any may be NULL).  No passage of the paper: library housekeeping. */
 pi_status pi_batch_info(const pi_ctx* ctx, int32_t* num_systems, int64_t* total_cells,
                         int64_t* total_n_max);
 
-/* Grid dimensions (nx, ny, nz) of one system into dims (host array of 3). */
+/* Grid dimensions (nx, ny, nz) of one system into dims (host array of 3):
+ * n_d = max(1, floor((hi_d - lo_d) / r_c)), the grid of cells at least r_c
+ * wide of Sec. 3.  PI_ERR_INVALID_ARG for a system index out of range. */
 pi_status pi_batch_grid(const pi_ctx* ctx, int32_t system, int32_t dims[3]);
 
-/* Grid dimensions (nx, ny, nz) of the first system into dims (host array of 3). */
+/* Grid dimensions (nx, ny, nz) of the first system into dims (host array of
+ * 3), as pi_batch_grid (Sec. 3's grid of cells at least r_c wide). */
 pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3]);
 
 /* Borrowed device pointers to the binning results, valid until the next
- * pi_bin or pi_destroy (any pointer argument may be NULL):
+ * pi_bin or pi_destroy (any pointer argument may be NULL): the arrays of
+ * Fig. 1 and Sec. 2 --
  *   counts[C] particles per cell; offsets[C+1] start of each cell in sorted
  *   order, offsets[C] = n; perm[n] input index of sorted slot k;
- *   sx, sy, sz[n] positions in sorted order. */
+ *   sx, sy, sz[n] positions in sorted order (the secondary SoA copy).
+ * The library owns them; read them only after the work of the last pi_bin
+ * on its stream is complete. */
 pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t** offsets,
                     const uint32_t** perm, const float** sx, const float** sy,
                     const float** sz);
 
-/* Copies the binning results of the last pi_bin into caller-owned device
- * buffers, asynchronously on `stream` (any pointer may be NULL to skip it):
+/* Copies the binning results of the last pi_bin (Fig. 1 and Sec. 2, as in
+ * pi_binned) into caller-owned device buffers, asynchronously on `stream`
+ * (any pointer may be NULL to skip it):
  * counts[C], offsets[C+1] (uint32), perm[n] (uint32), sx, sy, sz[n] (FP32),
  * with C and n as in pi_binned().  Errors: PI_ERR_INVALID_ARG,
  * PI_ERR_NOT_BINNED, PI_ERR_CUDA. */
@@ -310,11 +336,15 @@ pi_status pi_total_f64(pi_ctx* ctx, const float* v, double* out, pi_stream strea
 
 /* Synchronises `stream`, then returns the device-side status of the work
  * enqueued so far (PI_ERR_TIMEOUT, PI_ERR_OUT_OF_BOX, PI_ERR_CAPACITY or
- * PI_OK) and, if max_per_cell is not NULL, M_C of the last pi_bin. */
+ * PI_OK) and, if max_per_cell is not NULL, M_C of the last pi_bin (the
+ * largest cell count, which Sec. 5.1 uses to size its shared memory).  The
+ * status check itself has no passage in the paper: library housekeeping. */
 pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell);
 
 /* Sets an option (keys PI_OPT_*).  Host-side only; takes effect for work
- * enqueued afterwards.  Errors: PI_ERR_INVALID_ARG for an unknown key or value. */
+ * enqueued afterwards.  Errors: PI_ERR_INVALID_ARG for an unknown key or
+ * value.  The options select among the paper's kernels (Alg. 1, Sec. 7.1-7.2)
+ * and the build's own shapes; the call itself is library housekeeping. */
 pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
 
 /* Exclusive scan of per-cell counts that allocates nothing.
@@ -326,10 +356,14 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
  * budget), or a latency-critical loop that must not call cudaMalloc/cudaFree,
  * which can synchronise the whole device.
  *
- *   counts  device array of C uint32 counts (caller-owned, read only).
+ *   counts  device array of C uint32 counts (caller-owned, read only),
+ *           16-byte aligned (the scan reads four counts at a time).
  *   C       1 <= C <= 16,777,216 (2^24); larger C returns PI_ERR_CAPACITY.
- *   offsets device array of C+1 uint32 (caller-owned, written):
- *           offsets[c] = sum of counts[0..c-1], offsets[C] = the total.
+ *   offsets device array of C+1 uint32 (caller-owned, written), 16-byte
+ *           aligned: offsets[c] = sum of counts[0..c-1], offsets[C] = the
+ *           total.  A pointer that is not 16-byte aligned (a view that
+ *           starts at an odd element, say) returns PI_ERR_INVALID_ARG with
+ *           nothing enqueued.
  *   result  optional device array of 2 uint32 (caller-owned, written):
  *           result[0] = the largest count (M_C), result[1] = device error
  *           bits (0 = ok; non-zero means a bounded wait ran out and offsets
@@ -342,8 +376,11 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value);
  * device current) and caches it; make that first call before any stream
  * capture.  Every call shares the array and clears what it needs first, so
  * calls that may overlap on the GPU (other streams, other host threads) race
- * and must be serialised by the caller.
- * Errors: PI_ERR_INVALID_ARG, PI_ERR_CAPACITY, PI_ERR_CUDA. */
+ * and must be serialised by the caller.  If that first look-up fails, the
+ * failure is kept for the device and every later call on it returns
+ * PI_ERR_CUDA; pi_last_error() names the cause of every error.
+ * Errors: PI_ERR_INVALID_ARG, PI_ERR_CAPACITY (also for a device index of
+ * 64 or more), PI_ERR_CUDA. */
 pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, uint32_t* offsets,
                                  uint32_t* result, pi_stream stream);
 
@@ -388,50 +425,59 @@ typedef struct {
     int64_t slot_capacity; /* written: capacity of the slot that ran it      */
 } pi_job;
 
-/* Device memory one slot of the given particle capacity is charged against
+/* (The serving calls below have no passage in the paper, which runs one
+ * system at a time; each job is one step of Sec. 2's method.)
+ * Device memory one slot of the given particle capacity is charged against
  * the HBM budget: capacity * 144 bytes + 1 MiB (the context, up to one cell
  * per particle, and its staging buffers). */
 int64_t pi_server_slot_bytes(int64_t capacity);
 
-/* Creates a server on the current device.  capacity: num_buckets (1 ..
+/* Creates a server on the current device (no passage of the paper: the
+ * request loop is the build's own).  capacity: num_buckets (1 ..
  * PI_SERVER_MAX_BUCKETS) distinct particle capacities (each also the cell
  * capacity of its slots), 1 .. 2^30; initial_slots: slots made at once per
- * bucket (NULL: none; fewer if the budget runs out); max_slots_per_bucket
- * >= 1; hbm_budget: bytes the slots may be charged (<= 0: half of the
- * device's free memory).  Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM,
- * PI_ERR_CUDA. */
+ * bucket (NULL: none; fewer if the budget runs out); max_slots_per_bucket >=
+ * 1; hbm_budget: bytes the slots may be charged (<= 0: half of the device's
+ * free memory).  Errors: PI_ERR_INVALID_ARG, PI_ERR_NOMEM, PI_ERR_CUDA.
+ */
 pi_status pi_server_create(int32_t num_buckets, const int64_t* capacity, const int32_t* initial_slots,
                            int32_t max_slots_per_bucket, int64_t hbm_budget, pi_server** out);
 
-/* Serves num_jobs jobs, blocking until all are complete: a job is admitted
- * once `arrival` seconds have passed since the call started and a slot that
- * fits it is free (oldest arrival first).  Writes each job's t_start,
- * t_done and slot_capacity, and the time from the start to the last
- * completion into *makespan_s (may be NULL).  Every job is checked first:
- * PI_ERR_INVALID_ARG for a bad job, PI_ERR_CAPACITY for one that fits no
- * bucket (nothing runs then).  Afterwards the device status of every slot
- * is collected as in pi_sync_status.  The host arrays of a job must stay
- * valid until the call returns.  The calling thread polls while jobs run
- * (it sleeps only when nothing is running or queued).  Like a context, a
- * server is used by one host thread at a time. */
+/* Serves num_jobs jobs (each one step of Sec. 2's method), blocking until all
+ * are complete: a job is admitted once `arrival` seconds have passed since
+ * the call started and a slot that fits it is free (oldest arrival first).
+ * Writes each job's t_start, t_done and slot_capacity, and the time from the
+ * start to the last completion into *makespan_s (may be NULL).  Every job is
+ * checked first: PI_ERR_INVALID_ARG for a bad job, PI_ERR_CAPACITY for one
+ * that fits no bucket (nothing runs then).  Afterwards the device status of
+ * every slot is collected as in pi_sync_status.  The host arrays of a job
+ * must stay valid until the call returns.  The calling thread polls while
+ * jobs run (it sleeps only when nothing is running or queued).  Like a
+ * context, a server is used by one host thread at a time.
+ */
 pi_status pi_server_run(pi_server* srv, pi_job* jobs, int64_t num_jobs, double* makespan_s);
 
 /* Buckets (num_buckets; capacity and slots as arrays of that length, any
- * pointer may be NULL) and the bytes charged to the HBM budget. */
+ * pointer may be NULL) and the bytes charged to the HBM budget.  No passage
+ * of the paper: library housekeeping. */
 pi_status pi_server_info(const pi_server* srv, int32_t* num_buckets, int64_t* capacity, int32_t* slots,
                          int64_t* hbm_used);
 
 /* Destroys the server and its slots (waits for their streams).  NULL is
- * accepted. */
+ * accepted.  No passage of the paper: library housekeeping. */
 pi_status pi_server_destroy(pi_server* srv);
 
-/* Number of kernels this context has launched since pi_create (host counter). */
+/* Number of kernels this context has launched since pi_create (host
+ * counter).  No passage of the paper: library housekeeping. */
 pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count);
 
-/* Static text for a status code. */
+/* Static text for a status code.  No passage of the paper: library
+ * housekeeping. */
 const char* pi_status_str(pi_status s);
 
-/* Text of the last CUDA error seen by this host thread ("" if none). */
+/* Text of the last error seen by this host thread ("" if none): the CUDA
+ * error of a failed runtime call, or the reason of some argument errors.
+ * No passage of the paper: library housekeeping. */
 const char* pi_last_error(void);
 
 #ifdef __cplusplus

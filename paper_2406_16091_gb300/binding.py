@@ -313,11 +313,37 @@ def pi_copy_binned(ctx, counts=None, offsets=None, perm=None, sx=None, sy=None, 
                                  _ptr(sz), _stream(stream)), "pi_copy_binned")
 
 
+def _check_u32_device(t, need: int, what: str) -> None:
+    """A contiguous tensor of 4-byte elements on the current CUDA device with
+    at least ``need`` entries (checked before the C call, so that a short or
+    foreign buffer never reaches a kernel)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: a torch tensor is required")
+    if t.element_size() != 4 or t.is_floating_point() or t.is_complex():
+        raise TypeError(f"{what}: 4-byte integer elements are required, not {t.dtype}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what}: must be on the current CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    if t.numel() < need:
+        raise ValueError(f"{what}: {t.numel()} entries, {need} needed")
+
+
 def pi_scan_counts_noalloc(counts, C: int, offsets, result=None, stream=None) -> None:
     """Exclusive scan of C device counts into C+1 device offsets using the
     library's fixed scratch array (no allocation); result (2 uint32, device)
-    receives M_C and the device error bits."""
-    _check(load().pi_scan_counts_noalloc(_ptr(counts), int(C), _ptr(offsets), _ptr(result),
+    receives M_C and the device error bits.  The tensors are checked here
+    (4-byte integer elements, contiguous, on the current device, long
+    enough); the library checks the size limit and the 16-byte alignment."""
+    C = int(C)
+    if C >= 1:
+        _check_u32_device(counts, C, "counts")
+        _check_u32_device(offsets, C + 1, "offsets")
+        if result is not None:
+            _check_u32_device(result, 2, "result")
+    _check(load().pi_scan_counts_noalloc(_ptr(counts), C, _ptr(offsets), _ptr(result),
                                          _stream(stream)), "pi_scan_counts_noalloc")
 
 

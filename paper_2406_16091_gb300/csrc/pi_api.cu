@@ -68,7 +68,7 @@ struct pi_ctx {
 
     int64_t n;                      // particles of the last pi_bin (all systems)
     std::vector<uint32_t> pbase_h;  // [S+1] particle bases of the last pi_bin
-    std::vector<float> kscale_h;    // per-system kernel scale last written to d_kscale
+    std::vector<float> kscale_h;    // [2S] per-system kernel scales last written to d_kscale
     int binned;                     // a pi_bin has been enqueued since the last failure
     uint32_t epoch;                 // scan launch epoch
     uint64_t launches;              // kernels launched
@@ -163,7 +163,7 @@ pi_status make_system(const pi_box& box, float r_c, SysDesc& d, int64_t& cells)
     return PI_OK;
 }
 
-// Scale t of the interaction kernel for length h.
+// Scale t of the interaction kernel for length h (FP32).
 float kernel_scale(int kernel, float h)
 {
     const double hd = (double)h;
@@ -172,6 +172,30 @@ float kernel_scale(int kernel, float h)
         case PI_KERNEL_HIGHFLOP: return h * h;  // sigma^2 in FP32
         case PI_KERNEL_LOWFLOP: return 0.f;
         default: return (float)(-1.4426950408889634 / (hd * hd));  // -log2(e) / h^2
+    }
+}
+
+// The FP32 remainder of the Gaussian's FP64 scale after its FP32 value (the
+// fine Gaussian uses t + tl).
+float kernel_scale_lo(int kernel, float h)
+{
+    if (kernel != PI_KERNEL_GAUSSIAN) return 0.f;
+    const double hd = (double)h, t = -1.4426950408889634 / (hd * hd);
+    return (float)(t - (double)(float)t);
+}
+
+// Whether the scale of h is usable: finite for the Gaussian (below about
+// h = 6.5e-20 it overflows FP32, and 0 * -inf would turn the term of two
+// coincident particles into NaN), finite and non-zero for Lennard-Jones
+// (sigma^2 = h^2 must neither overflow nor flush to zero).
+bool scale_ok(int kernel, float h)
+{
+    const float t = kernel_scale(kernel, h);
+    switch (kernel) {
+        case PI_KERNEL_LJ:
+        case PI_KERNEL_HIGHFLOP: return std::isfinite(t) && t > 0.f;
+        case PI_KERNEL_LOWFLOP: return true;
+        default: return std::isfinite(t);
     }
 }
 
@@ -223,7 +247,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->wbase.assign(S + 1, 0);
     c->rbase.assign(S + 1, 0);
     c->pbase_h.assign(S + 1, 0);
-    c->kscale_h.assign(S, std::nanf(""));
+    c->kscale_h.assign(2 * (size_t)S, std::nanf(""));
     int64_t C = 0, N = 0, R = 0, RW = 0;
     for (int s = 0; s < S; ++s) {
         int64_t cells = 0;
@@ -287,7 +311,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_cbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_wbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_rbase = k.take<uint32_t>((size_t)S + 1);
-    const size_t o_kscale = k.take<float>((size_t)S);
+    const size_t o_kscale = k.take<float>(2 * (size_t)S);
     const size_t o_partial = k.take<double>((size_t)S * pi::TOTAL_PARTS);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
@@ -558,8 +582,14 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
                             uint32_t* nbr, int out_order, pi_stream stream)
 {
     if (!ctx || !h) return PI_ERR_INVALID_ARG;
-    for (int s = 0; s < ctx->S; ++s)
+    for (int s = 0; s < ctx->S; ++s) {
         if (!(h[s] > 0.0f) || std::isinf(h[s])) return PI_ERR_INVALID_ARG;
+        if (!scale_ok(ctx->kernel, h[s])) {
+            std::snprintf(g_last_error, sizeof g_last_error,
+                          "pi_interact: h = %g of system %d gives no finite FP32 kernel scale", (double)h[s], s);
+            return PI_ERR_INVALID_ARG;
+        }
+    }
     if (out_order != PI_ORDER_SORTED && out_order != PI_ORDER_ORIGINAL) return PI_ERR_INVALID_ARG;
     if (!ctx->binned) return PI_ERR_NOT_BINNED;
     if (ctx->n > 0 && (!S || !Vx || !Vy || !Vz)) return PI_ERR_INVALID_ARG;
@@ -580,22 +610,33 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     a.n = (uint32_t)ctx->n;
     a.np = (uint32_t)(ctx->n + pi::ROW_PADS * ctx->rows);
     a.work = ctx->work;
-    a.kernel = ctx->kernel;
     a.one = 1.0f;
     a.zero = 0.0f;
+    // the Gaussian with the compensated exponent where some system's kernel
+    // is short next to its cutoff (r_c^2 / h^2 above FINE_GAUSS_RATIO)
+    bool fine = false;
+    if (ctx->kernel == PI_KERNEL_GAUSSIAN)
+        for (int s = 0; s < ctx->S; ++s) {
+            const double r = (double)ctx->rc[s] / (double)h[s];
+            fine = fine || r * r > pi::FINE_GAUSS_RATIO;
+        }
+    a.kernel = fine ? pi::KERNEL_GAUSSIAN_FINE : ctx->kernel;
     if (ctx->S == 1) {
         a.kscale = nullptr;
         a.kscale0 = kernel_scale(ctx->kernel, h[0]);
+        a.kscale0_lo = kernel_scale_lo(ctx->kernel, h[0]);
     } else {
         // write the per-system scales only when they changed
+        const int S = ctx->S;
         bool same = true;
-        std::vector<float> t(ctx->S);
-        for (int s = 0; s < ctx->S; ++s) {
+        std::vector<float> t(2 * (size_t)S);
+        for (int s = 0; s < S; ++s) {
             t[s] = kernel_scale(ctx->kernel, h[s]);
-            same = same && t[s] == ctx->kscale_h[s];
+            t[S + s] = kernel_scale_lo(ctx->kernel, h[s]);
         }
+        for (int i = 0; i < 2 * S; ++i) same = same && t[i] == ctx->kscale_h[i];
         if (!same) {
-            PI_TRY(pi::launch_set_kscale(ctx->d_kscale, t.data(), ctx->S, st));
+            PI_TRY(pi::launch_set_kscale(ctx->d_kscale, t.data(), 2 * S, st));
             ctx->launches += 1;
             ctx->kscale_h = t;
         }
@@ -626,7 +667,8 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
         // per cell) and the compensated sums keep all their registers and
         // run fewer warps
         constexpr int64_t QUAD_THREADS_PER_SM = 5 * 128;
-        const bool packed = !kahan && (ctx->kernel == PI_KERNEL_GAUSSIAN || ctx->kernel == PI_KERNEL_LOWFLOP);
+        const bool packed =
+            !kahan && ((ctx->kernel == PI_KERNEL_GAUSSIAN && !fine) || ctx->kernel == PI_KERNEL_LOWFLOP);
         const bool full_wave = ctx->n / 4 >= (int64_t)ctx->num_sms * QUAD_THREADS_PER_SM;
         const int tile = ctx->tile >= 0 ? ctx->tile
                          : (packed && full_wave && ctx->n >= 8 * ctx->C ? pi::HIGH_OCCUPANCY_TILE

@@ -579,13 +579,13 @@ __global__ void k_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uin
 
 struct KscaleArgs {
     float* dst;
-    int S;
-    float vals[MAX_SYSTEMS];
+    int count;
+    float vals[2 * MAX_SYSTEMS];
 };
 
 __global__ void k_set_kscale(KscaleArgs k)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.S; i += gridDim.x * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.count; i += gridDim.x * blockDim.x)
         k.dst[i] = k.vals[i];
 }
 }  // namespace
@@ -597,13 +597,14 @@ cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s)
+cudaError_t launch_set_kscale(float* kscale, const float* vals, int count, cudaStream_t s)
 {
+    if (count < 0 || count > 2 * MAX_SYSTEMS) return cudaErrorInvalidValue;
     KscaleArgs k;
     k.dst = kscale;
-    k.S = S;
-    for (int i = 0; i < S; ++i) k.vals[i] = vals[i];
-    k_set_kscale<<<(S + 255) / 256, 256, 0, s>>>(k);
+    k.count = count;
+    for (int i = 0; i < count; ++i) k.vals[i] = vals[i];
+    k_set_kscale<<<(count + 255) / 256, 256, 0, s>>>(k);
     return cudaGetLastError();
 }
 

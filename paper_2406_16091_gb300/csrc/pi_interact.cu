@@ -91,43 +91,88 @@ struct KahanAcc {
     __device__ __forceinline__ float value() const { return v; }
 };
 
-// Value of the interaction kernel for one pair inside the cutoff; t is the
+// Scale of the kernel (t; for the fine Gaussian also the remainder tl of
+// the FP64 scale after t) and the opaque constants of the high-FLOP kernel.
+struct KParams {
+    float t, tl, one, zero;
+};
+
+// s + e = a + b exactly (Knuth's two-sum, six rounded operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+constexpr float LN2_F = 0.693147180559945309f;
+
+// exp(-r^2/h^2) for a short kernel length h.  In FP32 the exponent
+// u = r2 t carries the rounding of r2 and of t relative to |u|, which reaches
+// 64 log2(e) at h = r_c/8, so the plain form's relative error per term grows
+// as (r/h)^2 (about 1e-5 at h = r_c/10).  Here r^2 of the FP32 offsets is
+// kept as a sum with its rounding errors (exact squares by fma, two-sums),
+// the product with the scale t + tl keeps its rounding error (fma), and the
+// small remainder c of the exponent is applied to first order:
+// K = 2^uh (1 + c ln 2), accurate to a few ulp whatever h.  For a far
+// candidate (a row's sentinel slots at 1e18) uh overflows to -inf and c to
+// +inf or NaN; c is clamped to [-1, 1] (fminf/fmaxf return the number
+// against a NaN) so that K = 0 * (1 + c ln 2) stays an exact 0, which the
+// pair test's mask then keeps out of the sums.
+__device__ __forceinline__ float gauss_fine(float dx, float dy, float dz, float th, float tl)
+{
+    const float px = __fmul_rn(dx, dx), ex = __fmaf_rn(dx, dx, -px);
+    const float py = __fmul_rn(dy, dy), ey = __fmaf_rn(dy, dy, -py);
+    const float pz = __fmul_rn(dz, dz), ez = __fmaf_rn(dz, dz, -pz);
+    float s1, e1, s2, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, s2, e2);
+    const float uh = __fmul_rn(s2, th);
+    const float ue = __fmaf_rn(s2, th, -uh);
+    const float es = __fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, __fadd_rn(e1, e2)));
+    const float c = fminf(fmaxf(__fmaf_rn(th, es, __fmaf_rn(tl, s2, ue)), -1.f), 1.f);
+    const float k0 = ex2_approx(uh);
+    return __fmaf_rn(__fmul_rn(k0, c), LN2_F, k0);
+}
+
+// Value of the interaction kernel for one pair inside the cutoff at FP32
+// offset (dx, dy, dz), r2 the frozen FP32 squared distance; kp.t is the
 // system's scale (Gaussian: -log2(e)/h^2; Lennard-Jones: sigma^2).
 template <int KERNEL>
-__device__ __forceinline__ float kernel_value(float r2, float t, float one, float zero)
+__device__ __forceinline__ float kernel_value(float dx, float dy, float dz, float r2, const KParams& kp)
 {
     if constexpr (KERNEL == KERNEL_GAUSSIAN) {
-        return ex2_approx(__fmul_rn(r2, t));
+        return ex2_approx(__fmul_rn(r2, kp.t));
+    } else if constexpr (KERNEL == KERNEL_GAUSSIAN_FINE) {
+        return gauss_fine(dx, dy, dz, kp.t, kp.tl);
     } else if constexpr (KERNEL == KERNEL_LOWFLOP) {
         return 1.0f;
     } else {
+        const float t = kp.t;
         const float rs2 = __fmaf_rn(0.01f, t, r2);
         const float sr = __fmul_rn(t, __frcp_rn(rs2));
         const float s3 = __fmul_rn(__fmul_rn(sr, sr), sr);
         float K = __fmul_rn(4.0f, __fsub_rn(__fmul_rn(s3, s3), s3));
         if constexpr (KERNEL == KERNEL_HIGHFLOP) {
 #pragma unroll
-            for (int i = 0; i < 75; ++i) K = __fmaf_rn(K, one, zero);
+            for (int i = 0; i < 75; ++i) K = __fmaf_rn(K, kp.one, kp.zero);
         }
         return K;
     }
 }
 
-// Scale of the kernel and the opaque constants of the high-FLOP kernel.
-struct KParams {
-    float t, one, zero;
-};
-
-// Where the tiled kernel excludes the self pair by identity instead of
-// adding K(0) and taking it off again: kernels whose value at r = 0 is far
-// larger than their typical sum (Lennard-Jones), and the compensated
-// precision mode, where taking K(0) off would cost the accuracy of particles
-// whose sum is small next to K(0).
-template <int KERNEL, class Acc>
-__host__ __device__ constexpr bool self_by_identity()
+// The kernel parameters of system sid: kscale holds the S scales, then the
+// S remainders of the fine Gaussian.
+__device__ __forceinline__ KParams kparams(const InteractArgs& a, int sid)
 {
-    return KERNEL == KERNEL_LJ || KERNEL == KERNEL_HIGHFLOP || std::is_same<Acc, KahanAcc>::value;
+    return a.kscale ? KParams{a.kscale[sid], a.kscale[a.sy.S + sid], a.one, a.zero}
+                    : KParams{a.kscale0, a.kscale0_lo, a.one, a.zero};
 }
+
+// Every path excludes the self pair by identity (the source's stable slot
+// equals the target's), as Sec. 2's j != i states: adding K(0) and taking it
+// off at the end would round every partial sum at the magnitude of K(0),
+// which for a short kernel length h is far larger than the particle's sum.
 
 // Per-target accumulators of one interaction kernel.
 template <class Acc, int KERNEL>
@@ -152,7 +197,7 @@ struct Sums {
     {
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         const bool in = (r2 < rc2) && !self;
-        const float e = kernel_value<KERNEL>(r2, kp.t, kp.one, kp.zero);
+        const float e = kernel_value<KERNEL>(dx, dy, dz, r2, kp);
         add(dx, dy, dz, in ? e : 0.f, in);
     }
 
@@ -160,20 +205,19 @@ struct Sums {
     __device__ __forceinline__ void pair(float dx, float dy, float dz, float rc2, const KParams& kp)
     {
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 < rc2) add(dx, dy, dz, kernel_value<KERNEL>(r2, kp.t, kp.one, kp.zero), true);
+        if (r2 < rc2) add(dx, dy, dz, kernel_value<KERNEL>(dx, dy, dz, r2, kp), true);
     }
 };
 
 template <class Acc, int KERNEL>
-__device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot,
-                                          const Sums<Acc, KERNEL>& r, float s_bias, uint32_t n_bias)
+__device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot, const Sums<Acc, KERNEL>& r)
 {
     const uint32_t o = a.original_order ? a.perm[slot] : slot;
-    a.S[o] = r.s.value() - s_bias;
+    a.S[o] = r.s.value();
     a.Vx[o] = r.vx.value();
     a.Vy[o] = r.vy.value();
     a.Vz[o] = r.vz.value();
-    if (a.nbr) a.nbr[o] = r.n - n_bias;
+    if (a.nbr) a.nbr[o] = r.n;
 }
 
 // ---- Alg. 1: Par-Part-NoLoop ------------------------------------------------
@@ -195,7 +239,7 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
     const int cy = axis_cell(yt, g.lo[1], g.inv_w[1], ny);
     const int cz = axis_cell(zt, g.lo[2], g.inv_w[2], nz);
     Sums<Acc, KERNEL> r;
-    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
+    const KParams kp = kparams(a, sid);
     for (int bz = max(cz - 1, 0); bz <= min(cz + 1, nz - 1); ++bz)
         for (int by = max(cy - 1, 0); by <= min(cy + 1, ny - 1); ++by) {
             const uint32_t row = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
@@ -206,7 +250,7 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
                 r.pair(__fsub_rn(a.sx[j], xt), __fsub_rn(a.sy_pos[j], yt), __fsub_rn(a.sz[j], zt), d.rc2, kp);
             }
         }
-    store_out(a, k, r, 0.f, 0u);
+    store_out(a, k, r);
 }
 
 // ---- tiled interaction ----------------------------------------------------------
@@ -274,7 +318,7 @@ struct Smem {
     uint32_t win[10][T::NT];
     Plan plan;
     SysDesc d;             // the system of the current X-row
-    float t;               // its kernel scale
+    KParams kp;            // its kernel parameters
     uint32_t coarse_mask;  // bit r: row r holds a cell without sub-bin starts
     uint32_t row;          // current X-row, local to its system
     int xs, xe;            // its cells [xs, xe) handled by this work item
@@ -601,16 +645,9 @@ __device__ __forceinline__ void target_windows(const E (*tbl)[RB], uint32_t coar
     }
 }
 
-// 1.0f if a < b else 0.0f (PTX set with a float destination).
-__device__ __forceinline__ float lt_mask(float a, float b)
-{
-    float m;
-    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
-    return m;
-}
-
-// 1.0f if a < b and u != v, else 0.0f: the pair test of the kernels that
-// exclude the self pair by identity (u, v the slots of source and target).
+// 1.0f if a < b and u != v, else 0.0f (PTX set with a float destination):
+// the pair test with the self pair excluded by identity (u, v the stable
+// slots of source and target).
 __device__ __forceinline__ float lt_ne_mask(float a, float b, float u, float v)
 {
     float m;
@@ -627,17 +664,42 @@ __device__ __forceinline__ float lt_ne_mask(float a, float b, float u, float v)
 // round it, candidate after candidate, so each target's sums are those of
 // the sequential scalar loop.  The pair test gives a 1/0 mask m and the
 // term is K = value * m, so a candidate that fails it (the other target's,
-// a row's sentinel slots, the target itself where it is excluded by
-// identity) contributes an exact zero, which leaves the plain sums as they
-// were.  The compensated sums take the same zero through the mask: with
+// a row's sentinel slots, the target itself) contributes an exact zero,
+// which leaves the plain sums as they were.  The compensated sums take the same zero through the mask: with
 // y = t - c*m, u = v + y, c' = (u - v) - y and c <- c*(1 - m) + c', a
 // rejected candidate leaves v and c unchanged (up to the sign of a zero c)
 // and an accepted one is the Kahan step exactly.  Compensations are kept
 // negated (cn = -c) so that every step is one add or fma.
+// gauss_fine for two targets with packed FP32 arithmetic (each element
+// rounded as the scalar steps round it).
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ float2 gauss_fine2(float2 dx, float2 dy, float2 dz, float2 th, float2 tl)
+{
+    const float2 px = __fmul2_rn(dx, dx), ex = __ffma2_rn(dx, dx, neg2(px));
+    const float2 py = __fmul2_rn(dy, dy), ey = __ffma2_rn(dy, dy, neg2(py));
+    const float2 pz = __fmul2_rn(dz, dz), ez = __ffma2_rn(dz, dz, neg2(pz));
+    float2 s1, e1, s2, e2;
+    two_sum2(px, py, s1, e1);
+    two_sum2(s1, pz, s2, e2);
+    const float2 uh = __fmul2_rn(s2, th);
+    const float2 ue = __ffma2_rn(s2, th, neg2(uh));
+    const float2 es = __fadd2_rn(__fadd2_rn(ex, ey), __fadd2_rn(ez, __fadd2_rn(e1, e2)));
+    float2 c = __ffma2_rn(th, es, __ffma2_rn(tl, s2, ue));
+    c = make_float2(fminf(fmaxf(c.x, -1.f), 1.f), fminf(fmaxf(c.y, -1.f), 1.f));
+    const float2 k0 = make_float2(ex2_approx(uh.x), ex2_approx(uh.y));
+    return __ffma2_rn(__fmul2_rn(k0, c), make_float2(LN2_F, LN2_F), k0);
+}
+
 template <class Acc, int KERNEL>
 struct PairSumsT {
     static constexpr bool kahan = std::is_same<Acc, KahanAcc>::value;
-    static constexpr bool by_id = self_by_identity<KERNEL, Acc>();
     float2 s = make_float2(0.f, 0.f), vx = make_float2(0.f, 0.f), vy = make_float2(0.f, 0.f),
            vz = make_float2(0.f, 0.f), n = make_float2(0.f, 0.f);
     float2 cs = make_float2(0.f, 0.f), cx = make_float2(0.f, 0.f), cy = make_float2(0.f, 0.f),
@@ -662,15 +724,13 @@ struct PairSumsT {
         const float2 dy = make_float2(__fsub_rn(p.y, ta.y), __fsub_rn(p.y, tb.y));
         const float2 dz = make_float2(__fsub_rn(p.z, ta.z), __fsub_rn(p.z, tb.z));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        float2 m;
-        if constexpr (by_id)
-            m = make_float2(lt_ne_mask(r2.x, rc2, p.w, ta.w), lt_ne_mask(r2.y, rc2, p.w, tb.w));
-        else
-            m = make_float2(lt_mask(r2.x, rc2), lt_mask(r2.y, rc2));
+        const float2 m = make_float2(lt_ne_mask(r2.x, rc2, p.w, ta.w), lt_ne_mask(r2.y, rc2, p.w, tb.w));
         float2 K;
         if constexpr (KERNEL == KERNEL_GAUSSIAN) {
             const float2 t = __fmul2_rn(r2, ks);
             K = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), m);
+        } else if constexpr (KERNEL == KERNEL_GAUSSIAN_FINE) {
+            K = __fmul2_rn(gauss_fine2(dx, dy, dz, ks, make_float2(kp.tl, kp.tl)), m);
         } else if constexpr (KERNEL == KERNEL_LOWFLOP) {
             K = m;
         } else {
@@ -728,11 +788,10 @@ __device__ __forceinline__ void window_sums(const float4* src, int j, int je, fl
                                             float zt, uint32_t slot, float rc2, const KParams& kp,
                                             Sums<Acc, KERNEL>& r)
 {
-    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
     for (; j < je; ++j) {
         const float4 s0 = src[j];
         r.pair_nb(__fsub_rn(s0.x, xt), __fsub_rn(s0.y, yt), __fsub_rn(s0.z, zt), rc2, kp,
-                  by_id && __float_as_uint(s0.w) == slot);
+                  __float_as_uint(s0.w) == slot);
     }
 }
 
@@ -839,7 +898,7 @@ __device__ __forceinline__ void chunk_pair(const InteractArgs& a, const float4* 
                                            const uint16_t (*tbl_s)[RB], const uint32_t (*tbl_g)[RB_GLOBAL],
                                            uint32_t coarse_mask, const SysDesc& d, uint32_t (*win)[WT],
                                            unsigned tid, int mode, int first, int qa, bool has_b, int cy,
-                                           int cz, int base, const KParams& kp, float kself, uint32_t nself)
+                                           int cz, int base, const KParams& kp)
 {
     const int qb = has_b ? qa + 1 : qa;
     const float4 ta = mode == 0 ? buf[first + qa] : a.P[first + qa];
@@ -857,8 +916,8 @@ __device__ __forceinline__ void chunk_pair(const InteractArgs& a, const float4* 
         target_sums_global<Acc, KERNEL>(a.P, tbl_g, coarse_mask, d, ta, cy, cz, base, kp, ra);
         if (has_b) target_sums_global<Acc, KERNEL>(a.P, tbl_g, coarse_mask, d, tb, cy, cz, base, kp, rb);
     }
-    store_out(a, __float_as_uint(ta.w), ra, kself, nself);
-    if (has_b) store_out(a, __float_as_uint(tb.w), rb, kself, nself);
+    store_out(a, __float_as_uint(ta.w), ra);
+    if (has_b) store_out(a, __float_as_uint(tb.w), rb);
 }
 
 template <class T, class Acc, int KERNEL>
@@ -873,11 +932,6 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(a.seq + 1u) & 1u] = 0u;
     if (load_error(a.ctrl)) return;
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    // The self pair (r = 0) adds exactly kernel_value(0) to S and 1 to n;
-    // both are taken off at the end instead of testing identities per pair
-    // (except for the kernels of self_by_identity).
-    const float k0_scale_free = KERNEL == KERNEL_GAUSSIAN ? ex2_approx(0.f) : 0.f;
-
     if (tid == 0) {
         sm.failed = 0;
         sm.buf[T::CAP] = sentinel();
@@ -894,7 +948,7 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
             if (item < a.work) {
                 const int sid = a.sy.S == 1 ? 0 : find_system(a.sy.wbase, a.sy.S, item);
                 sm.d = a.sy.sys[sid];
-                sm.t = a.kscale ? a.kscale[sid] : a.kscale0;
+                sm.kp = kparams(a, sid);
                 const uint32_t local = item - sm.d.work_base;
                 const uint32_t seg = local % sm.d.nseg;
                 sm.row = local / sm.d.nseg;
@@ -909,14 +963,6 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
         const int nx = d.g.n[0], ny = d.g.n[1];
         const int cy = (int)(row % (uint32_t)ny), cz = (int)(row / (uint32_t)ny);
         const uint32_t rb0 = d.cell_base + (uint32_t)nx * row;
-        // the self pair's contribution (0 where it is excluded by identity)
-        float kself = k0_scale_free;
-        uint32_t nself = 1u;
-        if constexpr (KERNEL == KERNEL_LOWFLOP) kself = 1.0f;
-        if constexpr (self_by_identity<KERNEL, Acc>()) {
-            kself = 0.f;
-            nself = 0u;
-        }
 
         const int xe = sm.xe;
         for (int x0 = sm.xs; x0 < xe;) {
@@ -960,15 +1006,14 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
             const int t0 = p.sbeg[4] + (int)(tb - p.gbeg[4]);
             const int base = XSUB * p.xa;
             if (!sm.failed) {
-                const KParams kp{sm.t, a.one, a.zero};
+                const KParams kp = sm.kp;
                 const int first = mode == 0 ? t0 : (int)tb;
                 for (int q0 = 0; q0 < ntarget; q0 += 2 * NT) {
                     const int qa = q0 + 2 * (int)tid;
                     if (qa >= ntarget) continue;
                     chunk_pair<T::CAP, T::RB, NT, Acc, KERNEL>(a, sm.buf, sm.tbl.staged, sm.tbl.global,
                                                                sm.coarse_mask, sm.d, sm.win, tid, mode, first,
-                                                               qa, qa + 1 < ntarget, cy, cz, base, kp, kself,
-                                                               nself);
+                                                               qa, qa + 1 < ntarget, cy, cz, base, kp);
                 }
             }
             __syncthreads();
@@ -1160,8 +1205,7 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
 }
 
 template <class T, class Acc, int KERNEL>
-__device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, unsigned lane, float kself,
-                            uint32_t nself)
+__device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, unsigned lane)
 {
     constexpr int NS = T::NS;
     for (uint32_t v = 0;; ++v) {
@@ -1175,7 +1219,7 @@ __device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, 
                   ng = st.ngroups;
         const uint32_t tb = st.tb;
         const int first = mode == 0 ? p.sbeg[4] + (int)(tb - p.gbeg[4]) : (int)tb;
-        const KParams kp{st.t, a.one, a.zero};
+        const KParams kp{st.t, 0.f, a.one, a.zero};  // the fine Gaussian never runs here
         for (;;) {
             int g = 0;
             if (lane == 0) g = atomicAdd(&st.next_group, 1);
@@ -1185,8 +1229,7 @@ __device__ void ws_consumer(const InteractArgs& a, WsSmem<T>& sm, unsigned tid, 
             if (qa < nt)
                 chunk_pair<T::CAP, T::RB, 32 * T::W, Acc, KERNEL>(a, st.buf, st.tbl.staged, st.tbl.global,
                                                                   st.coarse_mask, st.d, sm.win, tid, mode,
-                                                                  first, qa, qa + 1 < nt, cy, cz, base, kp,
-                                                                  kself, nself);
+                                                                  first, qa, qa + 1 < nt, cy, cz, base, kp);
         }
         __syncwarp();
         bar_arrive(&st.empty);
@@ -1214,18 +1257,10 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
     }
     __syncthreads();
     if (sm.failed) return;
-    // the self pair's contribution (0 where it is excluded by identity)
-    float kself = KERNEL == KERNEL_GAUSSIAN ? ex2_approx(0.f) : 0.f;
-    uint32_t nself = 1u;
-    if constexpr (KERNEL == KERNEL_LOWFLOP) kself = 1.0f;
-    if constexpr (self_by_identity<KERNEL, Acc>()) {
-        kself = 0.f;
-        nself = 0u;
-    }
     if (warp == (unsigned)T::W)
         ws_producer<T>(a, sm, lane);
     else
-        ws_consumer<T, Acc, KERNEL>(a, sm, tid, lane, kself, nself);
+        ws_consumer<T, Acc, KERNEL>(a, sm, tid, lane);
 }
 
 // ---- direct interaction (no staging) ------------------------------------------
@@ -1407,16 +1442,6 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     for (int k = 0; k < G; ++k) ps[k / 2].to(r[k], (k & 1) != 0);
 }
 
-// The self pair's contribution, taken off at the end (0 where the pair test
-// excludes it by identity).
-template <class Acc, int KERNEL>
-__device__ __forceinline__ void self_terms(float& kself, uint32_t& nself)
-{
-    constexpr bool by_id = self_by_identity<KERNEL, Acc>();
-    kself = by_id ? 0.f : (KERNEL == KERNEL_LOWFLOP ? 1.0f : ex2_approx(0.f));
-    nself = by_id ? 0u : 1u;
-}
-
 // Slots ka and ka + 1 of P (either may be a sentinel or past the end).
 template <int WT, bool DENSE, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t (*win)[WT], unsigned col,
@@ -1446,22 +1471,19 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
     // X-row of one system; otherwise each runs alone (b repeating a)
     const bool together = has_b && sid1 == sid && axis_cell(t1.y, g.lo[1], g.inv_w[1], g.n[1]) == cy &&
                           axis_cell(t1.z, g.lo[2], g.inv_w[2], g.n[2]) == cz;
-    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
-    float kself;
-    uint32_t nself;
-    self_terms<Acc, KERNEL>(kself, nself);
+    const KParams kp = kparams(a, sid);
     {
         const float4 t[2] = {ta, together ? t1 : ta};
         const int cx[2] = {cxa, together ? cxb : cxa};
         Sums<Acc, KERNEL> r[2];
         direct_group<WT, 2, DENSE>(a, d, win, col, t, cx, cy, cz, kp, r);
-        store_out(a, __float_as_uint(ta.w), r[0], kself, nself);
-        if (together) store_out(a, __float_as_uint(t1.w), r[1], kself, nself);
+        store_out(a, __float_as_uint(ta.w), r[0]);
+        if (together) store_out(a, __float_as_uint(t1.w), r[1]);
     }
     if (has_b && !together) {
         const SysDesc& d1 = a.sy.sys[sid1];
         const Grid& g1 = d1.g;
-        const KParams kp1{a.kscale ? a.kscale[sid1] : a.kscale0, a.one, a.zero};
+        const KParams kp1 = kparams(a, sid1);
         const int cx1 = axis_cell(t1.x, g1.lo[0], g1.inv_w[0], g1.n[0]);
         const int cy1 = axis_cell(t1.y, g1.lo[1], g1.inv_w[1], g1.n[1]);
         const int cz1 = axis_cell(t1.z, g1.lo[2], g1.inv_w[2], g1.n[2]);
@@ -1469,7 +1491,7 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
         const int cx[2] = {cx1, cx1};
         Sums<Acc, KERNEL> r[2];
         direct_group<WT, 2, DENSE>(a, d1, win, col, t, cx, cy1, cz1, kp1, r);
-        store_out(a, __float_as_uint(t1.w), r[0], kself, nself);
+        store_out(a, __float_as_uint(t1.w), r[0]);
     }
 }
 
@@ -1573,15 +1595,12 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     for (int k = 0; k < 4; ++k) cx[k] = axis_cell(t[k].x, g.lo[0], g.inv_w[0], g.n[0]);
     const int cy = axis_cell(tf.y, g.lo[1], g.inv_w[1], g.n[1]);
     const int cz = axis_cell(tf.z, g.lo[2], g.inv_w[2], g.n[2]);
-    const KParams kp{a.kscale ? a.kscale[sid] : a.kscale0, a.one, a.zero};
-    float kself;
-    uint32_t nself;
-    self_terms<Acc, KERNEL>(kself, nself);
+    const KParams kp = kparams(a, sid);
     Sums<Acc, KERNEL> r[4];
     direct_group<DIRECT_THREADS, 4, false>(a, d, win, threadIdx.x, t, cx, cy, cz, kp, r);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (v[k]) store_out(a, __float_as_uint(t[k].w), r[k], kself, nself);
+        if (v[k]) store_out(a, __float_as_uint(t[k].w), r[k]);
 }
 
 template <class Acc, int KERNEL>
@@ -1612,6 +1631,8 @@ cudaError_t launch_ppnl_acc(const InteractArgs& a, cudaStream_t s)
         case KERNEL_LJ: return launch_dependent(k_interact_ppnl<Acc, KERNEL_LJ>, blocks, threads, 0, s, a);
         case KERNEL_LOWFLOP: return launch_dependent(k_interact_ppnl<Acc, KERNEL_LOWFLOP>, blocks, threads, 0, s, a);
         case KERNEL_HIGHFLOP: return launch_dependent(k_interact_ppnl<Acc, KERNEL_HIGHFLOP>, blocks, threads, 0, s, a);
+        case KERNEL_GAUSSIAN_FINE:
+            return launch_dependent(k_interact_ppnl<Acc, KERNEL_GAUSSIAN_FINE>, blocks, threads, 0, s, a);
         default: return launch_dependent(k_interact_ppnl<Acc, KERNEL_GAUSSIAN>, blocks, threads, 0, s, a);
     }
 }
@@ -1634,7 +1655,8 @@ template <class Acc>
 cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm, int num_sms,
                              cudaStream_t s)
 {
-    // the comparator kernels run on the direct kernels or the 128-thread shape
+    // the comparator kernels and the fine Gaussian run on the direct kernels
+    // or the 128-thread shape
     if (a.kernel != KERNEL_GAUSSIAN && tile != 5 && tile != 6) tile = 2;
     uint64_t grid = (uint64_t)num_sms * (uint64_t)(per_sm[tile] < 1 ? 1 : per_sm[tile]);
     if (grid > a.work) grid = a.work;
@@ -1655,6 +1677,11 @@ cudaError_t launch_tiled_acc(const InteractArgs& a, int tile, const int* per_sm,
             tile == 5   ? launch_direct_one<Acc, KERNEL_HIGHFLOP>(a, s)
             : tile == 6 ? launch_direct4_one<Acc, KERNEL_HIGHFLOP>(a, s)
                         : launch_tiled_one<TileL, Acc, KERNEL_HIGHFLOP>(a, g, s);
+            break;
+        case KERNEL_GAUSSIAN_FINE:
+            tile == 5   ? launch_direct_one<Acc, KERNEL_GAUSSIAN_FINE>(a, s)
+            : tile == 6 ? launch_direct4_one<Acc, KERNEL_GAUSSIAN_FINE>(a, s)
+                        : launch_tiled_one<TileL, Acc, KERNEL_GAUSSIAN_FINE>(a, g, s);
             break;
         default:
             switch (tile) {
@@ -1718,6 +1745,9 @@ cudaError_t tiled_occupancy_acc(int* per_sm)
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_LOWFLOP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_GAUSSIAN_FINE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_interact_tiled<TileL, Acc, KERNEL_HIGHFLOP>,

@@ -13,7 +13,7 @@
 //   pbase[S+1]      first particle of each system in the current step
 //   offsets[C+1]    exclusive scan of counts; offsets[C] = n
 //   scan_status[T]  decoupled-lookback tile descriptors (T = scan tiles)
-//   sys[S], cbase[S+1], wbase[S+1], kscale[S]   per-system constants
+//   sys[S], cbase[S+1], wbase[S+1], kscale[2S]  per-system constants
 //   cell[n_max]     cell of each input particle            (binning scratch)
 //   rank[n_max]     provisional slot inside its cell        (binning scratch)
 //   rec[n_max]      32-byte Rec per particle in unstable slot order (binning
@@ -236,12 +236,16 @@ cudaError_t launch_total_f64(const float* v, const Systems& sy, double* partial,
 cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uint32_t* rbase,
                               const SysDesc& d, uint32_t cells, uint32_t work, uint32_t rows, cudaStream_t s);
 
-// Per-system scale of the interaction kernel, written from launch parameters
-// (vals[s] for s < S) into kscale.
-cudaError_t launch_set_kscale(float* kscale, const float* vals, int S, cudaStream_t s);
+// Per-system scales of the interaction kernel, written from launch
+// parameters (vals[i] for i < count, count <= 2 MAX_SYSTEMS) into kscale.
+cudaError_t launch_set_kscale(float* kscale, const float* vals, int count, cudaStream_t s);
 
-// Interaction kernels (PI_KERNEL_* of include/pi.h).
-enum : int { KERNEL_GAUSSIAN = 0, KERNEL_LJ = 1, KERNEL_LOWFLOP = 2, KERNEL_HIGHFLOP = 3 };
+// Interaction kernels (PI_KERNEL_* of include/pi.h), and the Gaussian with
+// a compensated exponent that the host picks for short kernel lengths
+// (r_c^2 / h^2 > FINE_GAUSS_RATIO), where the plain FP32 exponent's rounding
+// would exceed the accuracy the sums are held to.
+enum : int { KERNEL_GAUSSIAN = 0, KERNEL_LJ = 1, KERNEL_LOWFLOP = 2, KERNEL_HIGHFLOP = 3, KERNEL_GAUSSIAN_FINE = 4 };
+constexpr double FINE_GAUSS_RATIO = 16.0;
 
 struct InteractArgs {
     Systems sy;
@@ -255,8 +259,11 @@ struct InteractArgs {
     uint32_t n;             // particles of all systems
     uint32_t np;            // entries of P: n plus ROW_PADS per X-row
     uint32_t work;          // work items (X-row segments) of all systems
-    const float* kscale;    // [S]: Gaussian K = 2^(r2 * kscale[s]); Lennard-Jones sigma^2
-    float kscale0;          // the scale when S == 1 (kscale may then be null)
+    const float* kscale;    // [2S]: scale t of system s at [s] (Gaussian K = 2^(r2 t), t =
+                            // -log2(e)/h^2 in FP32; Lennard-Jones sigma^2), the FP32
+                            // remainder of the FP64 scale at [S + s] (fine Gaussian)
+    float kscale0;          // the scale and remainder when S == 1 (kscale may then be null)
+    float kscale0_lo;
     int kernel;             // KERNEL_*
     float one, zero;        // 1 and 0, opaque to the compiler (high-FLOP kernel)
     float* S;

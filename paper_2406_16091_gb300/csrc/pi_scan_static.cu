@@ -42,23 +42,47 @@ static __device__ __align__(256) unsigned char g_scan_scratch[NOALLOC_BYTES];
 extern "C" pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, uint32_t* offsets,
                                             uint32_t* result, pi_stream stream)
 {
+    char msg[200];
     if (!counts || !offsets || C < 1) return PI_ERR_INVALID_ARG;
     if (C > NOALLOC_MAX_CELLS) {
-        char msg[160];
         std::snprintf(msg, sizeof msg,
                       "pi_scan_counts_noalloc: %lld cells exceed the fixed scratch limit of %lld",
                       (long long)C, (long long)NOALLOC_MAX_CELLS);
         pi::set_last_error_text(msg);
         return PI_ERR_CAPACITY;
     }
+    // the scan reads the counts and writes the offsets 16 bytes at a time
+    if ((((uintptr_t)counts | (uintptr_t)offsets) & 15u) != 0u || ((uintptr_t)result & 3u) != 0u) {
+        pi::set_last_error_text(
+            "pi_scan_counts_noalloc: counts and offsets must be 16-byte aligned, result 4-byte aligned");
+        return PI_ERR_INVALID_ARG;
+    }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PI_ERR_CUDA;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PI_ERR_CAPACITY;
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) {
+        std::snprintf(msg, sizeof msg, "pi_scan_counts_noalloc: cudaGetDevice: %s", cudaGetErrorName(ge));
+        pi::set_last_error_text(msg);
+        return PI_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        std::snprintf(msg, sizeof msg, "pi_scan_counts_noalloc: device %d is beyond the %d devices it serves", dev,
+                      NOALLOC_MAX_DEVICES);
+        pi::set_last_error_text(msg);
+        return PI_ERR_CAPACITY;
+    }
     // once per device, with that device current: the device address of the array
     std::call_once(g_setup_once[dev], [dev] {
         g_setup_err[dev] = cudaGetSymbolAddress(&g_scratch_addr[dev], g_scan_scratch);
     });
-    if (g_setup_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return PI_ERR_CUDA;
+    if (g_setup_err[dev] != cudaSuccess || !g_scratch_addr[dev]) {
+        // the failed look-up is kept: later calls on this device fail the same way
+        std::snprintf(msg, sizeof msg,
+                      "pi_scan_counts_noalloc: cudaGetSymbolAddress of the scratch array failed on device %d "
+                      "(%s); the failure is kept for this device",
+                      dev, cudaGetErrorName(g_setup_err[dev]));
+        pi::set_last_error_text(msg);
+        return PI_ERR_CUDA;
+    }
 
     cudaStream_t s = (cudaStream_t)stream;
     char* base = (char*)g_scratch_addr[dev];
@@ -69,16 +93,16 @@ extern "C" pi_status pi_scan_counts_noalloc(const uint32_t* counts, int64_t C, u
     // and the descriptors this call uses (a cleared descriptor reads as "not
     // ready", so one fixed epoch suffices)
     const size_t words = (sizeof(pi::Ctrl) + tiles * sizeof(unsigned long long)) / 4;
-    if (pi::launch_zero((uint32_t*)base, words, nullptr, nullptr, 0, s) != cudaSuccess) return PI_ERR_CUDA;
-    if (pi::launch_scan(counts, (uint32_t)C, offsets, status, ctrl, 1u, 1000000000ull, 0, s) !=
-        cudaSuccess)
+    cudaError_t e = pi::launch_zero((uint32_t*)base, words, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = pi::launch_scan(counts, (uint32_t)C, offsets, status, ctrl, 1u, 1000000000ull, 0, s);
+    if (e == cudaSuccess && result)
+        e = cudaMemcpyAsync(result, &ctrl->max_per_cell, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && result)
+        e = cudaMemcpyAsync(result + 1, &ctrl->error, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        std::snprintf(msg, sizeof msg, "pi_scan_counts_noalloc: launch: %s", cudaGetErrorName(e));
+        pi::set_last_error_text(msg);
         return PI_ERR_CUDA;
-    if (result) {
-        if (cudaMemcpyAsync(result, &ctrl->max_per_cell, sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                            s) != cudaSuccess ||
-            cudaMemcpyAsync(result + 1, &ctrl->error, sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                            s) != cudaSuccess)
-            return PI_ERR_CUDA;
     }
     return PI_OK;
 }

@@ -45,3 +45,11 @@ def test_workload_line_names_the_layout():
         assert cfg["workload"].startswith(name + ":")
         assert w.layout in cfg["workload"]
         assert cfg["n_particles"] == w.n and cfg["r_c"] == w.rc
+
+
+def test_binning_bytes_follow_the_algorithmic_formula():
+    """48 bytes per particle and 12 per cell: 103.8 MB at 2,097,152
+    particles in 64^3 cells; the figure with the P record is separate."""
+    n, C = 2097152, 64 ** 3
+    assert bench.binning_bytes(n, C) == 48 * n + 12 * C == 103_809_024
+    assert bench.binning_bytes_with_p(n, C) > bench.binning_bytes(n, C)

@@ -162,7 +162,7 @@ def _random_case(seed):
                    for a, l, h in zip((x, y, z), lo, hi))
     else:
         x, y, z = W.uniform(n, 500 + seed, lo, hi)
-    h = float(rc * rng.uniform(0.3, 1.2))
+    h = float(rc * rng.uniform(0.1, 1.2))
     return x, y, z, lo, hi, rc, h
 
 
@@ -178,7 +178,66 @@ def test_random_configurations(seed):
         g = run_gpu(x, y, z, lo, hi, rc, h, algo=algo, tile=tile, precision=prec, n_max=max(len(x), 1))
         check_binning(g, b)
         if len(x):
-            check_interaction(g, r)
+            check_interaction(g, r, rc=rc)
+
+
+# Short kernels (h a small fraction of r_c): every path excludes the self
+# pair by identity, so a particle's sum is never rounded at the size of
+# K(0) = 1; from r_c^2/h^2 > 16 on the Gaussian's exponent is compensated
+# (at h = r_c/4 the plain FP32 form runs, at r_c/8 and r_c/12 the fine one).
+SHORT_VARIANTS = [(B.PI_ALGO_TILED, 0, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 2, B.PI_PREC_FP32),
+                  (B.PI_ALGO_TILED, 5, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 6, B.PI_PREC_FP32),
+                  (B.PI_ALGO_PPNL, None, B.PI_PREC_FP32), (B.PI_ALGO_TILED, 5, B.PI_PREC_KAHAN),
+                  (B.PI_ALGO_TILED, 6, B.PI_PREC_KAHAN)]
+SHORT_CASES = {
+    "scale_ppc1": W.SCALE_VARIANTS[1],
+    "clustered_400000": W.scaled(W.CLUSTERED, 400000),
+}
+
+
+@pytest.mark.parametrize("hdiv", [4, 8])
+@pytest.mark.parametrize("name", list(SHORT_CASES))
+def test_short_kernel_lengths(name, hdiv):
+    w = SHORT_CASES[name]
+    x, y, z = w.positions()
+    h = w.rc / hdiv
+    b, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, h)
+    for algo, tile, prec in SHORT_VARIANTS:
+        g = run_gpu(x, y, z, w.lo, w.hi, w.rc, h, algo=algo, tile=tile, precision=prec)
+        check_binning(g, b)
+        check_interaction(g, r, rc=w.rc)
+
+
+@pytest.mark.parametrize("hdiv", [2, 4, 8, 12])
+def test_two_particles_near_the_cutoff(hdiv):
+    """Two particles 0.9 r_c apart: each sees the other alone, S = exp(-0.81
+    (r_c/h)^2) -- at h = r_c/12 below 2^-126, where FP32 flushes it to 0."""
+    rng = np.random.default_rng(hdiv)
+    rc = 1.0 / 16
+    for k in range(8):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        p0 = rng.uniform(0.2, 0.8, 3)
+        p1 = p0 + 0.9 * rc * u
+        x, y, z = (np.array([p0[i], p1[i]], np.float32) for i in range(3))
+        h = rc / hdiv
+        b, r = oracle_run(x, y, z, (0, 0, 0), (1, 1, 1), rc, h)
+        assert r.nbr.tolist() == [1, 1]
+        for algo, tile, prec in SHORT_VARIANTS:
+            g = run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), rc, h, algo=algo, tile=tile, precision=prec)
+            check_binning(g, b)
+            check_interaction(g, r, rc=rc)
+            if hdiv <= 8:
+                assert np.all(g["S"] > 0)
+
+
+def test_kernel_length_without_fp32_scale_is_rejected():
+    """h so small that -log2(e)/h^2 overflows FP32: refused on the host."""
+    x, y, z = W.uniform(100, 3)
+    with pytest.raises(B.PiError) as e:
+        run_gpu(x, y, z, (0, 0, 0), (1, 1, 1), 0.1, 1e-20)
+    assert e.value.status == B.PI_ERR_INVALID_ARG
+    assert "finite FP32 kernel scale" in B.last_error()
 
 
 def test_coincident_particles():
