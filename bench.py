@@ -61,6 +61,8 @@ def parse():
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
     p.add_argument("--max-slots", type=int, default=8, help="serving study: slots per capacity bucket")
+    p.add_argument("--binning", choices=["per_particle", "bucketed"], default="per_particle",
+                   help="binning path (PI_OPT_BINNING)")
     p.add_argument("--no-extras", action="store_true",
                    help="leave out the batched, serving and per-configuration records of the line")
     p.add_argument("--serving-jobs", type=int, default=1000,
@@ -239,6 +241,7 @@ def workload_config(w, args):
                         f"r_c={w.rc:.9g}, Gaussian K with h=r_c/2, outputs S, V and neighbour count",
             "n_particles": w.n, "cells": [w.cells_per_axis()] * 3, "r_c": w.rc, "h": w.h,
             "layout": w.layout, "algo": args.algo, "precision": args.precision,
+            "binning": getattr(args, "binning", "per_particle"),
             "parallelism": f"replicas x{args.gpus}",
             "l2": f"flushed before every timed step ({args.flush_mb} MB write)"}
 
@@ -273,6 +276,8 @@ def run_ours(args):
     B.pi_set_option(ctx, B.PI_OPT_ALGO, B.PI_ALGO_TILED if args.algo == "tiled" else B.PI_ALGO_PPNL)
     B.pi_set_option(ctx, B.PI_OPT_PRECISION,
                     B.PI_PREC_FP32 if args.precision == "fp32" else B.PI_PREC_KAHAN)
+    B.pi_set_option(ctx, B.PI_OPT_BINNING,
+                    B.PI_BIN_BUCKETED if args.binning == "bucketed" else B.PI_BIN_PER_PARTICLE)
     tx, ty, tz = (torch.from_numpy(a).to(dev) for a in (x, y, z))
     S, Vx, Vy, Vz = (torch.empty(n, device=dev) for _ in range(4))
     nb = torch.empty(n, dtype=torch.int32, device=dev)
@@ -467,9 +472,12 @@ def run_ours(args):
         roofline["frac_at_median_clock"] = achieved / (alu_peak * clocks["sm_mhz"] / sm_max)
     C = w.cells_per_axis() ** 3
     bin_bytes = binning_bytes(n, C)
+    bin_kernels = (["k_zero", "k_bucket_count", "k_scan", "k_bucket_scatter", "k_bucket_cells", "k_bucket_big"]
+                   if args.binning == "bucketed" else ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"])
     mean_bin = statistics.fmean(t_bin)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bin_traffic = recorded_traffic("binning", source_hash([os.path.join(src, "pi_bin.cu"),
+                                                          os.path.join(src, "pi_bucket.cu"),
                                                           os.path.join(src, "pi_internal.cuh")]))
     bin_dram = bin_traffic["dram_bytes_per_launch"] if bin_traffic else None
     binning = {"bound": "hbm", "achieved": bin_bytes / mean_bin / 1e9, "peak": hbm_peak,
@@ -479,7 +487,7 @@ def run_ours(args):
                "bytes_with_P_record": binning_bytes_with_p(n, C), "mean_us": 1e6 * mean_bin,
                "traffic": bin_dram,
                "traffic_over_algorithmic": bin_dram / bin_bytes if bin_dram else None,
-               "kernels": ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"]}
+               "kernels": bin_kernels}
 
     # the other parts of the metric and the other configurations, measured
     # after the timed region: batched systems, served jobs, per configuration

@@ -58,7 +58,10 @@ typedef enum {
     PI_ERR_NOT_BINNED = 4,  /* pi_interact before a successful pi_bin */
     PI_ERR_CUDA = 5,        /* a CUDA runtime call failed; see pi_last_error() */
     PI_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (device) */
-    PI_ERR_NOMEM = 7        /* device allocation failed */
+    PI_ERR_NOMEM = 7,       /* device allocation failed */
+    PI_ERR_CHECK = 8        /* debug builds (PI_CHECK): an index failed its bounds
+                               check and the access was skipped (device); the
+                               check's site is in pi_last_error() */
 } pi_status;
 
 /* Output order of pi_interact. */
@@ -103,9 +106,17 @@ enum {
      * full wave of shape 6 (4 x 640 per SM), shape 5 otherwise.
      * pi_autotune sets a shape from measurements.  Results do not depend on
      * it. */
-    PI_OPT_TILE = 6
+    PI_OPT_TILE = 6,
+    /* Binning: PI_BIN_PER_PARTICLE (default) takes one global atomic and
+     * one 32-byte provisional record per particle; PI_BIN_BUCKETED counts
+     * the particles per bucket of consecutive cells and ranks each bucket's
+     * cells in shared memory, when the bucket-by-chunk count matrix fits the
+     * context (up to about 8 M cells; the per-particle path otherwise).
+     * Results are the same bit for bit. */
+    PI_OPT_BINNING = 7
 };
 enum { PI_TILE_AUTO = -1 };
+enum { PI_BIN_PER_PARTICLE = 0, PI_BIN_BUCKETED = 1 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
 enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
 
@@ -273,18 +284,24 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
 
 /* Autotuner of the interaction for the data of the last pi_bin /
  * pi_batch_bin (Sec. 5 sizes its launches from M_C and the shared memory;
- * here the candidates are measured instead): runs the interaction (arguments as pi_batch_interact, h one
- * entry per system) once untimed and `reps` times timed (1 <= reps <= 100)
- * with each tile shape of the tiled algorithm (PI_OPT_TILE 0..6) and then
- * with PI_ALGO_PPNL, keeps the candidate with the smallest median time for
- * later calls (setting PI_OPT_ALGO and PI_OPT_TILE), and returns its index in
- * *chosen (0..6 = tile shape, 7 = PI_ALGO_PPNL) and the medians in ms[8]
- * (milliseconds; either pointer may be NULL).  The choice changes only the
- * speed: every tile shape sums each target's terms in the same order, so
- * their outputs are identical; PPNL's agree with them within the stated
- * tolerance.  Synchronises `stream`.  The output arrays hold the last run's
- * results.  Errors: those of pi_batch_interact, PI_ERR_INVALID_ARG,
- * PI_ERR_CUDA (the previous algorithm and shape are then kept). */
+ * here the candidates are measured instead): runs the interaction
+ * (arguments as pi_batch_interact, h one entry per system) once untimed and
+ * `reps` times timed (1 <= reps <= 100) with each tile shape of the tiled
+ * algorithm (PI_OPT_TILE 0..6), then with PI_ALGO_PPNL, and -- for a batch
+ * context -- with a shape per occupancy regime: the systems are grouped by
+ * mean particles per cell (below 4, 4 to 8, 8 and more), each group is
+ * timed alone with shapes 5 and 6 and takes the faster, and the resulting
+ * per-system plan (pi_batch_set_tiles) is timed as a whole.  The candidate
+ * with the smallest median time is kept for later calls (PI_OPT_ALGO,
+ * PI_OPT_TILE or the per-system plan); *chosen receives its index (0..6 =
+ * tile shape, 7 = PI_ALGO_PPNL, 8 = the per-regime plan) and ms[9] the
+ * medians in milliseconds (ms[8] = 0 for a single system); either pointer
+ * may be NULL.  The choice changes only the speed: every tile shape sums
+ * each target's terms in the same order, so their outputs are identical;
+ * PPNL's agree with them within the stated tolerance.  Synchronises
+ * `stream`.  The output arrays hold the results of the chosen
+ * configuration.  Errors: those of pi_batch_interact, PI_ERR_INVALID_ARG,
+ * PI_ERR_CUDA (the previous configuration is then kept). */
 pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                       uint32_t* nbr, int out_order, int reps, int32_t* chosen, float* ms,
                       pi_stream stream);
@@ -293,6 +310,22 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
  * any may be NULL).  No passage of the paper: library housekeeping. */
 pi_status pi_batch_info(const pi_ctx* ctx, int32_t* num_systems, int64_t* total_cells,
                         int64_t* total_n_max);
+
+/* Per-system tile shapes of a batch context (a shape per occupancy regime
+ * of the systems; Sec. 5 sizes its kernels per problem): tiles is a
+ * host array of num_systems entries, each 5 (two targets per thread) or 6
+ * (four targets per thread), or NULL to clear the plan.  Under a plan
+ * pi_batch_interact (with PI_ALGO_TILED) makes one launch of each shape in
+ * use, over the P ranges of its systems; outputs do not depend on the
+ * shapes.  The ranges are written into the context by a small launch on the
+ * interaction's stream whenever the plan or the particle counts change.
+ * pi_autotune may set a plan.  Host-side only.  Errors: PI_ERR_INVALID_ARG. */
+pi_status pi_batch_set_tiles(pi_ctx* ctx, const int32_t* tiles);
+
+/* The per-system tile shapes in use into tiles (host array of num_systems):
+ * 5 or 6 under a plan, -1 for every system without one.  No passage of the
+ * paper: library housekeeping. */
+pi_status pi_batch_tiles(const pi_ctx* ctx, int32_t* tiles);
 
 /* Grid dimensions (nx, ny, nz) of one system into dims (host array of 3):
  * n_d = max(1, floor((hi_d - lo_d) / r_c)), the grid of cells at least r_c
@@ -335,8 +368,8 @@ pi_status pi_copy_binned(const pi_ctx* ctx, uint32_t* counts, uint32_t* offsets,
 pi_status pi_total_f64(pi_ctx* ctx, const float* v, double* out, pi_stream stream);
 
 /* Synchronises `stream`, then returns the device-side status of the work
- * enqueued so far (PI_ERR_TIMEOUT, PI_ERR_OUT_OF_BOX, PI_ERR_CAPACITY or
- * PI_OK) and, if max_per_cell is not NULL, M_C of the last pi_bin (the
+ * enqueued so far (PI_ERR_CHECK in a debug build, PI_ERR_TIMEOUT,
+ * PI_ERR_OUT_OF_BOX, PI_ERR_CAPACITY or PI_OK) and, if max_per_cell is not NULL, M_C of the last pi_bin (the
  * largest cell count, which Sec. 5.1 uses to size its shared memory).  The
  * status check itself has no passage in the paper: library housekeeping. */
 pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell);

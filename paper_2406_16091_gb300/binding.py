@@ -22,6 +22,7 @@ PI_ERR_NOT_BINNED = 4
 PI_ERR_CUDA = 5
 PI_ERR_TIMEOUT = 6
 PI_ERR_NOMEM = 7
+PI_ERR_CHECK = 8
 
 PI_ORDER_SORTED = 0
 PI_ORDER_ORIGINAL = 1
@@ -32,8 +33,12 @@ PI_OPT_WAIT_LIMIT_NS = 3
 PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
+PI_OPT_BINNING = 7
+PI_BIN_PER_PARTICLE = 0  # one global atomic and one 32-byte record per particle (default)
+PI_BIN_BUCKETED = 1  # buckets of cells ranked in shared memory, when they fit
 PI_NUM_TILES = 7  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_AUTOTUNE_PPNL = PI_NUM_TILES  # pi_autotune's index of PI_ALGO_PPNL
+PI_AUTOTUNE_REGIMES = PI_NUM_TILES + 1  # pi_autotune's index of the per-regime plan
 PI_TILE_AUTO = -1  # PI_OPT_TILE default: shape by mean occupancy
 PI_KERNEL_GAUSSIAN = 0
 PI_KERNEL_LJ = 1
@@ -68,7 +73,7 @@ class PiError(RuntimeError):
         self.status = status
         msg = f"{where}: {status_str(status)} ({status})"
         extra = last_error()
-        if status == PI_ERR_CUDA and extra:
+        if status in (PI_ERR_CUDA, PI_ERR_CHECK) and extra:
             msg += f": {extra}"
         super().__init__(msg)
 
@@ -94,6 +99,8 @@ def load():
         "pi_batch_interact": ([P, P, P, P, P, P, P, i32, P], i32),
         "pi_batch_info": ([P, P, P, P], i32),
         "pi_batch_grid": ([P, i32, P], i32),
+        "pi_batch_set_tiles": ([P, P], i32),
+        "pi_batch_tiles": ([P, P], i32),
         "pi_destroy": ([P], i32),
         "pi_reconfigure": ([P, ctypes.POINTER(PiBox), f32, P], i32),
         "pi_bin": ([P, P, P, P, i64, P], i32),
@@ -209,6 +216,22 @@ def pi_batch_grid(ctx, system: int):
     dims = (ctypes.c_int32 * 3)()
     _check(load().pi_batch_grid(ctx, int(system), ctypes.cast(dims, ctypes.c_void_p)), "pi_batch_grid")
     return tuple(dims)
+
+
+def pi_batch_set_tiles(ctx, tiles) -> None:
+    """Per-system tile shapes (5 or 6 each) of a batch context; None clears."""
+    if tiles is None:
+        _check(load().pi_batch_set_tiles(ctx, None), "pi_batch_set_tiles")
+        return
+    arr = (ctypes.c_int32 * len(tiles))(*[int(t) for t in tiles])
+    _check(load().pi_batch_set_tiles(ctx, ctypes.cast(arr, ctypes.c_void_p)), "pi_batch_set_tiles")
+
+
+def pi_batch_tiles(ctx, num_systems: int):
+    """The per-system tile shapes in use (-1 each without a plan)."""
+    arr = (ctypes.c_int32 * int(num_systems))()
+    _check(load().pi_batch_tiles(ctx, ctypes.cast(arr, ctypes.c_void_p)), "pi_batch_tiles")
+    return list(arr)
 
 
 def pi_reconfigure(ctx, lo, hi, r_c: float, stream=None) -> None:
@@ -349,12 +372,13 @@ def pi_scan_counts_noalloc(counts, C: int, offsets, result=None, stream=None) ->
 
 def pi_autotune(ctx, h, S, Vx, Vy, Vz, nbr=None, out_order: int = PI_ORDER_SORTED, reps: int = 3,
                 stream=None):
-    """Times every tile shape and PI_ALGO_PPNL on the binned data, keeps the
-    fastest.  Returns (chosen index: shape 0..6 or PI_AUTOTUNE_PPNL,
-    [median ms per candidate])."""
+    """Times every tile shape, PI_ALGO_PPNL and (batches) a shape per
+    occupancy regime on the binned data, keeps the fastest.  Returns (chosen
+    index: shape 0..6, PI_AUTOTUNE_PPNL or PI_AUTOTUNE_REGIMES, [median ms
+    per candidate])."""
     arr = (ctypes.c_float * len(h))(*[float(v) for v in h])
     chosen = ctypes.c_int32()
-    ms = (ctypes.c_float * (PI_NUM_TILES + 1))()
+    ms = (ctypes.c_float * (PI_NUM_TILES + 2))()
     _check(load().pi_autotune(ctx, ctypes.cast(arr, ctypes.c_void_p), _ptr(S), _ptr(Vx), _ptr(Vy),
                               _ptr(Vz), _ptr(nbr), int(out_order), int(reps), ctypes.byref(chosen),
                               ctypes.cast(ms, ctypes.c_void_p), _stream(stream)), "pi_autotune")

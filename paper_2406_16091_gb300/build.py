@@ -47,8 +47,21 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def _flags_stamp(extra_flags) -> str:
+    return " ".join(NVCC_FLAGS + list(extra_flags))
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
+    """Compiles libpi.so.  The environment variable PI_CHECK=1 adds
+    -DPI_CHECK: the debug build whose kernels bounds-check their indexed
+    accesses and report a failed check as PI_ERR_CHECK instead of
+    faulting.  A change of flags forces a rebuild."""
+    extra_flags = list(extra_flags)
+    if os.environ.get("PI_CHECK", "0") not in ("", "0") and "-DPI_CHECK" not in extra_flags:
+        extra_flags.append("-DPI_CHECK")
+    stamp = os.path.join(BUILD, "flags.txt")
+    same_flags = os.path.exists(stamp) and open(stamp).read() == _flags_stamp(extra_flags)
+    if not force and same_flags and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
@@ -71,6 +84,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(_flags_stamp(extra_flags))
     return LIB
 
 

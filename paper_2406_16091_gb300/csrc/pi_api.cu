@@ -79,6 +79,21 @@ struct pi_ctx {
     int tile;                       // tile shape of the tiled kernel (0 .. NUM_TILES - 1, or PI_TILE_AUTO)
     uint64_t wait_limit_ns;
     int withhold_scan;
+
+    int binning;                    // PI_BIN_* (PI_OPT_BINNING)
+    // bucketed binning: count matrix, its scan, overflow buckets
+    uint32_t* mat;
+    uint32_t* mat_base;
+    uint2* ovf_list;
+    size_t mat_cap;                 // entries of mat (mat_base has one more)
+
+    // per-system tile shapes of a batch (empty: every system runs `tile`);
+    // entries 5 or 6, or 0 for a system left out (autotuner trials only)
+    std::vector<int> sys_tile;
+    // device range lists of the per-system shapes: [0, 2S) the ranges of
+    // shape 5, [2S, 4S) of shape 6, [4S, 5S) and [5S, 6S) their first blocks
+    uint32_t* d_ranges;
+    std::vector<uint32_t> ranges_h;  // what was last written there
 };
 
 namespace {
@@ -222,6 +237,7 @@ const char* pi_status_str(pi_status s)
         case PI_ERR_CUDA: return "CUDA error";
         case PI_ERR_TIMEOUT: return "device-side wait timed out";
         case PI_ERR_NOMEM: return "device allocation failed";
+        case PI_ERR_CHECK: return "bounds check failed (debug build)";
     }
     return "unknown status";
 }
@@ -287,6 +303,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->kernel = PI_KERNEL_GAUSSIAN;
     c->tile = PI_TILE_AUTO;
     c->wait_limit_ns = 1000000000ull;
+    c->binning = PI_BIN_PER_PARTICLE;
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -299,7 +316,12 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     }
 
     const size_t nm = (size_t)N;
-    const size_t tiles = ((size_t)C + 1 + pi::SCAN_TILE - 1) / pi::SCAN_TILE;
+    // the bucketed binning's count matrix: at most BUCKET_MAX buckets of at
+    // least 32 cells by the chunks of n_max particles, capped at 4 M entries
+    const size_t buckets_max = std::min<size_t>(pi::BUCKET_MAX, ((size_t)C + 31) / 32);
+    const size_t chunks_max = std::max<size_t>(1, (nm + pi::BUCKET_CHUNK - 1) / pi::BUCKET_CHUNK);
+    const size_t mat_cap = std::min<size_t>((size_t)4 << 20, buckets_max * chunks_max + 1);
+    const size_t tiles = (std::max<size_t>((size_t)C, mat_cap) + 1 + pi::SCAN_TILE - 1) / pi::SCAN_TILE;
     Carver k;
     const size_t o_ctrl = k.take<Ctrl>(1);
     const size_t o_counts = k.take<uint32_t>((size_t)C + 4);
@@ -313,6 +335,10 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     const size_t o_rbase = k.take<uint32_t>((size_t)S + 1);
     const size_t o_kscale = k.take<float>(2 * (size_t)S);
     const size_t o_partial = k.take<double>((size_t)S * pi::TOTAL_PARTS);
+    const size_t o_ranges = k.take<uint32_t>(6 * (size_t)S);
+    const size_t o_mat = k.take<uint32_t>(mat_cap);
+    const size_t o_mat_base = k.take<uint32_t>(mat_cap + 1);
+    const size_t o_ovf = k.take<uint2>(pi::BUCKET_MAX);
     const size_t o_cell = k.take<uint32_t>(nm + 4);
     const size_t o_rank = k.take<uint32_t>(nm + 4);
     const size_t o_rec = k.take<Rec>(nm + 4);
@@ -344,6 +370,11 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->d_rbase = (uint32_t*)(base + o_rbase);
     c->d_kscale = (float*)(base + o_kscale);
     c->d_partial = (double*)(base + o_partial);
+    c->d_ranges = (uint32_t*)(base + o_ranges);
+    c->mat = (uint32_t*)(base + o_mat);
+    c->mat_base = (uint32_t*)(base + o_mat_base);
+    c->ovf_list = (uint2*)(base + o_ovf);
+    c->mat_cap = mat_cap;
     c->cell = (uint32_t*)(base + o_cell);
     c->rank = (uint32_t*)(base + o_rank);
     c->rec = (Rec*)(base + o_rec);
@@ -446,6 +477,26 @@ pi_status pi_batch_grid(const pi_ctx* ctx, int32_t system, int32_t dims[3])
 
 pi_status pi_grid(const pi_ctx* ctx, int32_t dims[3]) { return pi_batch_grid(ctx, 0, dims); }
 
+pi_status pi_batch_set_tiles(pi_ctx* ctx, const int32_t* tiles)
+{
+    if (!ctx) return PI_ERR_INVALID_ARG;
+    if (!tiles) {
+        ctx->sys_tile.clear();
+        return PI_OK;
+    }
+    for (int s = 0; s < ctx->S; ++s)
+        if (tiles[s] != 5 && tiles[s] != 6) return PI_ERR_INVALID_ARG;
+    ctx->sys_tile.assign(tiles, tiles + ctx->S);
+    return PI_OK;
+}
+
+pi_status pi_batch_tiles(const pi_ctx* ctx, int32_t* tiles)
+{
+    if (!ctx || !tiles) return PI_ERR_INVALID_ARG;
+    for (int s = 0; s < ctx->S; ++s) tiles[s] = ctx->sys_tile.empty() ? -1 : ctx->sys_tile[s];
+    return PI_OK;
+}
+
 pi_status pi_binned(const pi_ctx* ctx, const uint32_t** counts, const uint32_t** offsets,
                     const uint32_t** perm, const float** sx, const float** sy, const float** sz)
 {
@@ -504,6 +555,10 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
             if (value < PI_TILE_AUTO || value >= pi::NUM_TILES) return PI_ERR_INVALID_ARG;
             ctx->tile = (int)value;
             return PI_OK;
+        case PI_OPT_BINNING:
+            if (value != PI_BIN_PER_PARTICLE && value != PI_BIN_BUCKETED) return PI_ERR_INVALID_ARG;
+            ctx->binning = (int)value;
+            return PI_OK;
         case PI_OPT_KERNEL:
             if (value < PI_KERNEL_GAUSSIAN || value > PI_KERNEL_HIGHFLOP) return PI_ERR_INVALID_ARG;
             ctx->kernel = (int)value;
@@ -543,7 +598,34 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
     const uint32_t C = (uint32_t)ctx->C;
     pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, ctx->S};
 
-    // control block, counts and xbins are one contiguous zeroed prefix of the
+    pi::BucketPlan plan;
+    if (ctx->binning == PI_BIN_BUCKETED && pi::bucket_plan(nn, C, ctx->mat_cap, plan)) {
+        // bucketed: count per chunk and bucket, scan the count matrix,
+        // scatter to buckets, rank each bucket's cells in shared memory (and
+        // the buckets too large for it grid-wide); every cell's count,
+        // offset and sub-bin word is written, so only the control block is
+        // cleared
+        float4* rec = reinterpret_cast<float4*>(ctx->rec);
+        float4* rec2 = rec + ctx->n_max_total;
+        PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, sizeof(Ctrl) / 4, ctx->pbase, ctx->pbase_h.data(), ctx->S + 1,
+                               s));
+        PI_TRY(pi::launch_bucket_count(x, y, z, nn, sy, plan, ctx->mat, ctx->ctrl, s));
+        PI_TRY(pi::launch_scan(ctx->mat, plan.B * plan.chunks, ctx->mat_base, ctx->scan_status, ctx->ctrl,
+                               ctx->epoch, ctx->wait_limit_ns, ctx->withhold_scan, s, 0));
+        PI_TRY(pi::launch_bucket_scatter(x, y, z, nn, sy, plan, ctx->mat_base, rec, ctx->ctrl, s));
+        PI_TRY(pi::launch_bucket_cells(rec, nn, sy, plan, ctx->mat_base, ctx->counts, ctx->offsets, ctx->perm,
+                                       ctx->sx, ctx->sy, ctx->sz, ctx->P, ctx->xbins, rec2, ctx->ovf_list,
+                                       ctx->ctrl, s));
+        PI_TRY(pi::launch_bucket_big(rec2, nn, sy, plan, ctx->offsets, ctx->perm, ctx->sx, ctx->sy, ctx->sz, ctx->P,
+                                     ctx->xbins, ctx->ovf_list, ctx->ctrl, ctx->num_sms, s));
+        ctx->launches += 6;
+        ctx->n = total;
+        ctx->binned = 1;
+        return PI_OK;
+    }
+
+    // per particle: control block, counts and xbins are one contiguous
+    // zeroed prefix of the
     // arena; the same launch writes this step's particle bases
     const size_t zero_words = ((char*)(ctx->xbins + C) - (char*)ctx->ctrl + 3) / 4;
     PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, zero_words, ctx->pbase, ctx->pbase_h.data(),
@@ -577,6 +659,85 @@ pi_status pi_bin(pi_ctx* ctx, const float* x, const float* y, const float* z, in
     if (ctx->S != 1) return PI_ERR_INVALID_ARG;
     return pi_batch_bin(ctx, x, y, z, &n, stream);
 }
+
+}  // extern "C"
+
+namespace {
+
+// The P ranges (row pads included) of the systems whose shape in
+// ctx->sys_tile is `tile`, merged where consecutive systems share it, with
+// the first block of each range for groups of `per` slots; returns the
+// blocks of the list.  Systems without particles store nothing and are
+// left out.
+unsigned plan_ranges(const pi_ctx* ctx, int tile, uint32_t per, uint32_t* words, uint32_t* rblock, int& nr)
+{
+    nr = 0;
+    for (int s = 0; s < ctx->S; ++s) {
+        if (ctx->sys_tile[s] != tile || ctx->pbase_h[s + 1] == ctx->pbase_h[s]) continue;
+        const uint32_t b = ctx->pbase_h[s] + pi::ROW_PADS * ctx->rbase[s];
+        const uint32_t e = ctx->pbase_h[s + 1] + pi::ROW_PADS * ctx->rbase[s + 1];
+        if (nr > 0 && words[2 * nr - 1] == b) {
+            words[2 * nr - 1] = e;
+        } else {
+            words[2 * nr] = b;
+            words[2 * nr + 1] = e;
+            ++nr;
+        }
+    }
+    unsigned blocks = 0;
+    const uint32_t span = per * (uint32_t)pi::DIRECT_BLOCK;
+    for (int r = 0; r < nr; ++r) {
+        rblock[r] = blocks;
+        blocks += (words[2 * r + 1] - words[2 * r] + span - 1) / span;
+    }
+    return blocks;
+}
+
+// The interaction of a batch under a per-system shape plan: one launch of
+// each direct shape that some system uses, over its systems' P ranges.
+pi_status launch_plan(pi_ctx* ctx, pi::InteractArgs a, bool kahan, cudaStream_t st, int* launched)
+{
+    const size_t S = (size_t)ctx->S;
+    std::vector<uint32_t> w(6 * S, 0u);
+    int nr5 = 0, nr6 = 0;
+    const unsigned b5 = plan_ranges(ctx, 5, 2u, w.data(), w.data() + 4 * S, nr5);
+    const unsigned b6 = plan_ranges(ctx, 6, 4u, w.data() + 2 * S, w.data() + 5 * S, nr6);
+    if (w != ctx->ranges_h) {
+        PI_TRY(pi::launch_write_words(ctx->d_ranges, w.data(), w.size(), st));
+        *launched += (int)((w.size() + 4095) / 4096);
+        ctx->ranges_h = w;
+    }
+    cudaError_t e = cudaSuccess;
+    if (nr5 > 0) {
+        a.ranges = reinterpret_cast<const uint2*>(ctx->d_ranges);
+        a.rblock = ctx->d_ranges + 4 * S;
+        a.nranges = nr5;
+        a.range_blocks = b5;
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], 5, st, launched);
+    }
+    if (e == cudaSuccess && nr6 > 0) {
+        a.ranges = reinterpret_cast<const uint2*>(ctx->d_ranges + 2 * S);
+        a.rblock = ctx->d_ranges + 5 * S;
+        a.nranges = nr6;
+        a.range_blocks = b6;
+        e = pi::launch_interact_tiled(a, kahan, ctx->num_sms, ctx->tiled_per_sm[kahan ? 1 : 0], 6, st, launched);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pi_interact: launch");
+    return PI_OK;
+}
+
+// Occupancy regimes of the per-system autotuning: mean particles per cell
+// below 4, below 8, and from 8 on (the shapes' crossover is near 8).
+int occupancy_regime(const pi_ctx* ctx, int s)
+{
+    const double cells = (double)ctx->cbase[s + 1] - (double)ctx->cbase[s];
+    const double q = (double)(ctx->pbase_h[s + 1] - ctx->pbase_h[s]) / (cells > 0 ? cells : 1.0);
+    return q < 4.0 ? 0 : (q < 8.0 ? 1 : 2);
+}
+
+}  // namespace
+
+extern "C" {
 
 pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, float* Vy, float* Vz,
                             uint32_t* nbr, int out_order, pi_stream stream)
@@ -656,6 +817,11 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     const bool kahan = ctx->precision == PI_PREC_KAHAN;
     if (ctx->algo == PI_ALGO_PPNL) {
         e = pi::launch_interact_ppnl(a, kahan, ctx->num_sms, st, &launched);
+    } else if (!ctx->sys_tile.empty()) {
+        const pi_status ps = launch_plan(ctx, a, kahan, st, &launched);
+        ctx->launches += (uint64_t)launched;
+        ctx->tiled_seq += 1;
+        return ps;
     } else {
         // PI_TILE_AUTO: four targets per thread for the plain Gaussian and
         // low-FLOP sums from 8 particles per cell on average (measured
@@ -692,6 +858,7 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_autotune: set device");
     cudaStream_t st = (cudaStream_t)stream;
     const int saved_algo = ctx->algo, saved_tile = ctx->tile;
+    const std::vector<int> saved_plan = ctx->sys_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PI_TRY(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -699,15 +866,10 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
         cudaEventDestroy(e0);
         return cuda_fail(ce, "pi_autotune: event");
     }
-    // candidates: every tile shape of the tiled algorithm, then Alg. 1
-    constexpr int PPNL = pi::NUM_TILES;
-    float best = 0.f;
-    int best_c = -1;
     pi_status result = PI_OK;
-    for (int t = 0; t <= PPNL && result == PI_OK; ++t) {
-        ctx->algo = t == PPNL ? PI_ALGO_PPNL : PI_ALGO_TILED;
-        if (t < PPNL) ctx->tile = t;
-        // one untimed run, then the timed ones; the median counts
+    // median milliseconds of the interaction as the context stands: one
+    // untimed run, then `reps` timed ones
+    auto median_ms = [&](float& med) {
         result = pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr, out_order, stream);
         std::vector<float> times;
         for (int r = 0; r < reps && result == PI_OK; ++r) {
@@ -720,13 +882,59 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
             if (ce != cudaSuccess && result == PI_OK) result = cuda_fail(ce, "pi_autotune: timing");
             times.push_back(m);
         }
-        if (result != PI_OK) break;
+        if (result != PI_OK) return false;
         std::sort(times.begin(), times.end());
-        const float med = times[times.size() / 2];
+        med = times[times.size() / 2];
+        return true;
+    };
+    // candidates: every tile shape of the tiled algorithm, then Alg. 1, then
+    // (batches) a shape per occupancy regime
+    constexpr int PPNL = pi::NUM_TILES, REGIMES = pi::NUM_TILES + 1;
+    float best = 0.f;
+    int best_c = -1;
+    ctx->sys_tile.clear();
+    for (int t = 0; t <= PPNL && result == PI_OK; ++t) {
+        ctx->algo = t == PPNL ? PI_ALGO_PPNL : PI_ALGO_TILED;
+        if (t < PPNL) ctx->tile = t;
+        float med = 0.f;
+        if (!median_ms(med)) break;
         if (ms) ms[t] = med;
         if (best_c < 0 || med < best) {
             best = med;
             best_c = t;
+        }
+    }
+    if (ms) ms[REGIMES] = 0.f;
+    std::vector<int> plan;
+    if (result == PI_OK && ctx->S > 1) {
+        // per regime, the faster direct shape on its systems alone
+        ctx->algo = PI_ALGO_TILED;
+        plan.assign(ctx->S, 0);
+        for (int g = 0; g < 3 && result == PI_OK; ++g) {
+            std::vector<int> trial(ctx->S, 0);
+            bool any = false;
+            for (int s = 0; s < ctx->S; ++s)
+                if (occupancy_regime(ctx, s) == g && ctx->pbase_h[s + 1] > ctx->pbase_h[s]) any = true;
+            if (!any) continue;
+            float tm[2] = {0.f, 0.f};
+            for (int k = 0; k < 2 && result == PI_OK; ++k) {
+                for (int s = 0; s < ctx->S; ++s) trial[s] = occupancy_regime(ctx, s) == g ? 5 + k : 0;
+                ctx->sys_tile = trial;
+                median_ms(tm[k]);
+            }
+            for (int s = 0; s < ctx->S; ++s)
+                if (occupancy_regime(ctx, s) == g) plan[s] = tm[1] < tm[0] ? 6 : 5;
+        }
+        for (int s = 0; s < ctx->S; ++s)
+            if (plan[s] == 0) plan[s] = 5;  // systems without particles
+        float med = 0.f;
+        ctx->sys_tile = plan;
+        if (result == PI_OK && median_ms(med)) {
+            if (ms) ms[REGIMES] = med;
+            if (med < best) {
+                best = med;
+                best_c = REGIMES;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -734,12 +942,19 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
     if (result != PI_OK || best_c < 0) {
         ctx->algo = saved_algo;
         ctx->tile = saved_tile;
+        ctx->sys_tile = saved_plan;
         return result;
     }
     ctx->algo = best_c == PPNL ? PI_ALGO_PPNL : PI_ALGO_TILED;
-    ctx->tile = best_c == PPNL ? saved_tile : best_c;
+    ctx->tile = (best_c == PPNL || best_c == REGIMES) ? saved_tile : best_c;
+    if (best_c == REGIMES)
+        ctx->sys_tile = plan;
+    else
+        ctx->sys_tile.clear();
     if (chosen) *chosen = best_c;
-    return result;
+    // the outputs of the chosen configuration (the last trial may have left
+    // some systems out)
+    return pi_batch_interact(ctx, h, S, Vx, Vy, Vz, nbr, out_order, stream);
 }
 
 pi_status pi_interact(pi_ctx* ctx, float h, float* S, float* Vx, float* Vy, float* Vz,
@@ -773,6 +988,11 @@ pi_status pi_sync_status(pi_ctx* ctx, pi_stream stream, uint32_t* max_per_cell)
     Ctrl h{};
     PI_TRY(cudaMemcpy(&h, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     if (max_per_cell) *max_per_cell = h.max_per_cell;
+    if (h.error & pi::ERR_CHECK) {
+        std::snprintf(g_last_error, sizeof g_last_error, "bounds check failed at site %u (see CheckSite)",
+                      h.check_site);
+        return PI_ERR_CHECK;
+    }
     if (h.error & pi::ERR_TIMEOUT) return PI_ERR_TIMEOUT;
     if (h.error & pi::ERR_OUT_OF_BOX) return PI_ERR_OUT_OF_BOX;
     if (h.error & pi::ERR_CAPACITY) return PI_ERR_CAPACITY;

@@ -16,6 +16,7 @@
 //                interaction reads, and each cell's x-sub-bin starts
 //
 // All kernels are HBM- or L2-bound integer work; none uses tensor cores.
+#include <algorithm>
 #include <mutex>
 
 #include "pi_internal.cuh"
@@ -106,6 +107,11 @@ __global__ void __launch_bounds__(256) k_hist(const float* __restrict__ x,
             cell[j] = cell_of(px[j], py[j], pz[j], d.g, ok) + d.cell_base;
             all_ok &= ok | !valid[j];
         }
+#ifdef PI_CHECK
+        const uint32_t c_all = __ldg(sy.cbase + sy.S);
+#pragma unroll
+        for (int j = 0; j < HP; ++j) valid[j] = valid[j] && PI_BOUNDS(ctrl, cell[j], c_all, CS_HIST_COUNTS);
+#endif
 #pragma unroll
         for (int j = 0; j < HP; ++j) rank[j] = valid[j] ? atomicAdd(&counts[cell[j]], 1u) : 0u;
         if (full) {
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
                                                        uint32_t* __restrict__ offsets,
                                                        unsigned long long* __restrict__ status,
                                                        Ctrl* __restrict__ ctrl, uint32_t epoch,
-                                                       uint64_t wait_limit_ns, int withhold_first)
+                                                       uint64_t wait_limit_ns, int withhold_first, int track_max)
 {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_warp_sum[SCAN_THREADS / 32];
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t items = (uint64_t)C + 1;  // item C is a zero count -> offsets[C] = total
+    if (!PI_BOUNDS(ctrl, tile, (items + SCAN_TILE - 1) / SCAN_TILE, CS_SCAN_TILE)) return;
     const uint64_t my0 = (uint64_t)tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
 
     uint32_t v[SCAN_ITEMS];
@@ -261,7 +268,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
         }
         if (lane == 0) {
             s_prefix = prefix;
-            if (tile_max) atomicMax(&ctrl->max_per_cell, tile_max);
+            if (tile_max && track_max) atomicMax(&ctrl->max_per_cell, tile_max);
         }
     }
     __syncthreads();
@@ -306,17 +313,10 @@ __device__ __forceinline__ Rec load_rec(const Rec* src)
 }
 
 // The x-sub-bin thermometer of a particle at x in cell c_local of grid g
-// (see Rec): sub-bin = clamp(floor((x - lo) * XSUB * inv_w) - XSUB * cx, 0,
-// XSUB - 1), monotone in x along an X-row.
+// (see Rec and x_sub_bin).
 __device__ __forceinline__ uint2 sub_bin_thermometer(float x, uint32_t c_local, const Grid& g)
 {
-    static_assert(XSUB == 8, "the thermometer has 7 one-byte counts");
-    const float invs = g.inv_w[0] * (float)XSUB;
-    const int cxs = XSUB * (int)(c_local % (uint32_t)g.n[0]);
-    const int sb = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
-    // bytes sb .. 6 are 1 (byte b - 1 counts "sub-bin < b")
-    const unsigned long long t = 0x01010101010101ull & (~0ull << (8 * sb));
-    return make_uint2((uint32_t)t, (uint32_t)(t >> 32));
+    return thermometer(x_sub_bin(x, c_local, g));
 }
 
 // a4, first half: each particle to its provisional slot offsets[cell] +
@@ -379,6 +379,11 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
         // the cell's range; the test against n only keeps a corrupted rank
         // from writing outside the records
         uint32_t lo[4];
+#ifdef PI_CHECK
+        const uint32_t c_all = __ldg(sy.cbase + sy.S);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) valid[j] = valid[j] && PI_BOUNDS(ctrl, c[j], c_all, CS_SCATTER_REC);
+#endif
 #pragma unroll
         for (int j = 0; j < 4; ++j) lo[j] = valid[j] ? offsets[c[j]] : 0u;
 #pragma unroll
@@ -431,6 +436,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         const SysDesc& d = sy.sys[sid];
         const uint32_t end_cell = d.cell_base + (r - d.row_base + 1u) * (uint32_t)d.g.n[0];
         const uint32_t pos = offsets[end_cell] + ROW_PADS * r;
+        if (!PI_BOUNDS(ctrl, pos + ROW_PADS - 1u, (uint64_t)n + ROW_PADS * (uint64_t)rows, CS_STAB_OUT)) continue;
 #pragma unroll
         for (int k = 0; k < ROW_PADS; ++k)
             P[pos + k] = make_float4(1e18f, 1e18f, 1e18f, __uint_as_float(0xffffffffu));
@@ -441,6 +447,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         if (i >= n || c >= C) { bad = true; continue; }
         const uint32_t s0 = offsets[c], s1 = offsets[c + 1];
         if (k < s0 || k >= s1) { bad = true; continue; }
+        if (!PI_BOUNDS(ctrl, s1 - 1u, n, CS_STAB_MEMBER)) continue;
         // stable rank, x-rank and the sum of the members' sub-bin
         // thermometers (byte b - 1 = members whose sub-bin is < b)
         uint32_t r = 0, xr = 0, lt_lo = 0, lt_hi = 0;
@@ -454,6 +461,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
             lt_hi += m.w;
         }
         const uint32_t dst = s0 + r;
+        if (!PI_BOUNDS(ctrl, dst, n, CS_STAB_OUT)) continue;
         perm[dst] = i;
         sx[dst] = me.x;
         sy_out[dst] = me.y;
@@ -461,6 +469,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
         const int sid = sy.S == 1 ? 0 : find_system(sy.cbase, sy.S, c);
         const SysDesc& d = sy.sys[sid];
         const uint32_t row = d.row_base + (c - d.cell_base) / (uint32_t)d.g.n[0];
+        if (!PI_BOUNDS(ctrl, s0 + xr + ROW_PADS * row, (uint64_t)n + ROW_PADS * (uint64_t)rows, CS_STAB_OUT)) continue;
         P[s0 + xr + ROW_PADS * row] = make_float4(me.x, me.y, me.z, __uint_as_float(dst));
         // the first member in x order writes the cell's sub-bin starts; the
         // byte sums are exact up to 255 members, larger cells are flagged
@@ -540,11 +549,11 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
 
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
-                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s)
+                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max)
 {
     const uint64_t tiles = ((uint64_t)C + 1 + SCAN_TILE - 1) / SCAN_TILE;
     return launch_dependent(k_scan, dim3((unsigned)tiles), dim3(SCAN_THREADS), 0, s, counts, C, offsets, status,
-                            ctrl, epoch, wait_limit_ns, withhold_first);
+                            ctrl, epoch, wait_limit_ns, withhold_first, track_max);
 }
 
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
@@ -595,6 +604,35 @@ cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, ui
 {
     k_set_system<<<1, 32, 0, s>>>(sys, cbase, wbase, rbase, d, cells, work, rows);
     return cudaGetLastError();
+}
+
+namespace {
+constexpr int WORDS_PER_LAUNCH = 4096;
+struct WordsArgs {
+    uint32_t* dst;
+    int count;
+    uint32_t vals[WORDS_PER_LAUNCH];
+};
+
+__global__ void k_write_words(WordsArgs k)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.count; i += gridDim.x * blockDim.x)
+        k.dst[i] = k.vals[i];
+}
+}  // namespace
+
+cudaError_t launch_write_words(uint32_t* dst, const uint32_t* vals, size_t count, cudaStream_t s)
+{
+    for (size_t off = 0; off < count; off += WORDS_PER_LAUNCH) {
+        WordsArgs k;
+        k.dst = dst + off;
+        k.count = (int)std::min<size_t>(WORDS_PER_LAUNCH, count - off);
+        for (int i = 0; i < k.count; ++i) k.vals[i] = vals[off + i];
+        k_write_words<<<(k.count + 255) / 256, 256, 0, s>>>(k);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_set_kscale(float* kscale, const float* vals, int count, cudaStream_t s)

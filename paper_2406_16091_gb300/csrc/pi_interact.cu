@@ -212,7 +212,9 @@ struct Sums {
 template <class Acc, int KERNEL>
 __device__ __forceinline__ void store_out(const InteractArgs& a, uint32_t slot, const Sums<Acc, KERNEL>& r)
 {
+    if (!PI_BOUNDS(a.ctrl, slot, a.n, CS_DIRECT_TARGET)) return;
     const uint32_t o = a.original_order ? a.perm[slot] : slot;
+    if (!PI_BOUNDS(a.ctrl, o, a.n, CS_DIRECT_TARGET)) return;
     a.S[o] = r.s.value();
     a.Vx[o] = r.vx.value();
     a.Vy[o] = r.vy.value();
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(128) k_interact_ppnl(InteractArgs a)
             const uint32_t row = d.cell_base + (uint32_t)nx * ((uint32_t)by + (uint32_t)ny * (uint32_t)bz);
             const uint32_t j0 = a.offsets[row + max(cx - 1, 0)];
             const uint32_t j1 = a.offsets[row + min(cx + 1, nx - 1) + 1];
+            if (!PI_BOUNDS(a.ctrl, j1, (uint64_t)a.n + 1u, CS_PPNL_SRC)) continue;
             for (uint32_t j = j0; j < j1; ++j) {
                 if (j == k) continue;
                 r.pair(__fsub_rn(a.sx[j], xt), __fsub_rn(a.sy_pos[j], yt), __fsub_rn(a.sz[j], zt), d.rc2, kp);
@@ -505,12 +508,29 @@ __device__ __forceinline__ float4 sentinel()
 }
 
 // The sentinel slots after the staged rows of a chunk (one warp).
-__device__ __forceinline__ void write_row_pads(float4* buf, const Plan& p, unsigned lane)
+template <int CAP>
+__device__ __forceinline__ void write_row_pads(float4* buf, const Plan& p, unsigned lane, Ctrl* ctrl)
 {
     if (lane < 9u * ROW_PAD) {
         const int rr = (int)lane / ROW_PAD;
-        buf[p.sbeg[rr] + p.rlen[rr] + (int)lane % ROW_PAD] = sentinel();
+        const int at = p.sbeg[rr] + p.rlen[rr] + (int)lane % ROW_PAD;
+        if (PI_BOUNDS(ctrl, at, CAP, CS_STAGED_BUF)) buf[at] = sentinel();
     }
+    (void)ctrl;
+}
+
+// Whether the staged rows of a plan fit the buffer (debug builds; always
+// true otherwise: plan_chunk sizes mode-0 chunks to CAP).
+template <int CAP>
+__device__ __forceinline__ bool rows_fit(const Plan& p, Ctrl* ctrl)
+{
+    bool ok = true;
+#ifdef PI_CHECK
+    for (int rr = 0; rr < 9; ++rr) ok = ok && PI_BOUNDS(ctrl, p.sbeg[rr] + p.rlen[rr], CAP + 1, CS_STAGED_BUF);
+#endif
+    (void)p;
+    (void)ctrl;
+    return ok;
 }
 
 // Lookup table of one chunk, built from the offsets and the per-cell
@@ -554,6 +574,7 @@ __device__ __forceinline__ void build_table(const InteractArgs& a, const SysDesc
         const int e = (int)t + i * NT;
         if (e >= total) break;
         const int rr = (int)(((float)e + 0.5f) * inv), k = e - rr * per;
+        if (!PI_BOUNDS(a.ctrl, XSUB * k + (k == ncell ? 1 : XSUB), RB + 1, CS_STAGED_TABLE)) continue;
         E* ent = &tbl[rr][XSUB * k];
         if (k == ncell) {
             ent[0] = (E)start[i];
@@ -811,7 +832,7 @@ __device__ __forceinline__ void target_pair_sums_staged(const float4* buf, const
                                                         const float4& ta, const float4& tb, int cy,
                                                         int cz, int base, const KParams& kp,
                                                         Sums<PlainAcc, KERNEL_GAUSSIAN>& ra,
-                                                        Sums<PlainAcc, KERNEL_GAUSSIAN>& rb)
+                                                        Sums<PlainAcc, KERNEL_GAUSSIAN>& rb, Ctrl* ctrl)
 {
     int nw = 0;
     {
@@ -827,6 +848,9 @@ __device__ __forceinline__ void target_pair_sums_staged(const float4* buf, const
         }
     }
     // nw >= 1: the window of a's own row holds a
+#ifdef PI_CHECK
+    if (!PI_BOUNDS(ctrl, nw > 0 ? 0 : 1, 1, CS_STAGED_BUF)) return;
+#endif
     const float rc2 = d.rc2;
     const float2 ks = make_float2(kp.t, kp.t);
     PairSums ps;
@@ -843,6 +867,7 @@ __device__ __forceinline__ void target_pair_sums_staged(const float4* buf, const
     // window's end (the same row outside the windows, or the row's sentinel
     // slots) add exact zeros.
     do {
+        if (!PI_BOUNDS(ctrl, (uint64_t)((c - cb) / 16u) + 3u, CAP + 1, CS_STAGED_BUF)) break;
         const float4 s0 = lds_f4(c), s1 = lds_f4(c + 16u), s2 = lds_f4(c + 32u), s3 = lds_f4(c + 48u);
         ps.cand(s0, ta, tb, rc2, ks, kp);
         ps.cand(s1, ta, tb, rc2, ks, kp);
@@ -907,7 +932,7 @@ __device__ __forceinline__ void chunk_pair(const InteractArgs& a, const float4* 
     if (mode == 0) {
         if constexpr (packed_path<Acc, KERNEL>()) {
             target_pair_sums_staged<CAP, RB, WT>(buf, tbl_s, coarse_mask, d, win, tid, ta, tb, cy, cz, base, kp,
-                                                 ra, rb);
+                                                 ra, rb, a.ctrl);
         } else {
             target_sums_staged<RB, Acc, KERNEL>(buf, tbl_s, coarse_mask, d, ta, cy, cz, base, kp, ra);
             if (has_b) target_sums_staged<RB, Acc, KERNEL>(buf, tbl_s, coarse_mask, d, tb, cy, cz, base, kp, rb);
@@ -970,8 +995,8 @@ __global__ void __launch_bounds__(T::NT, T::MINB) k_interact_tiled(InteractArgs 
                 if (lane == 0) sm.coarse_mask = 0u;
                 plan_chunk<T>(a, d, sm.plan, x0, xe, cy, cz, lane);
                 __syncwarp();
-                if (sm.plan.mode == 0) write_row_pads(sm.buf, sm.plan, lane);
-                if (lane == 0 && sm.plan.mode == 0) {
+                if (sm.plan.mode == 0) write_row_pads<T::CAP>(sm.buf, sm.plan, lane, a.ctrl);
+                if (lane == 0 && sm.plan.mode == 0 && rows_fit<T::CAP>(sm.plan, a.ctrl)) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_expect_tx(&sm.bar, (uint32_t)sm.plan.total * 16u);
                     for (int rr = 0; rr < 9; ++rr)
@@ -1154,8 +1179,8 @@ __device__ void ws_producer(const InteractArgs& a, WsSmem<T>& sm, unsigned lane)
             __syncwarp();
             const Plan& p = st.plan;
             const int x1 = p.x1, mode = p.mode, ncell = p.xb - p.xa + 1;
-            if (mode == 0) write_row_pads(st.buf, p, lane);
-            if (lane == 0 && mode == 0) {
+            if (mode == 0) write_row_pads<T::CAP>(st.buf, p, lane, a.ctrl);
+            if (lane == 0 && mode == 0 && rows_fit<T::CAP>(p, a.ctrl)) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 bar_expect_tx_only(&st.full, (uint32_t)p.total * 16u);
                 for (int rr = 0; rr < 9; ++rr)
@@ -1273,7 +1298,7 @@ __global__ void __launch_bounds__(T::THREADS, T::MINB) k_interact_ws(InteractArg
 // loads hit).  No chunks, no barriers: only the window lists live in shared
 // memory, so occupancy is set by registers alone.
 
-constexpr int DIRECT_THREADS = 128;
+constexpr int DIRECT_THREADS = DIRECT_BLOCK;
 
 // First index in [lo, hi) of P whose x is >= v (strict: > v); hi if none.
 __device__ __noinline__ uint32_t x_bound(const float4* P, uint32_t lo, uint32_t hi, float v, bool strict)
@@ -1297,6 +1322,13 @@ __device__ __forceinline__ uint32_t sub_bin_start(const InteractArgs& a, uint32_
                                                   bool& dense)
 {
     const uint32_t k = (uint32_t)(b >> 3), sub = (uint32_t)(b & 7);
+#ifdef PI_CHECK
+    // offsets has C + 1 entries, xbins C: the start of a cell may be read
+    // at index C (the end of the last row), a sub-bin word only inside
+    const uint64_t c_all = __ldg(a.sy.cbase + a.sy.S);
+    if (!PI_BOUNDS(a.ctrl, (uint64_t)rb + k, c_all + 1u, CS_DIRECT_LOOKUP)) return 0u;
+    if (sub != 0 && !PI_BOUNDS(a.ctrl, (uint64_t)rb + k, c_all, CS_DIRECT_LOOKUP)) return 0u;
+#endif
     const uint32_t start = __ldg(a.offsets + rb + k);
     if (sub == 0) return start;
     const uint2 w = __ldg(a.xbins + rb + k);
@@ -1405,13 +1437,21 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
         group_windows_direct<DENSE, G>(a, d, t, cx, cy, cz, ulo, uhi);
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr)
-            if (uhi[rr] > ulo[rr]) {
+            if (uhi[rr] > ulo[rr] && PI_BOUNDS(a.ctrl, 2 * nw + 1, 18, CS_DIRECT_WIN)) {
                 win[2 * nw][col] = ulo[rr];
                 win[2 * nw + 1][col] = uhi[rr];
                 ++nw;
             }
     }
     // nw >= 1: the window of the first target's own row holds it
+#ifdef PI_CHECK
+    // (a debug build whose checks dropped every window has nothing to read)
+    if (!PI_BOUNDS(a.ctrl, nw > 0 ? 0 : 1, 1, CS_DIRECT_WIN)) {
+#pragma unroll
+        for (int k = 0; k < G; ++k) r[k] = Sums<Acc, KERNEL>();
+        return;
+    }
+#endif
     const float rc2 = d.rc2;
     const float2 ks = make_float2(kp.t, kp.t);
     PairSumsT<Acc, KERNEL> ps[G / 2];
@@ -1422,6 +1462,7 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     uint32_t wa = wb;
     uint32_t c = lds_u32(wa), ce = lds_u32(wa + WT * 4u);
     do {
+        if (!PI_BOUNDS(a.ctrl, (uint64_t)c + 3u, a.np, CS_DIRECT_SRC)) break;
         const float4* q = a.P + c;
         const float4 s0 = __ldg(q), s1 = __ldg(q + 1), s2 = __ldg(q + 2), s3 = __ldg(q + 3);
 #pragma unroll
@@ -1442,16 +1483,35 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     for (int k = 0; k < G; ++k) ps[k / 2].to(r[k], (k & 1) != 0);
 }
 
-// Slots ka and ka + 1 of P (either may be a sentinel or past the end).
+// The first P slot k0 of this thread's group of `per` consecutive slots
+// and the end of the slots the launch covers: all of P, or -- for a launch
+// over a list of P ranges (one tile shape for some systems of a batch) --
+// the range this block falls in (blocks are dealt out range by range).
+__device__ __forceinline__ void group_slots(const InteractArgs& a, uint32_t per, uint32_t& k0, uint32_t& kend)
+{
+    const uint32_t g = blockIdx.x * DIRECT_THREADS + threadIdx.x;
+    if (!a.ranges) {
+        k0 = per * g;
+        kend = a.np;
+        return;
+    }
+    const int r = find_system(a.rblock, a.nranges, blockIdx.x);
+    const uint2 rg = __ldg(a.ranges + r);
+    k0 = rg.x + per * (g - __ldg(a.rblock + r) * DIRECT_THREADS);
+    kend = rg.y;
+}
+
+// Slots ka and ka + 1 of P below kend (either may be a sentinel or past
+// the end).
 template <int WT, bool DENSE, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t (*win)[WT], unsigned col,
-                                                 uint32_t ka)
+                                                 uint32_t ka, uint32_t kend)
 {
-    if (ka >= a.np) return;
+    if (ka >= kend) return;
     constexpr uint32_t NONE = 0xffffffffu;
     float4 ta = __ldg(a.P + ka);
-    float4 t1 = ka + 1u < a.np ? __ldg(a.P + ka + 1u) : ta;
-    bool has_a = __float_as_uint(ta.w) != NONE, has_b = ka + 1u < a.np && __float_as_uint(t1.w) != NONE;
+    float4 t1 = ka + 1u < kend ? __ldg(a.P + ka + 1u) : ta;
+    bool has_a = __float_as_uint(ta.w) != NONE, has_b = ka + 1u < kend && __float_as_uint(t1.w) != NONE;
     if (!has_a) {
         if (!has_b) return;
         ta = t1;
@@ -1499,9 +1559,9 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
 // the common path keeps its code and registers.
 template <class Acc, int KERNEL>
 __device__ __noinline__ void direct_slot_pair_dense(const InteractArgs& a, uint32_t (*win)[DIRECT_THREADS],
-                                                    unsigned col, uint32_t ka)
+                                                    unsigned col, uint32_t ka, uint32_t kend)
 {
-    direct_slot_pair<DIRECT_THREADS, true, Acc, KERNEL>(a, win, col, ka);
+    direct_slot_pair<DIRECT_THREADS, true, Acc, KERNEL>(a, win, col, ka, kend);
 }
 
 // Resident CTAs per SM the direct kernel's registers are capped for.  The
@@ -1532,11 +1592,12 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL
     if (err) return;
     // grids with dense cells take the exact window bounds in them (a
     // separate copy of the path, so the common one keeps its registers)
-    const uint32_t k0 = 2u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
+    uint32_t k0, kend;
+    group_slots(a, 2u, k0, kend);
     if (mpc > DENSE_CELL)
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0);
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
     else
-        direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL>(a, win, threadIdx.x, k0);
+        direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
 }
 
 // Resident CTAs per SM the four-target direct kernel's registers are capped
@@ -1566,11 +1627,12 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     const uint32_t err = load_error(a.ctrl);
     const uint32_t mpc = *((volatile const uint32_t*)&a.ctrl->max_per_cell);
     if (err) return;
-    const uint32_t k0 = 4u * (blockIdx.x * DIRECT_THREADS + threadIdx.x);
-    if (k0 >= a.np) return;
+    uint32_t k0, kend;
+    group_slots(a, 4u, k0, kend);
+    if (k0 >= kend) return;
     if (mpc > DENSE_CELL) {
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0);
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0 + 2u);
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
+        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0 + 2u, kend);
         return;
     }
     constexpr uint32_t NONE = 0xffffffffu;
@@ -1578,7 +1640,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     bool v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        t[k] = k0 + k < a.np ? __ldg(a.P + k0 + k) : make_float4(0.f, 0.f, 0.f, __uint_as_float(NONE));
+        t[k] = k0 + k < kend ? __ldg(a.P + k0 + k) : make_float4(0.f, 0.f, 0.f, __uint_as_float(NONE));
         v[k] = __float_as_uint(t[k].w) != NONE;
     }
     if (!(v[0] || v[1] || v[2] || v[3])) return;
@@ -1603,24 +1665,27 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
         if (v[k]) store_out(a, __float_as_uint(t[k].w), r[k]);
 }
 
+// Blocks of a direct launch: over all of P, or a.range_blocks for a launch
+// over a list of ranges (the host deals the blocks out range by range).
+inline unsigned direct_grid(const InteractArgs& a, uint64_t per)
+{
+    if (a.ranges) return a.range_blocks;
+    const uint64_t groups = ((uint64_t)a.np + per - 1) / per;
+    return (unsigned)((groups + DIRECT_THREADS - 1) / DIRECT_THREADS);
+}
+
 template <class Acc, int KERNEL>
 void launch_direct4_one(const InteractArgs& a, cudaStream_t s)
 {
-    const uint64_t quads = ((uint64_t)a.np + 3) / 4;
     // an error is left for cudaGetLastError
-    (void)launch_dependent(k_interact_direct4<Acc, KERNEL>,
-                           dim3((unsigned)((quads + DIRECT_THREADS - 1) / DIRECT_THREADS)), dim3(DIRECT_THREADS), 0,
-                           s, a);
+    (void)launch_dependent(k_interact_direct4<Acc, KERNEL>, dim3(direct_grid(a, 4)), dim3(DIRECT_THREADS), 0, s, a);
 }
 
 template <class Acc, int KERNEL>
 void launch_direct_one(const InteractArgs& a, cudaStream_t s)
 {
-    const uint64_t pairs = ((uint64_t)a.np + 1) / 2;
     // an error is left for cudaGetLastError
-    (void)launch_dependent(k_interact_direct<Acc, KERNEL>,
-                           dim3((unsigned)((pairs + DIRECT_THREADS - 1) / DIRECT_THREADS)), dim3(DIRECT_THREADS), 0,
-                           s, a);
+    (void)launch_dependent(k_interact_direct<Acc, KERNEL>, dim3(direct_grid(a, 2)), dim3(DIRECT_THREADS), 0, s, a);
 }
 
 template <class Acc>

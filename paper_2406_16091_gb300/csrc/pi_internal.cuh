@@ -34,6 +34,7 @@ enum : uint32_t {
     ERR_OUT_OF_BOX = 1u,
     ERR_TIMEOUT = 2u,
     ERR_CAPACITY = 4u,
+    ERR_CHECK = 8u,  // a bounds check of the debug build failed (PI_CHECK)
 };
 
 struct Ctrl {
@@ -43,7 +44,10 @@ struct Ctrl {
     uint32_t n;             // particle count of the last pi_bin
     uint32_t work[2];       // next work item handed out by the tiled interaction;
                             // launch number q uses work[q & 1] and clears the other
-    uint32_t pad[58];       // the control block is 256 bytes
+    uint32_t check_site;    // debug builds: the first failed bounds check (CheckSite)
+    uint32_t pad0;
+    unsigned long long ovf; // bucketed binning: overflow buckets, count << 40 | their particles
+    uint32_t pad[54];       // the control block is 256 bytes
 };
 
 // Grid geometry.  inv_w[d] = fl32(n[d] / (hi[d] - lo[d])) computed in FP64.
@@ -78,6 +82,10 @@ constexpr int ROW_PADS = 3;
 constexpr int SEG_CELLS = 32;
 
 constexpr int MAX_SYSTEMS = 2048;
+
+// Threads per block of the direct interaction kernels (the host deals out
+// their blocks when a launch covers a list of P ranges).
+constexpr int DIRECT_BLOCK = 128;
 
 // The systems as kernels see them.
 struct Systems {
@@ -140,6 +148,60 @@ __device__ __forceinline__ uint32_t cell_of(float x, float y, float z, const Gri
     int cy = axis_cell(y, g.lo[1], g.inv_w[1], g.n[1]);
     int cz = axis_cell(z, g.lo[2], g.inv_w[2], g.n[2]);
     return (uint32_t)cx + (uint32_t)g.n[0] * ((uint32_t)cy + (uint32_t)g.n[1] * (uint32_t)cz);
+}
+
+// Bounds checks of the debug build (compiled with -DPI_CHECK).  Each
+// checked access names its site; an index outside its array sets ERR_CHECK
+// in the error word, records the first failing site in Ctrl::check_site,
+// and the access is skipped instead of made, so a bad index shows up as a
+// status (PI_ERR_CHECK from pi_sync_status) rather than a fault.  Normal
+// builds compile every check to `true`.
+enum CheckSite : uint32_t {
+    CS_HIST_COUNTS = 1,      // k_hist: counts[cell]
+    CS_SCATTER_REC = 2,      // k_scatter: rec[slot]
+    CS_STAB_MEMBER = 3,      // k_stabilise: rec[q] of a cell's members
+    CS_STAB_OUT = 4,         // k_stabilise: perm / sx / sy / sz / P / xbins
+    CS_DIRECT_SRC = 5,       // direct interaction: four-source trip from P
+    CS_DIRECT_WIN = 6,       // direct interaction: window list in shared memory
+    CS_DIRECT_LOOKUP = 7,    // direct interaction: offsets / xbins of a window bound
+    CS_DIRECT_TARGET = 8,    // direct interaction: target slots and outputs
+    CS_STAGED_BUF = 9,       // staged interaction: staged rows, pads, source reads
+    CS_STAGED_TABLE = 10,    // staged interaction: sub-bin lookup table
+    CS_PPNL_SRC = 11,        // Alg. 1: sorted sources of the stencil
+    CS_SCAN_TILE = 12,       // k_scan: tile descriptors
+};
+
+#ifdef PI_CHECK
+__device__ __forceinline__ bool pi_in_bounds(Ctrl* ctrl, uint64_t i, uint64_t n, uint32_t site)
+{
+    if (i < n) return true;
+    atomicOr(&ctrl->error, ERR_CHECK);
+    atomicCAS(&ctrl->check_site, 0u, site);
+    return false;
+}
+#define PI_BOUNDS(ctrl, i, n, site) ::pi::pi_in_bounds((ctrl), (uint64_t)(i), (uint64_t)(n), (site))
+#else
+#define PI_BOUNDS(ctrl, i, n, site) true
+#endif
+
+// x-sub-bin of a particle at x in cell c_local of grid g: clamp(floor((x -
+// lo) * XSUB * inv_w) - XSUB * cx, 0, XSUB - 1), monotone in x along an
+// X-row (FP32, the same rounding everywhere it is computed).
+__device__ __forceinline__ int x_sub_bin(float x, uint32_t c_local, const Grid& g)
+{
+    const float invs = g.inv_w[0] * (float)XSUB;
+    const int cxs = XSUB * (int)(c_local % (uint32_t)g.n[0]);
+    return min(max(__float2int_rd(__fmul_rn(__fsub_rn(x, g.lo[0]), invs)) - cxs, 0), XSUB - 1);
+}
+
+// The thermometer of sub-bin sb: byte b - 1 is 1 when sb < b (b = 1 ..
+// XSUB - 1), as (bytes 0..3, bytes 4..6); summed over a cell's members it
+// gives how many of them lie below each sub-bin boundary.
+__device__ __forceinline__ uint2 thermometer(int sb)
+{
+    static_assert(XSUB == 8, "the thermometer has 7 one-byte counts");
+    const unsigned long long t = 0x01010101010101ull & (~0ull << (8 * sb));
+    return make_uint2((uint32_t)t, (uint32_t)(t >> 32));
 }
 
 __device__ __forceinline__ uint32_t load_error(const Ctrl* ctrl)
@@ -208,15 +270,52 @@ struct ZeroArgs {
     uint32_t vals[NB];
 };
 
+static_assert(sizeof(Ctrl) == 256, "the control block is 256 bytes");
+
+// Bucketed binning (pi_bucket.cu).  The cells are split into B buckets of
+// 2^bc_log2 consecutive cells and the particles into chunks of `chunk`
+// consecutive input particles.  mat[b * chunks + k] counts the particles of
+// chunk k in bucket b; its exclusive scan (k_scan) in that bucket-major
+// order gives where chunk k's particles of bucket b start in bucket order,
+// and where every bucket starts.  One CTA per bucket then ranks the
+// bucket's cells in shared memory; buckets of more than BUCKET_CAP
+// particles go through a grid-wide path instead.
+constexpr int BUCKET_CAP = 2048;           // particles of a bucket ranked in shared memory
+constexpr int BUCKET_MAX_CELLS = 1024;     // cells per bucket
+constexpr int BUCKET_MAX = 8192;           // buckets (the chunk kernels' shared histogram)
+constexpr int BUCKET_CHUNK = 8192;         // particles per chunk
+struct BucketPlan {
+    uint32_t bc_log2;  // cells per bucket = 1 << bc_log2
+    uint32_t B;        // buckets
+    uint32_t chunks;   // chunks of BUCKET_CHUNK particles
+    uint32_t C;        // cells of all systems
+};
+// Whether the bucketed path takes n particles in C cells, and its plan.
+bool bucket_plan(uint64_t n, uint64_t C, uint64_t mat_capacity, BucketPlan& plan);
+cudaError_t launch_bucket_count(const float* x, const float* y, const float* z, uint32_t n, const Systems& sy,
+                                const BucketPlan& plan, uint32_t* mat, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_bucket_scatter(const float* x, const float* y, const float* z, uint32_t n,
+                                  const Systems& sy, const BucketPlan& plan, const uint32_t* base, float4* rec,
+                                  Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_bucket_cells(const float4* rec, uint32_t n, const Systems& sy, const BucketPlan& plan,
+                                const uint32_t* base, uint32_t* counts, uint32_t* offsets, uint32_t* perm,
+                                float* sx, float* sy_out, float* sz, float4* P, uint2* xbins, float4* rec2,
+                                uint2* ovf_list, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_bucket_big(const float4* rec2, uint32_t n, const Systems& sy, const BucketPlan& plan,
+                              const uint32_t* offsets, uint32_t* perm, float* sx, float* sy_out, float* sz,
+                              float4* P, uint2* xbins, const uint2* ovf_list, Ctrl* ctrl, int num_sms,
+                              cudaStream_t s);
+
 // Launch wrappers (each returns the cudaGetLastError of its launch).
 cudaError_t launch_zero(uint32_t* p, size_t n_words, uint32_t* pbase, const uint32_t* vals, int nb,
                         cudaStream_t s);
 cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n,
                         const Systems& sy, uint32_t* counts, uint32_t* cell, uint32_t* rank,
                         Ctrl* ctrl, int num_sms, cudaStream_t s);
+// track_max: also record the largest count in Ctrl::max_per_cell (M_C)
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
-                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s);
+                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max = 1);
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
                            const float* y, const float* z, uint32_t n, const Systems& sy,
                            const uint32_t* offsets, Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s);
@@ -235,6 +334,11 @@ cudaError_t launch_total_f64(const float* v, const Systems& sy, double* partial,
 // parameters: sys[0] = d, cbase[1] = cells, wbase[1] = work items.
 cudaError_t launch_set_system(SysDesc* sys, uint32_t* cbase, uint32_t* wbase, uint32_t* rbase,
                               const SysDesc& d, uint32_t cells, uint32_t work, uint32_t rows, cudaStream_t s);
+
+// Copies count words from host memory into device memory by kernel
+// launches whose parameters carry them (no host-side staging, so the copy
+// may be captured in a CUDA graph); vals is read before the call returns.
+cudaError_t launch_write_words(uint32_t* dst, const uint32_t* vals, size_t count, cudaStream_t s);
 
 // Per-system scales of the interaction kernel, written from launch
 // parameters (vals[i] for i < count, count <= 2 MAX_SYSTEMS) into kscale.
@@ -275,6 +379,13 @@ struct InteractArgs {
     Ctrl* ctrl;
     uint64_t wait_limit_ns; // bound of every device-side wait
     uint32_t seq;           // launch number of the tiled kernel (row counter slot)
+    // direct kernels only: a launch over some systems of a batch covers the
+    // P ranges [ranges[r].x, ranges[r].y), r < nranges, range r starting at
+    // block rblock[r] (range_blocks blocks in all); null: all of P
+    const uint2* ranges;
+    const uint32_t* rblock;
+    int nranges;
+    unsigned range_blocks;
 };
 
 // Each adds the number of kernels it launched to *launches.

@@ -29,8 +29,9 @@ def torch_mod():
 
 def run_gpu(x, y, z, lo, hi, rc, h, algo=B.PI_ALGO_TILED, precision=B.PI_PREC_FP32,
             order=B.PI_ORDER_SORTED, n_max=None, binned=True, nbr=True, repeat=1,
-            kernel=B.PI_KERNEL_GAUSSIAN, tile=None):
-    """One pi_bin + pi_interact on cuda:0.  Returns a dict of numpy arrays."""
+            kernel=B.PI_KERNEL_GAUSSIAN, tile=None, binning=None):
+    """One pi_bin + pi_interact on cuda:0.  Returns a dict of numpy arrays.
+    binning: PI_BIN_PER_PARTICLE (the default) or PI_BIN_BUCKETED."""
     torch = torch_mod()
     dev = torch.device("cuda", 0)
     n = len(x)
@@ -41,6 +42,8 @@ def run_gpu(x, y, z, lo, hi, rc, h, algo=B.PI_ALGO_TILED, precision=B.PI_PREC_FP
         B.pi_set_option(ctx, B.PI_OPT_KERNEL, kernel)
         if tile is not None:
             B.pi_set_option(ctx, B.PI_OPT_TILE, tile)
+        if binning is not None:
+            B.pi_set_option(ctx, B.PI_OPT_BINNING, binning)
         s = torch.cuda.current_stream()
         tx, ty, tz = (torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev) for a in (x, y, z))
         m = max(n, 1)

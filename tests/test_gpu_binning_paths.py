@@ -1,0 +1,87 @@
+"""The two binning paths against each other and the oracle.
+
+PI_BIN_PER_PARTICLE (the default) takes one global atomic and one provisional
+record per particle; PI_BIN_BUCKETED counts the particles per bucket of
+consecutive cells and ranks each bucket's cells in shared memory (buckets
+too large for it go through a grid-wide path).  Both must give the same counts, offsets,
+M_C, stable permutation and sorted positions bit for bit (checked against
+the oracle), and the same x-ordered copy and sub-bin words (checked through
+the interaction's outputs, which read them, bitwise)."""
+import numpy as np
+import pytest
+
+from paper_2406_16091_gb300 import binding as B
+from paper_2406_16091_gb300 import workloads as W
+
+from gpu_harness import check_binning, check_interaction, oracle_run, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _dense_cluster(n_bg=20000, n_cl=6000, sigma=0.004, seed=3):
+    rng = np.random.default_rng(seed)
+    bg = rng.random((n_bg, 3)).astype(np.float32)
+    cl = np.clip(0.5 + sigma * rng.standard_normal((n_cl, 3)), 0, np.nextafter(1, 0)).astype(np.float32)
+    p = np.concatenate([bg, cl])
+    return p[:, 0], p[:, 1], p[:, 2]
+
+
+def _one_giant_cell():
+    """6000 particles inside one cell (more than a bucket ranks in shared
+    memory) in a sparse background."""
+    rng = np.random.default_rng(11)
+    bg = rng.random((3000, 3)).astype(np.float32)
+    cell = (0.5 + (1.0 / 64) * rng.random((6000, 3)) * 0.9).astype(np.float32)
+    p = np.concatenate([bg, cell])
+    return p[:, 0], p[:, 1], p[:, 2]
+
+
+def _workload(w):
+    x, y, z = w.positions()
+    return x, y, z, w.lo, w.hi, w.rc, w.h
+
+
+CASES = {
+    "small": lambda: _workload(W.SMALL),
+    "ragged_4099": lambda: _workload(W.scaled(W.SMALL, 4099)),
+    "ppc1_200000": lambda: _workload(W.scaled(W.SCALE_VARIANTS[1], 200000)),
+    "ppc32_150000": lambda: _workload(W.scaled(W.SCALE_VARIANTS[32], 150000)),
+    "clustered_500000": lambda: _workload(W.scaled(W.CLUSTERED, 500000)),
+    "dense_cluster": lambda: (*_dense_cluster(), (0, 0, 0), (1, 1, 1), 1.0 / 64, 1.0 / 128),
+    "one_giant_cell": lambda: (*_one_giant_cell(), (0, 0, 0), (1, 1, 1), 1.0 / 64, 1.0 / 128),
+    "one_cell_grid": lambda: (*W.uniform(700, 5), (0, 0, 0), (1, 1, 1), 1.5, 0.75),
+    "long_rows": lambda: (*W.uniform(5000, 6, (0, 0, 0), (3.0, 0.04, 0.04)), (0, 0, 0), (3.0, 0.04, 0.04),
+                          0.01, 0.005),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_binning_paths_bitwise_equal(name):
+    x, y, z, lo, hi, rc, h = CASES[name]()
+    b, r = oracle_run(x, y, z, lo, hi, rc, h)
+    got = {}
+    for path in (B.PI_BIN_BUCKETED, B.PI_BIN_PER_PARTICLE):
+        for tile in (5, 6, 2):
+            g = run_gpu(x, y, z, lo, hi, rc, h, tile=tile, binning=path)
+            check_binning(g, b)
+            check_interaction(g, r)
+            got[(path, tile)] = g
+    ref = got[(B.PI_BIN_PER_PARTICLE, 5)]
+    for key, g in got.items():
+        for k in ("counts", "offsets", "perm", "sx", "sy", "sz", "S", "Vx", "Vy", "Vz", "nbr"):
+            assert np.array_equal(g[k].view(np.uint32), ref[k].view(np.uint32)), (key, k)
+
+
+def test_bucketed_binning_repeats_and_recovers_after_an_error():
+    """Steps after a failed step (a position outside the box) and repeated
+    steps on one context give the oracle's results."""
+    w = W.scaled(W.CLUSTERED, 300000)
+    x, y, z = w.positions()
+    b, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h)
+    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, repeat=3, binning=B.PI_BIN_BUCKETED)
+    check_binning(g, b)
+    check_interaction(g, r)
+    bad = x.copy()
+    bad[17] = np.float32(1.5)
+    g = run_gpu(bad, y, z, w.lo, w.hi, w.rc, w.h, binning=B.PI_BIN_BUCKETED)
+    assert g["status"] == B.PI_ERR_OUT_OF_BOX

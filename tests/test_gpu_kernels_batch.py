@@ -191,3 +191,115 @@ def test_batch_rejects_bad_counts():
             B.pi_bin(ctx, buf, buf, buf, 3)  # single-system call on a batch
     finally:
         B.pi_destroy(ctx)
+
+
+def _mixed_occupancy_systems(count=24, seed=1004):
+    """A scaled-down copy of the batched workload: N log-uniform in [1024,
+    40000], mean occupancy uniform in [2, 16], each in its own unit box."""
+    systems = W.batched_systems(count=count, seed=seed, n_hi=40000)
+    out = []
+    for sy in systems:
+        x, y, z = sy.positions()
+        out.append(dict(n=sy.n, lo=sy.lo, hi=sy.hi, rc=sy.rc, h=sy.h, x=x, y=y, z=z))
+    return out
+
+
+def _check_batch_outputs(systems, outs, nbr):
+    p0 = 0
+    for s in systems:
+        b, r = oracle_run(s["x"], s["y"], s["z"], s["lo"], s["hi"], s["rc"], s["h"])
+        n = s["n"]
+        sl = slice(p0, p0 + n)
+        g = {"S": outs[0][sl], "Vx": outs[1][sl], "Vy": outs[2][sl], "Vz": outs[3][sl], "nbr": nbr[sl]}
+        check_interaction(g, r)
+        p0 += n
+
+
+def test_batch_graph_replay_matches_oracle():
+    """pi_batch_bin + pi_batch_interact captured in one CUDA graph after
+    pi_autotune (which may keep a shape per occupancy regime), replayed twice;
+    every system of both replays against the oracle."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    systems = _mixed_occupancy_systems()
+    ns = [s["n"] for s in systems]
+    N = sum(ns)
+    hs = [s["h"] for s in systems]
+    ctx = B.pi_batch_create([(s["lo"], s["hi"]) for s in systems], [s["rc"] for s in systems], ns)
+    try:
+        cat = lambda k: torch.from_numpy(np.concatenate([s[k] for s in systems]).astype(np.float32)).to(dev)
+        tx, ty, tz = cat("x"), cat("y"), cat("z")
+        out = [torch.empty(N, device=dev) for _ in range(4)]
+        nb = torch.empty(N, dtype=torch.int32, device=dev)
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            B.pi_batch_bin(ctx, tx, ty, tz, ns, cs)
+            chosen, ms = B.pi_autotune(ctx, hs, *out, nb, B.PI_ORDER_SORTED, 2, cs)
+            assert len(ms) == B.PI_NUM_TILES + 2 and ms[B.PI_AUTOTUNE_REGIMES] > 0
+            tiles = B.pi_batch_tiles(ctx, len(systems))
+            if chosen == B.PI_AUTOTUNE_REGIMES:
+                assert set(tiles) <= {5, 6}
+            else:
+                assert tiles == [-1] * len(systems)
+            # an eager step first (writes the range lists the graph replays)
+            B.pi_batch_bin(ctx, tx, ty, tz, ns, cs)
+            B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, cs)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cs):
+                B.pi_batch_bin(ctx, tx, ty, tz, ns, cs)
+                B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, cs)
+        for _ in range(2):
+            for o in out:
+                o.fill_(float("nan"))
+            nb.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            status, _ = B.pi_sync_status(ctx, torch.cuda.current_stream(), raise_on_error=False)
+            assert status == B.PI_OK
+            _check_batch_outputs(systems, [o.cpu().numpy() for o in out], nb.cpu().numpy().view(np.uint32))
+        del g
+    finally:
+        B.pi_destroy(ctx)
+
+
+def test_batch_per_system_shapes_bitwise_equal():
+    """A plan that mixes the two- and four-target shapes over the systems
+    gives the same outputs bit for bit as one shape for all, and the oracle's
+    values; clearing the plan restores the context's shape."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    systems = _mixed_occupancy_systems(count=16, seed=77)
+    ns = [s["n"] for s in systems]
+    N = sum(ns)
+    hs = [s["h"] for s in systems]
+    ctx = B.pi_batch_create([(s["lo"], s["hi"]) for s in systems], [s["rc"] for s in systems], ns)
+    try:
+        st = torch.cuda.current_stream()
+        cat = lambda k: torch.from_numpy(np.concatenate([s[k] for s in systems]).astype(np.float32)).to(dev)
+        tx, ty, tz = cat("x"), cat("y"), cat("z")
+        B.pi_batch_bin(ctx, tx, ty, tz, ns, st)
+
+        def run():
+            out = [torch.full((N,), float("nan"), device=dev) for _ in range(4)]
+            nb = torch.full((N,), -1, dtype=torch.int32, device=dev)
+            B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, st)
+            B.pi_sync_status(ctx, st)
+            return [o.cpu().numpy().view(np.uint32) for o in out] + [nb.cpu().numpy().view(np.uint32)]
+
+        B.pi_set_option(ctx, B.PI_OPT_TILE, 5)
+        ref = run()
+        for plan in ([5, 6] * 8, [6] * 16, [6, 6, 5, 5, 5, 6, 6, 6, 5, 6, 5, 5, 6, 5, 6, 6]):
+            B.pi_batch_set_tiles(ctx, plan)
+            assert B.pi_batch_tiles(ctx, 16) == plan
+            got = run()
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b)
+        _check_batch_outputs(systems, [a.view(np.float32) for a in got[:4]], got[4])
+        B.pi_batch_set_tiles(ctx, None)
+        assert B.pi_batch_tiles(ctx, 16) == [-1] * 16
+        with pytest.raises(B.PiError):
+            B.pi_batch_set_tiles(ctx, [5] * 15 + [2])
+    finally:
+        B.pi_destroy(ctx)

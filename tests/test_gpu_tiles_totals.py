@@ -39,7 +39,9 @@ def test_tile_shapes_identical_and_autotune(name):
             for a, b in zip(res[0], r):
                 assert np.array_equal(a, b)
         chosen, ms = B.pi_autotune(ctx, [w.h], *out, nb, B.PI_ORDER_SORTED, 2, s)
-        assert len(ms) == B.PI_NUM_TILES + 1
+        # shapes 0..6, Alg. 1, and the per-regime plan (batches only: 0 here)
+        assert len(ms) == B.PI_NUM_TILES + 2 and ms[B.PI_AUTOTUNE_REGIMES] == 0
+        ms = ms[:B.PI_NUM_TILES + 1]
         assert chosen in range(B.PI_NUM_TILES + 1) and all(m > 0 for m in ms)
         assert ms[chosen] == min(ms)
         # the chosen candidate stays in use
