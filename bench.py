@@ -476,9 +476,11 @@ def run_ours(args):
                    if args.binning == "bucketed" else ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"])
     mean_bin = statistics.fmean(t_bin)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    bin_traffic = recorded_traffic("binning", source_hash([os.path.join(src, "pi_bin.cu"),
-                                                          os.path.join(src, "pi_bucket.cu"),
-                                                          os.path.join(src, "pi_internal.cuh")]))
+    # the DRAM bytes of the binning path that ran (its kernels' sources)
+    bin_files = ["pi_bin.cu", "pi_bucket.cu", "pi_internal.cuh"] if args.binning == "bucketed" else \
+        ["pi_bin.cu", "pi_internal.cuh"]
+    bin_traffic = recorded_traffic("binning_bucketed" if args.binning == "bucketed" else "binning",
+                                   source_hash([os.path.join(src, f) for f in bin_files]))
     bin_dram = bin_traffic["dram_bytes_per_launch"] if bin_traffic else None
     binning = {"bound": "hbm", "achieved": bin_bytes / mean_bin / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": bin_bytes / mean_bin / 1e9 / hbm_peak,

@@ -451,6 +451,9 @@ bool bucket_plan(uint64_t n, uint64_t C, uint64_t mat_capacity, BucketPlan& plan
     while (lg <= 10 && ((C + (1ull << lg) - 1) >> lg) > (uint64_t)BUCKET_MAX) ++lg;
     if (lg > 10) return false;
     const uint64_t B = (C + (1ull << lg) - 1) >> lg;
+    // buckets that would mostly overflow the shared-memory ranking take
+    // the per-particle path instead
+    if (n > B * (uint64_t)(BUCKET_CAP / 2)) return false;
     // chunks of BUCKET_CHUNK particles, fewer (and longer) if the count
     // matrix would not fit its buffer
     uint64_t chunks = (n + BUCKET_CHUNK - 1) / BUCKET_CHUNK;
