@@ -264,18 +264,33 @@ def test_batch_graph_replay_matches_oracle():
         B.pi_destroy(ctx)
 
 
-def test_batch_per_system_shapes_bitwise_equal():
+@pytest.mark.parametrize("kern,prec,order,hdiv", [
+    ((B.PI_KERNEL_GAUSSIAN, oracle.GAUSSIAN), B.PI_PREC_FP32, B.PI_ORDER_SORTED, 2),
+    ((B.PI_KERNEL_GAUSSIAN, oracle.GAUSSIAN), B.PI_PREC_KAHAN, B.PI_ORDER_ORIGINAL, 2),
+    ((B.PI_KERNEL_GAUSSIAN, oracle.GAUSSIAN), B.PI_PREC_FP32, B.PI_ORDER_SORTED, 8),   # compensated exponent
+    ((B.PI_KERNEL_LJ, oracle.LJ), B.PI_PREC_FP32, B.PI_ORDER_ORIGINAL, 2),
+], ids=["gauss", "kahan-original", "short-h", "lj-original"])
+def test_batch_per_system_shapes_bitwise_equal(kern, prec, order, hdiv):
     """A plan that mixes the two- and four-target shapes over the systems
     gives the same outputs bit for bit as one shape for all, and the oracle's
     values; clearing the plan restores the context's shape."""
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
     systems = _mixed_occupancy_systems(count=16, seed=77)
+    systems[5]["n"] = 0  # a system without particles inside a plan
+    for k in "xyz":
+        systems[5][k] = systems[5][k][:0]
+    for sy in systems:
+        sy["h"] = sy["rc"] / hdiv
     ns = [s["n"] for s in systems]
     N = sum(ns)
     hs = [s["h"] for s in systems]
-    ctx = B.pi_batch_create([(s["lo"], s["hi"]) for s in systems], [s["rc"] for s in systems], ns)
+    gk, ok = kern
+    ctx = B.pi_batch_create([(s["lo"], s["hi"]) for s in systems], [s["rc"] for s in systems],
+                            [max(n, 1) for n in ns])
     try:
+        B.pi_set_option(ctx, B.PI_OPT_KERNEL, gk)
+        B.pi_set_option(ctx, B.PI_OPT_PRECISION, prec)
         st = torch.cuda.current_stream()
         cat = lambda k: torch.from_numpy(np.concatenate([s[k] for s in systems]).astype(np.float32)).to(dev)
         tx, ty, tz = cat("x"), cat("y"), cat("z")
@@ -284,7 +299,7 @@ def test_batch_per_system_shapes_bitwise_equal():
         def run():
             out = [torch.full((N,), float("nan"), device=dev) for _ in range(4)]
             nb = torch.full((N,), -1, dtype=torch.int32, device=dev)
-            B.pi_batch_interact(ctx, hs, *out, nb, B.PI_ORDER_SORTED, st)
+            B.pi_batch_interact(ctx, hs, *out, nb, order, st)
             B.pi_sync_status(ctx, st)
             return [o.cpu().numpy().view(np.uint32) for o in out] + [nb.cpu().numpy().view(np.uint32)]
 
@@ -296,7 +311,20 @@ def test_batch_per_system_shapes_bitwise_equal():
             got = run()
             for a, b in zip(got, ref):
                 assert np.array_equal(a, b)
-        _check_batch_outputs(systems, [a.view(np.float32) for a in got[:4]], got[4])
+        # against the oracle, system by system
+        outs = [a.view(np.float32) for a in got[:4]]
+        p0 = 0
+        for sy in systems:
+            n = sy["n"]
+            if n:
+                b, r = oracle_run(sy["x"], sy["y"], sy["z"], sy["lo"], sy["hi"], sy["rc"], sy["h"], ok)
+                sl = slice(p0, p0 + n)
+                g = {"S": outs[0][sl], "Vx": outs[1][sl], "Vy": outs[2][sl], "Vz": outs[3][sl], "nbr": got[4][sl]}
+                if order == B.PI_ORDER_ORIGINAL:
+                    check_interaction(g, r, perm=b.perm, rc=sy["rc"])
+                else:
+                    check_interaction(g, r, rc=sy["rc"])
+            p0 += n
         B.pi_batch_set_tiles(ctx, None)
         assert B.pi_batch_tiles(ctx, 16) == [-1] * 16
         with pytest.raises(B.PiError):
