@@ -41,6 +41,19 @@ UNIT = "pairs/s"
 # 3 (displacement) + 5 (r^2) + 1 (scale) + 1 (exp2) + 1 (S) + 6 (V)
 FLOP_PER_PAIR = 17
 FP32_LANES_PER_SM = 128
+# The binning paths (PI_OPT_BINNING values of include/pi.h), their kernels
+# and the sources whose DRAM bytes profiles/traffic.json records.
+BINNING_PATHS = {
+    "per_particle": {"option": 0, "traffic_key": "binning", "files": ["pi_bin.cu", "pi_internal.cuh"],
+                     "kernels": ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"]},
+    "bucketed": {"option": 1, "traffic_key": "binning_bucketed",
+                 "files": ["pi_bin.cu", "pi_bucket.cu", "pi_internal.cuh"],
+                 "kernels": ["k_zero", "k_bucket_count", "k_scan", "k_bucket_scatter", "k_bucket_cells",
+                             "k_bucket_big"]},
+    "radix": {"option": 2, "traffic_key": "binning_radix", "files": ["pi_bin.cu", "pi_radix.cu", "pi_internal.cuh"],
+              "kernels": ["k_zero", "k_radix_keys", "k_scan", "k_radix_scatter", "k_radix_count",
+                          "k_radix_gather", "k_radix_rank"]},
+}
 
 
 def parse():
@@ -61,7 +74,7 @@ def parse():
                    default="none", help="run one of the extra studies instead of the main line")
     p.add_argument("--jobs", type=int, default=10000, help="serving study: number of jobs")
     p.add_argument("--max-slots", type=int, default=8, help="serving study: slots per capacity bucket")
-    p.add_argument("--binning", choices=["per_particle", "bucketed"], default="per_particle",
+    p.add_argument("--binning", choices=list(BINNING_PATHS), default="per_particle",
                    help="binning path (PI_OPT_BINNING)")
     p.add_argument("--no-extras", action="store_true",
                    help="leave out the batched, serving and per-configuration records of the line")
@@ -276,8 +289,7 @@ def run_ours(args):
     B.pi_set_option(ctx, B.PI_OPT_ALGO, B.PI_ALGO_TILED if args.algo == "tiled" else B.PI_ALGO_PPNL)
     B.pi_set_option(ctx, B.PI_OPT_PRECISION,
                     B.PI_PREC_FP32 if args.precision == "fp32" else B.PI_PREC_KAHAN)
-    B.pi_set_option(ctx, B.PI_OPT_BINNING,
-                    B.PI_BIN_BUCKETED if args.binning == "bucketed" else B.PI_BIN_PER_PARTICLE)
+    B.pi_set_option(ctx, B.PI_OPT_BINNING, BINNING_PATHS[args.binning]["option"])
     tx, ty, tz = (torch.from_numpy(a).to(dev) for a in (x, y, z))
     S, Vx, Vy, Vz = (torch.empty(n, device=dev) for _ in range(4))
     nb = torch.empty(n, dtype=torch.int32, device=dev)
@@ -472,15 +484,13 @@ def run_ours(args):
         roofline["frac_at_median_clock"] = achieved / (alu_peak * clocks["sm_mhz"] / sm_max)
     C = w.cells_per_axis() ** 3
     bin_bytes = binning_bytes(n, C)
-    bin_kernels = (["k_zero", "k_bucket_count", "k_scan", "k_bucket_scatter", "k_bucket_cells", "k_bucket_big"]
-                   if args.binning == "bucketed" else ["k_zero", "k_hist", "k_scan", "k_scatter", "k_stabilise"])
+    bin_path = BINNING_PATHS[args.binning]
+    bin_kernels = bin_path["kernels"]
     mean_bin = statistics.fmean(t_bin)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     # the DRAM bytes of the binning path that ran (its kernels' sources)
-    bin_files = ["pi_bin.cu", "pi_bucket.cu", "pi_internal.cuh"] if args.binning == "bucketed" else \
-        ["pi_bin.cu", "pi_internal.cuh"]
-    bin_traffic = recorded_traffic("binning_bucketed" if args.binning == "bucketed" else "binning",
-                                   source_hash([os.path.join(src, f) for f in bin_files]))
+    bin_traffic = recorded_traffic(bin_path["traffic_key"],
+                                   source_hash([os.path.join(src, f) for f in bin_path["files"]]))
     bin_dram = bin_traffic["dram_bytes_per_launch"] if bin_traffic else None
     binning = {"bound": "hbm", "achieved": bin_bytes / mean_bin / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": bin_bytes / mean_bin / 1e9 / hbm_peak,

@@ -111,12 +111,16 @@ enum {
      * one 32-byte provisional record per particle; PI_BIN_BUCKETED counts
      * the particles per bucket of consecutive cells and ranks each bucket's
      * cells in shared memory, when the bucket-by-chunk count matrix fits the
-     * context (up to about 8 M cells; the per-particle path otherwise).
-     * Results are the same bit for bit. */
+     * context (up to about 8 M cells; the per-particle path otherwise);
+     * PI_BIN_RADIX sorts the particles by cell with a stable
+     * least-significant-digit radix sort (digits of up to 9 bits, one count,
+     * scan and split pass per digit) and then gathers the sorted arrays,
+     * when its count matrices fit the context (the per-particle path
+     * otherwise).  Results are the same bit for bit. */
     PI_OPT_BINNING = 7
 };
 enum { PI_TILE_AUTO = -1 };
-enum { PI_BIN_PER_PARTICLE = 0, PI_BIN_BUCKETED = 1 };
+enum { PI_BIN_PER_PARTICLE = 0, PI_BIN_BUCKETED = 1, PI_BIN_RADIX = 2 };
 enum { PI_ALGO_TILED = 0, PI_ALGO_PPNL = 1 };
 enum { PI_PREC_FP32 = 0, PI_PREC_KAHAN = 1 };
 

@@ -36,6 +36,7 @@ PI_OPT_TILE = 6
 PI_OPT_BINNING = 7
 PI_BIN_PER_PARTICLE = 0  # one global atomic and one 32-byte record per particle (default)
 PI_BIN_BUCKETED = 1  # buckets of cells ranked in shared memory, when they fit
+PI_BIN_RADIX = 2  # a stable radix sort of the particles by cell, when it fits
 PI_NUM_TILES = 7  # tile shapes of PI_OPT_TILE (see include/pi.h)
 PI_AUTOTUNE_PPNL = PI_NUM_TILES  # pi_autotune's index of PI_ALGO_PPNL
 PI_AUTOTUNE_REGIMES = PI_NUM_TILES + 1  # pi_autotune's index of the per-regime plan

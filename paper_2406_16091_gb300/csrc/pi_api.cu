@@ -320,7 +320,11 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     // least 32 cells by the chunks of n_max particles, capped at 4 M entries
     const size_t buckets_max = std::min<size_t>(pi::BUCKET_MAX, ((size_t)C + 31) / 32);
     const size_t chunks_max = std::max<size_t>(1, (nm + pi::BUCKET_CHUNK - 1) / pi::BUCKET_CHUNK);
-    const size_t mat_cap = std::min<size_t>((size_t)4 << 20, buckets_max * chunks_max + 1);
+    // (or the radix binning's digit x chunk matrix: up to 2^RADIX_MAX_BITS
+    // digits by the chunks of n_max particles)
+    const size_t radix_chunks = std::max<size_t>(1, (nm + pi::RADIX_CHUNK - 1) / pi::RADIX_CHUNK);
+    const size_t mat_cap = std::max(std::min<size_t>((size_t)4 << 20, buckets_max * chunks_max + 1),
+                                    ((size_t)1 << pi::RADIX_MAX_BITS) * radix_chunks + 1);
     const size_t tiles = (std::max<size_t>((size_t)C, mat_cap) + 1 + pi::SCAN_TILE - 1) / pi::SCAN_TILE;
     Carver k;
     const size_t o_ctrl = k.take<Ctrl>(1);
@@ -556,7 +560,8 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
             ctx->tile = (int)value;
             return PI_OK;
         case PI_OPT_BINNING:
-            if (value != PI_BIN_PER_PARTICLE && value != PI_BIN_BUCKETED) return PI_ERR_INVALID_ARG;
+            if (value != PI_BIN_PER_PARTICLE && value != PI_BIN_BUCKETED && value != PI_BIN_RADIX)
+                return PI_ERR_INVALID_ARG;
             ctx->binning = (int)value;
             return PI_OK;
         case PI_OPT_KERNEL:
@@ -597,6 +602,44 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
     const uint32_t nn = (uint32_t)total;
     const uint32_t C = (uint32_t)ctx->C;
     pi::Systems sy{ctx->d_sys, ctx->pbase, ctx->d_cbase, ctx->d_wbase, ctx->d_rbase, ctx->S};
+
+    pi::RadixPlan rp;
+    if (ctx->binning == PI_BIN_RADIX && pi::radix_plan(nn, C, ctx->mat_cap, rp)) {
+        // radix: per digit pass, a histogram per chunk (the first fused with
+        // the cells), a scan of the digit x chunk matrix and a stable split;
+        // the sorted keys then give offsets, perm and the sorted positions,
+        // and a last pass counts, x-ranks and pads.  Every cell's count,
+        // offset and sub-bin word is written, so only the control block is
+        // cleared.  Keys and values ping-pong between (cell, rank) and the
+        // record buffer; each scan takes its own epoch and ticket.
+        uint32_t* keys[2] = {ctx->cell, reinterpret_cast<uint32_t*>(ctx->rec)};
+        uint32_t* vals[2] = {ctx->rank, reinterpret_cast<uint32_t*>(ctx->rec) + ctx->n_max_total + 4};
+        PI_TRY(pi::launch_zero((uint32_t*)ctx->ctrl, sizeof(Ctrl) / 4, ctx->pbase, ctx->pbase_h.data(), ctx->S + 1,
+                               s));
+        PI_TRY(pi::launch_radix_keys(x, y, z, nn, sy, rp, keys[0], ctx->mat, ctx->ctrl, s));
+        const uint32_t entries = rp.bins * rp.chunks;
+        for (uint32_t pass = 0; pass < rp.passes; ++pass) {
+            const uint32_t shift = pass * rp.digit_bits;
+            const int from = (int)(pass & 1u), to = from ^ 1;
+            if (pass > 0) {
+                PI_TRY(pi::launch_radix_count(keys[from], nn, rp, shift, ctx->mat, ctx->ctrl, s));
+                ctx->epoch = (ctx->epoch % 0x3ffffffeu) + 1u;
+            }
+            PI_TRY(pi::launch_scan(ctx->mat, entries, ctx->mat_base, ctx->scan_status, ctx->ctrl, ctx->epoch,
+                                   ctx->wait_limit_ns, pass == 0 ? ctx->withhold_scan : 0, s, 0, (int)pass));
+            PI_TRY(pi::launch_radix_scatter(keys[from], pass == 0 ? nullptr : vals[from], keys[to], vals[to], nn, rp,
+                                            shift, ctx->mat_base, ctx->ctrl, s));
+        }
+        const int fin = (int)(rp.passes & 1u);
+        PI_TRY(pi::launch_radix_gather(keys[fin], vals[fin], x, y, z, nn, C, ctx->offsets, ctx->perm, ctx->sx,
+                                       ctx->sy, ctx->sz, ctx->ctrl, ctx->num_sms, s));
+        PI_TRY(pi::launch_radix_rank(keys[fin], nn, sy, C, ctx->offsets, ctx->perm, ctx->sx, ctx->sy, ctx->sz,
+                                     ctx->counts, ctx->P, ctx->xbins, ctx->ctrl, ctx->num_sms, s));
+        ctx->launches += 5 + 3 * (rp.passes - 1);
+        ctx->n = total;
+        ctx->binned = 1;
+        return PI_OK;
+    }
 
     pi::BucketPlan plan;
     if (ctx->binning == PI_BIN_BUCKETED && pi::bucket_plan(nn, C, ctx->mat_cap, plan)) {

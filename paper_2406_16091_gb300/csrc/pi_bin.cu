@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
                                                        uint32_t* __restrict__ offsets,
                                                        unsigned long long* __restrict__ status,
                                                        Ctrl* __restrict__ ctrl, uint32_t epoch,
-                                                       uint64_t wait_limit_ns, int withhold_first, int track_max)
+                                                       uint64_t wait_limit_ns, int withhold_first, int track_max,
+                                                       int ticket_slot)
 {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_warp_sum[SCAN_THREADS / 32];
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const uint32_t* __restric
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     pdl_trigger();
     pdl_wait();
-    if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl->ticket, 1u);
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket_slot ? &ctrl->tickets[ticket_slot - 1] : &ctrl->ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t items = (uint64_t)C + 1;  // item C is a zero count -> offsets[C] = total
@@ -549,11 +550,13 @@ cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t
 
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
-                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max)
+                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max,
+                        int ticket_slot)
 {
+    if (ticket_slot < 0 || ticket_slot > 3) return cudaErrorInvalidValue;
     const uint64_t tiles = ((uint64_t)C + 1 + SCAN_TILE - 1) / SCAN_TILE;
     return launch_dependent(k_scan, dim3((unsigned)tiles), dim3(SCAN_THREADS), 0, s, counts, C, offsets, status,
-                            ctrl, epoch, wait_limit_ns, withhold_first, track_max);
+                            ctrl, epoch, wait_limit_ns, withhold_first, track_max, ticket_slot);
 }
 
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,

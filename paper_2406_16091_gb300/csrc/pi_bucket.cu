@@ -41,54 +41,6 @@ constexpr int GROUPS = 2;  // groups of four particles a chunk thread has in fli
 constexpr int CELL_THREADS = 256;
 constexpr unsigned long long OVF_MASK = (1ull << 40) - 1ull;
 
-// The system of input particle i (its particle base is the largest <= i).
-__device__ __forceinline__ int system_of_particle(const Systems& sy, uint32_t i)
-{
-    return sy.S == 1 ? 0 : find_system(sy.pbase, sy.S, i);
-}
-
-// Four consecutive input particles i0 .. i0 + 3 below `end`, as float4 loads
-// when the arrays are 16-byte aligned and the group is whole.
-__device__ __forceinline__ void load4(const float* x, const float* y, const float* z, uint32_t i0, uint32_t end,
-                                      int vec, float (&px)[4], float (&py)[4], float (&pz)[4], bool (&valid)[4])
-{
-    if (vec && i0 + 4u <= end) {
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(x + i0));
-        const float4 b = __ldcs(reinterpret_cast<const float4*>(y + i0));
-        const float4 c = __ldcs(reinterpret_cast<const float4*>(z + i0));
-        px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
-        py[0] = b.x; py[1] = b.y; py[2] = b.z; py[3] = b.w;
-        pz[0] = c.x; pz[1] = c.y; pz[2] = c.z; pz[3] = c.w;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) valid[j] = true;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            valid[j] = i0 + j < end;
-            px[j] = valid[j] ? x[i0 + j] : 0.f;
-            py[j] = valid[j] ? y[i0 + j] : 0.f;
-            pz[j] = valid[j] ? z[i0 + j] : 0.f;
-        }
-    }
-}
-
-// Global cells of four consecutive particles (the systems advance along
-// the group as in k_hist); `ok` collects the out-of-box test.
-__device__ __forceinline__ void cells4(const Systems& sy, uint32_t i0, const float (&px)[4], const float (&py)[4],
-                                       const float (&pz)[4], const bool (&valid)[4], uint32_t (&cell)[4], bool& ok)
-{
-    int s = system_of_particle(sy, i0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (sy.S > 1 && valid[j])
-            while (s + 1 < sy.S && i0 + j >= __ldg(sy.pbase + s + 1)) ++s;
-        const SysDesc& d = sy.sys[s];
-        bool in = true;
-        cell[j] = cell_of(px[j], py[j], pz[j], d.g, in) + d.cell_base;
-        ok &= in | !valid[j];
-    }
-}
-
 __global__ void __launch_bounds__(CHUNK_THREADS, 2) k_bucket_count(const float* __restrict__ x,
                                                                 const float* __restrict__ y,
                                                                 const float* __restrict__ z, uint32_t n,

@@ -47,7 +47,8 @@ struct Ctrl {
     uint32_t check_site;    // debug builds: the first failed bounds check (CheckSite)
     uint32_t pad0;
     unsigned long long ovf; // bucketed binning: overflow buckets, count << 40 | their particles
-    uint32_t pad[54];       // the control block is 256 bytes
+    uint32_t tickets[3];    // scan tile tickets of a step's second to fourth scans (radix binning)
+    uint32_t pad[51];       // the control block is 256 bytes
 };
 
 // Grid geometry.  inv_w[d] = fl32(n[d] / (hi[d] - lo[d])) computed in FP64.
@@ -204,6 +205,54 @@ __device__ __forceinline__ uint2 thermometer(int sb)
     return make_uint2((uint32_t)t, (uint32_t)(t >> 32));
 }
 
+// The system of input particle i (its particle base is the largest <= i).
+__device__ __forceinline__ int system_of_particle(const Systems& sy, uint32_t i)
+{
+    return sy.S == 1 ? 0 : find_system(sy.pbase, sy.S, i);
+}
+
+// Four consecutive input particles i0 .. i0 + 3 below `end`, as float4 loads
+// when the arrays are 16-byte aligned and the group is whole.
+__device__ __forceinline__ void load4(const float* x, const float* y, const float* z, uint32_t i0, uint32_t end,
+                                      int vec, float (&px)[4], float (&py)[4], float (&pz)[4], bool (&valid)[4])
+{
+    if (vec && i0 + 4u <= end) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(x + i0));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(y + i0));
+        const float4 c = __ldcs(reinterpret_cast<const float4*>(z + i0));
+        px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
+        py[0] = b.x; py[1] = b.y; py[2] = b.z; py[3] = b.w;
+        pz[0] = c.x; pz[1] = c.y; pz[2] = c.z; pz[3] = c.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) valid[j] = true;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            valid[j] = i0 + j < end;
+            px[j] = valid[j] ? x[i0 + j] : 0.f;
+            py[j] = valid[j] ? y[i0 + j] : 0.f;
+            pz[j] = valid[j] ? z[i0 + j] : 0.f;
+        }
+    }
+}
+
+// Global cells of four consecutive particles (the systems advance along
+// the group as in k_hist); `ok` collects the out-of-box test.
+__device__ __forceinline__ void cells4(const Systems& sy, uint32_t i0, const float (&px)[4], const float (&py)[4],
+                                       const float (&pz)[4], const bool (&valid)[4], uint32_t (&cell)[4], bool& ok)
+{
+    int s = system_of_particle(sy, i0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (sy.S > 1 && valid[j])
+            while (s + 1 < sy.S && i0 + j >= __ldg(sy.pbase + s + 1)) ++s;
+        const SysDesc& d = sy.sys[s];
+        bool in = true;
+        cell[j] = cell_of(px[j], py[j], pz[j], d.g, in) + d.cell_base;
+        ok &= in | !valid[j];
+    }
+}
+
 __device__ __forceinline__ uint32_t load_error(const Ctrl* ctrl)
 {
     return *((volatile const uint32_t*)&ctrl->error);
@@ -290,6 +339,35 @@ struct BucketPlan {
     uint32_t chunks;   // chunks of BUCKET_CHUNK particles
     uint32_t C;        // cells of all systems
 };
+// Radix binning (pi_radix.cu): a least-significant-digit radix sort of the
+// particles by global cell, digits of at most RADIX_MAX_BITS bits over
+// chunks of RADIX_CHUNK particles; the digit x chunk count matrices live in
+// the bucketed path's `mat` buffers.
+constexpr int RADIX_CHUNK = 4096;
+constexpr int RADIX_MAX_BITS = 9;
+struct RadixPlan {
+    uint32_t passes;      // digit passes, at most 4 (cells < 2^31)
+    uint32_t digit_bits;  // bits per digit
+    uint32_t bins;        // 1 << digit_bits
+    uint32_t chunks;
+    uint32_t C;
+};
+bool radix_plan(uint64_t n, uint64_t C, uint64_t mat_capacity, RadixPlan& plan);
+cudaError_t launch_radix_keys(const float* x, const float* y, const float* z, uint32_t n, const Systems& sy,
+                              const RadixPlan& plan, uint32_t* keys, uint32_t* mat, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_radix_count(const uint32_t* keys, uint32_t n, const RadixPlan& plan, uint32_t shift,
+                               uint32_t* mat, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_radix_scatter(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                 uint32_t* vals_out, uint32_t n, const RadixPlan& plan, uint32_t shift,
+                                 const uint32_t* base, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_radix_gather(const uint32_t* keys, const uint32_t* vals, const float* x, const float* y,
+                                const float* z, uint32_t n, uint32_t C, uint32_t* offsets, uint32_t* perm, float* sx,
+                                float* sy_out, float* sz, Ctrl* ctrl, int num_sms, cudaStream_t s);
+cudaError_t launch_radix_rank(const uint32_t* keys, uint32_t n, const Systems& sy, uint32_t C,
+                              const uint32_t* offsets, const uint32_t* perm, const float* sx, const float* sy_in,
+                              const float* sz, uint32_t* counts, float4* P, uint2* xbins, Ctrl* ctrl, int num_sms,
+                              cudaStream_t s);
+
 // Whether the bucketed path takes n particles in C cells, and its plan.
 bool bucket_plan(uint64_t n, uint64_t C, uint64_t mat_capacity, BucketPlan& plan);
 cudaError_t launch_bucket_count(const float* x, const float* y, const float* z, uint32_t n, const Systems& sy,
@@ -312,10 +390,14 @@ cudaError_t launch_zero(uint32_t* p, size_t n_words, uint32_t* pbase, const uint
 cudaError_t launch_hist(const float* x, const float* y, const float* z, uint32_t n,
                         const Systems& sy, uint32_t* counts, uint32_t* cell, uint32_t* rank,
                         Ctrl* ctrl, int num_sms, cudaStream_t s);
-// track_max: also record the largest count in Ctrl::max_per_cell (M_C)
+// track_max: also record the largest count in Ctrl::max_per_cell (M_C);
+// ticket_slot: 0 takes the tiles from Ctrl::ticket, 1..3 from
+// Ctrl::tickets[slot - 1] (each scan of a step needs its own, cleared by
+// k_zero, and its own epoch)
 cudaError_t launch_scan(const uint32_t* counts, uint32_t C, uint32_t* offsets,
                         unsigned long long* status, Ctrl* ctrl, uint32_t epoch,
-                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max = 1);
+                        uint64_t wait_limit_ns, int withhold_first, cudaStream_t s, int track_max = 1,
+                        int ticket_slot = 0);
 cudaError_t launch_scatter(const uint32_t* cell, const uint32_t* rank, const float* x,
                            const float* y, const float* z, uint32_t n, const Systems& sy,
                            const uint32_t* offsets, Rec* rec, Ctrl* ctrl, int num_sms, cudaStream_t s);

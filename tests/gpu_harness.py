@@ -31,7 +31,7 @@ def run_gpu(x, y, z, lo, hi, rc, h, algo=B.PI_ALGO_TILED, precision=B.PI_PREC_FP
             order=B.PI_ORDER_SORTED, n_max=None, binned=True, nbr=True, repeat=1,
             kernel=B.PI_KERNEL_GAUSSIAN, tile=None, binning=None):
     """One pi_bin + pi_interact on cuda:0.  Returns a dict of numpy arrays.
-    binning: PI_BIN_PER_PARTICLE (the default) or PI_BIN_BUCKETED."""
+    binning: PI_BIN_PER_PARTICLE (the default), PI_BIN_BUCKETED or PI_BIN_RADIX."""
     torch = torch_mod()
     dev = torch.device("cuda", 0)
     n = len(x)

@@ -53,3 +53,23 @@ def test_binning_bytes_follow_the_algorithmic_formula():
     n, C = 2097152, 64 ** 3
     assert bench.binning_bytes(n, C) == 48 * n + 12 * C == 103_809_024
     assert bench.binning_bytes_with_p(n, C) > bench.binning_bytes(n, C)
+
+
+def test_binning_paths_match_the_header_and_sources():
+    """Each --binning choice sets the PI_OPT_BINNING value include/pi.h
+    gives it, and names kernels and sources that exist."""
+    import re
+
+    header = open(os.path.join(ROOT, "include", "pi.h")).read()
+    enum = re.search(r"enum \{ (PI_BIN_[^}]*)\};", header).group(1)
+    values = {k.strip(): int(v) for k, v in (e.split("=") for e in enum.split(",") if e.strip())}
+    names = {"per_particle": "PI_BIN_PER_PARTICLE", "bucketed": "PI_BIN_BUCKETED", "radix": "PI_BIN_RADIX"}
+    assert set(bench.BINNING_PATHS) == set(names)
+    csrc = os.path.join(ROOT, "paper_2406_16091_gb300", "csrc")
+    for choice, path in bench.BINNING_PATHS.items():
+        assert path["option"] == values[names[choice]]
+        text = ""
+        for f in path["files"]:
+            text += open(os.path.join(csrc, f)).read()
+        for kern in path["kernels"]:
+            assert re.search(r"\b%s\b" % kern, text), (choice, kern)

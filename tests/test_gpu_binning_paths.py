@@ -1,9 +1,11 @@
-"""The two binning paths against each other and the oracle.
+"""The three binning paths against each other and the oracle.
 
 PI_BIN_PER_PARTICLE (the default) takes one global atomic and one provisional
 record per particle; PI_BIN_BUCKETED counts the particles per bucket of
 consecutive cells and ranks each bucket's cells in shared memory (buckets
-too large for it go through a grid-wide path).  Both must give the same counts, offsets,
+too large for it go through a grid-wide path); PI_BIN_RADIX sorts the
+particles by cell with a stable least-significant-digit radix sort (one,
+two or three digit passes by the number of cells).  All must give the same counts, offsets,
 M_C, stable permutation and sorted positions bit for bit (checked against
 the oracle), and the same x-ordered copy and sub-bin words (checked through
 the interaction's outputs, which read them, bitwise)."""
@@ -52,7 +54,13 @@ CASES = {
     "one_cell_grid": lambda: (*W.uniform(700, 5), (0, 0, 0), (1, 1, 1), 1.5, 0.75),
     "long_rows": lambda: (*W.uniform(5000, 6, (0, 0, 0), (3.0, 0.04, 0.04)), (0, 0, 0), (3.0, 0.04, 0.04),
                           0.01, 0.005),
+    # 81^3 = 531,441 cells: 20-bit keys, three radix passes of 7 bits
+    "three_digit_passes": lambda: (*W.uniform(150000, 8), (0, 0, 0), (1, 1, 1), 1.0 / 81, 1.0 / 162),
+    # 4^3 cells: one radix pass of 6 bits
+    "one_digit_pass": lambda: (*W.uniform(30000, 9), (0, 0, 0), (1, 1, 1), 0.25, 0.125),
 }
+
+PATHS = (B.PI_BIN_RADIX, B.PI_BIN_BUCKETED, B.PI_BIN_PER_PARTICLE)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -60,7 +68,7 @@ def test_binning_paths_bitwise_equal(name):
     x, y, z, lo, hi, rc, h = CASES[name]()
     b, r = oracle_run(x, y, z, lo, hi, rc, h)
     got = {}
-    for path in (B.PI_BIN_BUCKETED, B.PI_BIN_PER_PARTICLE):
+    for path in PATHS:
         for tile in (5, 6, 2):
             g = run_gpu(x, y, z, lo, hi, rc, h, tile=tile, binning=path)
             check_binning(g, b)
@@ -72,16 +80,17 @@ def test_binning_paths_bitwise_equal(name):
             assert np.array_equal(g[k].view(np.uint32), ref[k].view(np.uint32)), (key, k)
 
 
-def test_bucketed_binning_repeats_and_recovers_after_an_error():
+@pytest.mark.parametrize("path", [B.PI_BIN_BUCKETED, B.PI_BIN_RADIX], ids=["bucketed", "radix"])
+def test_binning_repeats_and_recovers_after_an_error(path):
     """Steps after a failed step (a position outside the box) and repeated
     steps on one context give the oracle's results."""
     w = W.scaled(W.CLUSTERED, 300000)
     x, y, z = w.positions()
     b, r = oracle_run(x, y, z, w.lo, w.hi, w.rc, w.h)
-    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, repeat=3, binning=B.PI_BIN_BUCKETED)
+    g = run_gpu(x, y, z, w.lo, w.hi, w.rc, w.h, repeat=3, binning=path)
     check_binning(g, b)
     check_interaction(g, r)
     bad = x.copy()
     bad[17] = np.float32(1.5)
-    g = run_gpu(bad, y, z, w.lo, w.hi, w.rc, w.h, binning=B.PI_BIN_BUCKETED)
+    g = run_gpu(bad, y, z, w.lo, w.hi, w.rc, w.h, binning=path)
     assert g["status"] == B.PI_ERR_OUT_OF_BOX

@@ -122,7 +122,9 @@ def _systems(seed=5):
 @pytest.mark.parametrize("algo", [(B.PI_ALGO_TILED, None), (B.PI_ALGO_TILED, 6), (B.PI_ALGO_TILED, 2),
                                   (B.PI_ALGO_PPNL, None)], ids=["direct", "direct4", "staged", "ppnl"])
 @pytest.mark.parametrize("order", [B.PI_ORDER_SORTED, B.PI_ORDER_ORIGINAL])
-def test_batch_matches_each_system_alone(algo, order):
+@pytest.mark.parametrize("binning", [B.PI_BIN_PER_PARTICLE, B.PI_BIN_RADIX, B.PI_BIN_BUCKETED],
+                         ids=["per_particle", "radix", "bucketed"])
+def test_batch_matches_each_system_alone(algo, order, binning):
     algo, tile = algo
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
@@ -133,6 +135,7 @@ def test_batch_matches_each_system_alone(algo, order):
                             [n + 5 for n in ns])
     try:
         B.pi_set_option(ctx, B.PI_OPT_ALGO, algo)
+        B.pi_set_option(ctx, B.PI_OPT_BINNING, binning)
         if tile is not None:
             B.pi_set_option(ctx, B.PI_OPT_TILE, tile)
         S_, C, _ = B.pi_batch_info(ctx)
