@@ -345,6 +345,18 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Two consecutive float4s from a 32-byte aligned global address, as one
+// 256-bit read-only vector load.
+__device__ __forceinline__ void ldg_pair(const float4* q, float4& u, float4& v)
+{
+    unsigned long long a0, a1, a2, a3;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a0), "=l"(a1), "=l"(a2), "=l"(a3) : "l"(q));
+    u = make_float4(__uint_as_float((uint32_t)a0), __uint_as_float((uint32_t)(a0 >> 32)),
+                    __uint_as_float((uint32_t)a1), __uint_as_float((uint32_t)(a1 >> 32)));
+    v = make_float4(__uint_as_float((uint32_t)a2), __uint_as_float((uint32_t)(a2 >> 32)),
+                    __uint_as_float((uint32_t)a3), __uint_as_float((uint32_t)(a3 >> 32)));
+}
+
 // Shared-memory loads by 32-bit shared-window address.  The "memory"
 // clobber keeps them after the C++ stores that wrote the data.
 __device__ __forceinline__ float4 lds_f4(uint32_t addr)
@@ -1420,15 +1432,16 @@ __device__ __forceinline__ void group_windows_direct(const InteractArgs& a, cons
 // four sources per trip, each source evaluated against every target of the
 // group, two at a time with packed arithmetic.  Candidates outside a
 // target's own windows -- the other targets', up to three past a window's end
-// (the same row outside the windows, or the row's sentinel slots) -- add
-// exact zeros, so each target's sums are those of the sequential loop over
-// its own windows.
+// (the same row outside the windows, or the row's sentinel slots), and for
+// four targets one before a window's start -- add exact zeros, so each
+// target's sums are those of the sequential loop over its own windows.
 template <int WT, int G, bool DENSE, class Acc, int KERNEL>
 __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
                                              unsigned col, const float4 (&t)[G], const int (&cx)[G], int cy,
                                              int cz, const KParams& kp, Sums<Acc, KERNEL> (&r)[G])
 {
     static_assert(G % 2 == 0, "targets go in packed pairs");
+    constexpr bool WIDE = G >= 4;
     int nw = 0;
     {
         uint32_t ulo[9], uhi[9];
@@ -1441,7 +1454,14 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr)
             if (uhi[rr] > ulo[rr] && PI_BOUNDS(a.ctrl, 2 * nw + 1, 18, CS_DIRECT_WIN)) {
-                win[2 * nw][col] = ulo[rr];
+                // four targets: an even start, so that trips of four
+                // sources start on 32-byte boundaries of P (its base is
+                // 256-byte aligned) and load as two 32-byte vectors; the
+                // slot before a window is outside every target's cutoff (or
+                // a row's sentinel) and adds zeros.  (Measured: faster for
+                // four targets, slower for two, whose extra slot per window
+                // costs more than the wider loads save.)
+                win[2 * nw][col] = WIDE ? ulo[rr] & ~1u : ulo[rr];
                 win[2 * nw + 1][col] = uhi[rr];
                 ++nw;
             }
@@ -1465,9 +1485,20 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     uint32_t wa = wb;
     uint32_t c = lds_u32(wa), ce = lds_u32(wa + WT * 4u);
     do {
-        if (!PI_BOUNDS(a.ctrl, (uint64_t)c + 3u, a.np, CS_DIRECT_SRC)) break;
+        if (!PI_BOUNDS(a.ctrl, (uint64_t)c + 3u, a.np, CS_DIRECT_SRC) ||
+            !PI_BOUNDS(a.ctrl, WIDE ? c & 1u : 0u, 1u, CS_DIRECT_SRC))
+            break;
         const float4* q = a.P + c;
-        const float4 s0 = __ldg(q), s1 = __ldg(q + 1), s2 = __ldg(q + 2), s3 = __ldg(q + 3);
+        float4 s0, s1, s2, s3;
+        if constexpr (WIDE) {
+            ldg_pair(q, s0, s1);
+            ldg_pair(q + 2, s2, s3);
+        } else {
+            s0 = __ldg(q);
+            s1 = __ldg(q + 1);
+            s2 = __ldg(q + 2);
+            s3 = __ldg(q + 3);
+        }
 #pragma unroll
         for (int h = 0; h < G / 2; ++h) {
             ps[h].cand(s0, t[2 * h], t[2 * h + 1], rc2, ks, kp);
