@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--algo", choices=["tiled", "ppnl"], default="tiled")
     p.add_argument("--precision", choices=["fp32", "kahan"], default="fp32")
     p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--e2e-in-flight", type=int, default=6,
+                   help="contexts (and streams) the end-to-end steps rotate over")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--flush-mb", type=int, default=512)
     p.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6"],
@@ -399,7 +401,7 @@ def run_ours(args):
             # copy in; outputs into one pinned block, one copy out), so one
             # step's copies and latency-bound binning overlap the others'
             # kernels.  Every step copies its positions in and its outputs out.
-            PIPE = 4
+            PIPE = max(1, args.e2e_in_flight)
             d = (n + 3) // 4 * 4
             hin = torch.empty(3 * d).pin_memory()
             for k, a_ in enumerate((x, y, z)):
