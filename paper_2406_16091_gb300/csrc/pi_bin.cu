@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ce
 {
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     bool bad = false;
     const uint32_t groups = (n + 3u) / 4u;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256) k_stabilise(const Rec* __restrict__ rec, 
 {
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     bool bad = false;
     const uint32_t C = __ldg(sy.cbase + sy.S);
     // the sentinel slots after every X-row of P: a particle far from every

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(CHUNK_THREADS, 2) k_bucket_scatter(const float
     extern __shared__ uint32_t cur[];
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const uint32_t k = blockIdx.x;
     for (uint32_t b = threadIdx.x; b < plan.B; b += CHUNK_THREADS) cur[b] = base[(size_t)b * plan.chunks + k];
     __syncthreads();
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_bucket_cells(
     CellSmem& sm = *reinterpret_cast<CellSmem*>(smem_raw);
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t b = blockIdx.x;
     const uint32_t c0 = b << plan.bc_log2, c1 = min(c0 + (1u << plan.bc_log2), plan.C), ncell = c1 - c0;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256) k_bucket_big(const float4* __restrict__ r
 {
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const unsigned long long o = *((volatile const unsigned long long*)&ctrl->ovf);
     const int nb = (int)min((unsigned long long)BUCKET_MAX, o >> 40);
     const uint32_t total = (uint32_t)(o & OVF_MASK);

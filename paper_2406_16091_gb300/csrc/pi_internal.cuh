@@ -258,6 +258,21 @@ __device__ __forceinline__ uint32_t load_error(const Ctrl* ctrl)
     return *((volatile const uint32_t*)&ctrl->error);
 }
 
+// The control block's error word and M_C as the kernels before this one left
+// them, read by one thread of the CTA and shared through shared memory: when
+// every thread reads the one line itself, the requests queue at the single
+// L2 slice that holds it.  Every thread of the CTA must call it (it holds a
+// barrier), once per kernel.
+__device__ __forceinline__ uint2 cta_ctrl_words(const Ctrl* ctrl)
+{
+    __shared__ uint2 s_words;
+    if (threadIdx.x == 0) s_words = make_uint2(load_error(ctrl), *((volatile const uint32_t*)&ctrl->max_per_cell));
+    __syncthreads();
+    return s_words;
+}
+
+__device__ __forceinline__ uint32_t cta_error(const Ctrl* ctrl) { return cta_ctrl_words(ctrl).x; }
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;

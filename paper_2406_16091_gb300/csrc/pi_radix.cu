@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_count(const uint32_t* _
     for (uint32_t b = threadIdx.x; b < plan.bins; b += RADIX_THREADS) hist[b] = 0u;
     __syncthreads();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const uint32_t k = blockIdx.x;
     const uint32_t beg = k * RADIX_CHUNK, end = min(beg + RADIX_CHUNK, n);
     const uint32_t mask = plan.bins - 1u;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t*
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     for (uint32_t b = lane; b < bins; b += 32) cnt[warp * bins + b] = 0u;
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const uint32_t k = blockIdx.x;
     for (uint32_t b = threadIdx.x; b < bins; b += RADIX_THREADS) gb[b] = base[(size_t)b * plan.chunks + k];
     __syncwarp();
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_radix_gather(const uint32_t* __restrict
 {
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     bool bad = false;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t c = keys[k], i = vals[k];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_radix_rank(const uint32_t* __restrict__
 {
     pdl_trigger();
     pdl_wait();
-    if (load_error(ctrl)) return;
+    if (cta_error(ctrl)) return;
     const uint32_t rows = __ldg(sy.rbase + sy.S);
     const uint64_t np = (uint64_t)n + ROW_PADS * (uint64_t)rows;
     uint32_t mx = 0;
