@@ -507,7 +507,7 @@ def run_ours(args):
     # after the timed region: batched systems, served jobs, per configuration
     extras = {}
     if not args.no_extras and ws == 1:
-        for key, fn in (("per_config", lambda: per_config_records(torch, B, args.flush_mb, alu_peak)),
+        for key, fn in (("per_config", lambda: per_config_records(torch, B, args.flush_mb, alu_peak, hbm_peak)),
                         ("batched", lambda: batched_record(torch, B, args.flush_mb, 10, 5)),
                         ("serving", lambda: serving_record(torch, B, args.serving_jobs, args.max_slots,
                                                            loads=(0.8,)))):
@@ -822,13 +822,17 @@ def study_serving(args):
     print(json.dumps(serving_record(torch, B, args.jobs, args.max_slots)), flush=True)
 
 
-def per_config_records(torch, B, flush_mb, alu_peak, names=("scale_ppc1", "scale_ppc2", "scale_ppc4",
-                                                              "scale_ppc16", "scale_ppc32", "clustered"),
+def per_config_records(torch, B, flush_mb, alu_peak, hbm_peak=6800.0,
+                       names=("scale_ppc1", "scale_ppc2", "scale_ppc4", "scale_ppc16", "scale_ppc32",
+                              "clustered"),
                        reps=20):
     """The other single-GPU configurations: per workload one full step and the
     interaction alone (medians of CUDA events, L2 flushed before each), with
-    the shape pi_autotune picks, the within-cutoff pairs per second and the
-    interaction's fraction of the FP32 peak on useful FLOP."""
+    the shape pi_autotune picks, the within-cutoff pairs per second, the
+    interaction's fraction of the FP32 peak on useful FLOP and, for the
+    low-occupancy rows where its arithmetic intensity is below the FP32/HBM
+    balance, its fraction of the HBM bandwidth on algorithmic bytes (36 per
+    particle + 4 per cell)."""
     dev = torch.device("cuda", 0)
     flush = torch.empty(flush_mb * (1 << 20) // 4, device=dev)
     s = torch.cuda.current_stream()
@@ -858,7 +862,9 @@ def per_config_records(torch, B, flush_mb, alu_peak, names=("scale_ppc1", "scale
                           "pairs_per_s": pairs / (step_ms * 1e-3),
                           "interact_pairs_per_s": pairs / (int_ms * 1e-3),
                           "full_step_particles_per_s": w.n / (step_ms * 1e-3),
-                          "interact_frac_of_fp32_peak": FLOP_PER_PAIR * pairs / (int_ms * 1e-3) / 1e12 / alu_peak}
+                          "interact_frac_of_fp32_peak": FLOP_PER_PAIR * pairs / (int_ms * 1e-3) / 1e12 / alu_peak,
+                          "interact_frac_of_hbm": (36 * w.n + 4 * (w.cells_per_axis() ** 3 + 1))
+                          / (int_ms * 1e-3) / 1e9 / hbm_peak}
             del t, out, nb
         finally:
             B.pi_destroy(ctx)
