@@ -111,6 +111,19 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def evaluations_per_pair(B, ctx, step, pairs, s):
+    """Target-source evaluations per within-cutoff pair of one step, counted by
+    the direct kernels (PI_OPT_COUNT_EVALS) in an untimed step; None for the
+    shapes that do not count."""
+    B.pi_set_option(ctx, B.PI_OPT_COUNT_EVALS, 1)
+    try:
+        step()
+        e = B.pi_eval_count(ctx, s)
+    finally:
+        B.pi_set_option(ctx, B.PI_OPT_COUNT_EVALS, 0)
+    return e / pairs if e and pairs else None
+
+
 def source_hash(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -375,6 +388,8 @@ def run_ours(args):
     eb1.record(s)
     eb1.synchronize()
     back_to_back = 1e3 * eb0.elapsed_time(eb1) / 200
+    # evaluations per useful pair, counted in one more (untimed) step
+    evals = evaluations_per_pair(B, ctx, step, pairs, s)
 
     # ---- end to end through the host-buffer entry points (pinned memory)
     e2e = None
@@ -481,6 +496,7 @@ def run_ours(args):
         "algorithmic_bytes_per_launch": 36 * n + 4 * (w.cells_per_axis() ** 3 + 1),
         "mean_launch_us": 1e6 * mean_int,
         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {sm_max:.0f} MHz",
+        "evaluations_per_useful_pair": evals,
     }
     if clocks:
         roofline["frac_at_median_clock"] = achieved / (alu_peak * clocks["sm_mhz"] / sm_max)
@@ -855,6 +871,7 @@ def per_config_records(torch, B, flush_mb, alu_peak, hbm_peak=6800.0,
             int_ms, _ = _time_events(torch, inter, reps, flush)
             step_ms, _ = _time_events(torch, step, reps, flush)
             _, mpc = B.pi_sync_status(ctx, s)
+            evals = evaluations_per_pair(B, ctx, step, pairs, s)
             rows[name] = {"n": w.n, "cells_per_axis": w.cells_per_axis(), "layout": w.layout,
                           "max_per_cell": mpc, "pairs": pairs,
                           "shape": "ppnl" if chosen == B.PI_AUTOTUNE_PPNL else f"tile{chosen}",
@@ -864,7 +881,8 @@ def per_config_records(torch, B, flush_mb, alu_peak, hbm_peak=6800.0,
                           "full_step_particles_per_s": w.n / (step_ms * 1e-3),
                           "interact_frac_of_fp32_peak": FLOP_PER_PAIR * pairs / (int_ms * 1e-3) / 1e12 / alu_peak,
                           "interact_frac_of_hbm": (36 * w.n + 4 * (w.cells_per_axis() ** 3 + 1))
-                          / (int_ms * 1e-3) / 1e9 / hbm_peak}
+                          / (int_ms * 1e-3) / 1e9 / hbm_peak,
+                          "evaluations_per_useful_pair": evals}
             del t, out, nb
         finally:
             B.pi_destroy(ctx)

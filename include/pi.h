@@ -117,7 +117,17 @@ enum {
      * scan and split pass per digit) and then gathers the sorted arrays,
      * when its count matrices fit the context (the per-particle path
      * otherwise).  Results are the same bit for bit. */
-    PI_OPT_BINNING = 7
+    PI_OPT_BINNING = 7,
+    /* Diagnostics: 1 makes the direct interaction kernels (PI_OPT_TILE 5 and
+     * 6) run a copy that counts their target-source evaluations -- each
+     * target against every source slot of its group's windows, the padding
+     * of four-source trips included -- into a device counter that
+     * pi_eval_count reads; 0 (default) counts nothing.  The copy exists for
+     * the Gaussian kernel in PI_PREC_FP32 (the windows, and so the count,
+     * depend on the positions and r_c only); other kernels, the Kahan mode,
+     * the staged shapes and Alg. 1 count nothing.  The count restarts at
+     * every pi_bin.  Results do not depend on it. */
+    PI_OPT_COUNT_EVALS = 8
 };
 enum { PI_TILE_AUTO = -1 };
 enum { PI_BIN_PER_PARTICLE = 0, PI_BIN_BUCKETED = 1, PI_BIN_RADIX = 2 };
@@ -507,6 +517,15 @@ pi_status pi_server_destroy(pi_server* srv);
 /* Number of kernels this context has launched since pi_create (host
  * counter).  No passage of the paper: library housekeeping. */
 pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count);
+
+/* Synchronises `stream` and reads the target-source evaluations the direct
+ * kernels counted since the last pi_bin (PI_OPT_COUNT_EVALS) into
+ * *evaluations; divided by the within-cutoff pairs (the sum of the nbr
+ * output) it is the evaluations per useful pair.  PI_ERR_INVALID_ARG for a
+ * NULL argument, PI_ERR_CUDA if the stream or the copy fails.  No passage of
+ * the paper: library diagnostics (Sec. 7.2 counts the candidates of the
+ * 27-cell stencil; this counts what the culling leaves). */
+pi_status pi_eval_count(pi_ctx* ctx, pi_stream stream, uint64_t* evaluations);
 
 /* Static text for a status code.  No passage of the paper: library
  * housekeeping. */

@@ -34,6 +34,7 @@ PI_OPT_TEST_WITHHOLD_SCAN = 4
 PI_OPT_KERNEL = 5
 PI_OPT_TILE = 6
 PI_OPT_BINNING = 7
+PI_OPT_COUNT_EVALS = 8  # diagnostics: the direct kernels count their evaluations
 PI_BIN_PER_PARTICLE = 0  # one global atomic and one 32-byte record per particle (default)
 PI_BIN_BUCKETED = 1  # buckets of cells ranked in shared memory, when they fit
 PI_BIN_RADIX = 2  # a stable radix sort of the particles by cell, when it fits
@@ -77,6 +78,28 @@ class PiError(RuntimeError):
         if status in (PI_ERR_CUDA, PI_ERR_CHECK) and extra:
             msg += f": {extra}"
         super().__init__(msg)
+
+
+class Handle:
+    """A context or server handle.  ctypes passes it as the C pointer (its
+    _as_parameter_); once destroyed it refuses to be passed, so a call on a
+    destroyed handle raises here instead of handing freed memory to the
+    library."""
+
+    __slots__ = ("_ptr", "_what")
+
+    def __init__(self, ptr, what: str):
+        self._ptr = ptr
+        self._what = what
+
+    @property
+    def _as_parameter_(self):
+        if self._ptr is None:
+            raise PiError(PI_ERR_INVALID_ARG, f"{self._what} used after it was destroyed")
+        return ctypes.c_void_p(self._ptr)
+
+    def _close(self):
+        self._ptr = None
 
 
 _lib = None
@@ -124,6 +147,7 @@ def load():
         "pi_sync_status": ([P, P, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pi_set_option": ([P, i32, i64], i32),
         "pi_launch_count": ([P, ctypes.POINTER(ctypes.c_uint64)], i32),
+        "pi_eval_count": ([P, P, ctypes.POINTER(ctypes.c_uint64)], i32),
         "pi_status_str": ([i32], ctypes.c_char_p),
         "pi_last_error": ([], ctypes.c_char_p),
     }
@@ -174,7 +198,7 @@ def pi_create(lo, hi, r_c: float, n_max: int):
     box = PiBox((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi))
     out = ctypes.c_void_p()
     _check(load().pi_create(ctypes.byref(box), float(r_c), int(n_max), ctypes.byref(out)), "pi_create")
-    return out.value
+    return Handle(out.value, "context")
 
 
 def pi_batch_create(boxes, r_c, n_max):
@@ -187,7 +211,7 @@ def pi_batch_create(boxes, r_c, n_max):
     _check(load().pi_batch_create(S, arr, ctypes.cast(rc, ctypes.c_void_p),
                                   ctypes.cast(nm, ctypes.c_void_p), ctypes.byref(out)),
            "pi_batch_create")
-    return out.value
+    return Handle(out.value, "context")
 
 
 def pi_batch_bin(ctx, x, y, z, n, stream=None) -> None:
@@ -242,6 +266,8 @@ def pi_reconfigure(ctx, lo, hi, r_c: float, stream=None) -> None:
 
 def pi_destroy(ctx) -> None:
     _check(load().pi_destroy(ctx), "pi_destroy")
+    if isinstance(ctx, Handle):
+        ctx._close()
 
 
 def pi_bin(ctx, x, y, z, n: int, stream=None) -> None:
@@ -294,7 +320,7 @@ def pi_server_create(capacities, initial_slots=None, max_slots_per_bucket: int =
     out = ctypes.c_void_p()
     _check(load().pi_server_create(int(k), caps, init, int(max_slots_per_bucket), int(hbm_budget),
                                    ctypes.byref(out)), "pi_server_create")
-    return out
+    return Handle(out.value, "server")
 
 
 def pi_server_run(srv, jobs) -> float:
@@ -316,6 +342,8 @@ def pi_server_info(srv):
 
 def pi_server_destroy(srv) -> None:
     _check(load().pi_server_destroy(srv), "pi_server_destroy")
+    if isinstance(srv, Handle):
+        srv._close()
 
 
 def pi_grid(ctx):
@@ -408,4 +436,12 @@ def pi_set_option(ctx, key: int, value: int) -> None:
 def pi_launch_count(ctx) -> int:
     c = ctypes.c_uint64()
     _check(load().pi_launch_count(ctx, ctypes.byref(c)), "pi_launch_count")
+    return int(c.value)
+
+
+def pi_eval_count(ctx, stream=None) -> int:
+    """Synchronises and returns the target-source evaluations the direct
+    kernels counted since the last bin (PI_OPT_COUNT_EVALS)."""
+    c = ctypes.c_uint64()
+    _check(load().pi_eval_count(ctx, _stream(stream), ctypes.byref(c)), "pi_eval_count")
     return int(c.value)

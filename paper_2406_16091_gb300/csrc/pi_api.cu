@@ -81,6 +81,7 @@ struct pi_ctx {
     int withhold_scan;
 
     int binning;                    // PI_BIN_* (PI_OPT_BINNING)
+    int count_evals;                // PI_OPT_COUNT_EVALS
     // bucketed binning: count matrix, its scan, overflow buckets
     uint32_t* mat;
     uint32_t* mat_base;
@@ -304,6 +305,7 @@ pi_status pi_batch_create(int32_t num_systems, const pi_box* boxes, const float*
     c->tile = PI_TILE_AUTO;
     c->wait_limit_ns = 1000000000ull;
     c->binning = PI_BIN_PER_PARTICLE;
+    c->count_evals = 0;
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -564,6 +566,10 @@ pi_status pi_set_option(pi_ctx* ctx, int key, int64_t value)
                 return PI_ERR_INVALID_ARG;
             ctx->binning = (int)value;
             return PI_OK;
+        case PI_OPT_COUNT_EVALS:
+            if (value != 0 && value != 1) return PI_ERR_INVALID_ARG;
+            ctx->count_evals = (int)value;
+            return PI_OK;
         case PI_OPT_KERNEL:
             if (value < PI_KERNEL_GAUSSIAN || value > PI_KERNEL_HIGHFLOP) return PI_ERR_INVALID_ARG;
             ctx->kernel = (int)value;
@@ -577,6 +583,18 @@ pi_status pi_launch_count(const pi_ctx* ctx, uint64_t* count)
 {
     if (!ctx || !count) return PI_ERR_INVALID_ARG;
     *count = ctx->launches;
+    return PI_OK;
+}
+
+pi_status pi_eval_count(pi_ctx* ctx, pi_stream stream, uint64_t* evaluations)
+{
+    if (!ctx || !evaluations) return PI_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_eval_count: set device");
+    PI_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long v = 0;
+    PI_TRY(cudaMemcpy(&v, &ctx->ctrl->evals, sizeof v, cudaMemcpyDeviceToHost));
+    *evaluations = v;
     return PI_OK;
 }
 
@@ -855,6 +873,7 @@ pi_status pi_batch_interact(pi_ctx* ctx, const float* h, float* S, float* Vx, fl
     a.ctrl = ctx->ctrl;
     a.wait_limit_ns = ctx->wait_limit_ns;
     a.seq = ctx->tiled_seq;
+    a.count_evals = ctx->count_evals;
     int launched = 0;
     cudaError_t e;
     const bool kahan = ctx->precision == PI_PREC_KAHAN;

@@ -1436,14 +1436,17 @@ __device__ __forceinline__ void group_windows_direct(const InteractArgs& a, cons
 // (the same row outside the windows, or the row's sentinel slots), and for
 // four targets one before a window's start -- add exact zeros, so each
 // target's sums are those of the sequential loop over its own windows.
-template <int WT, int G, bool DENSE, class Acc, int KERNEL>
-__device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
-                                             unsigned col, const float4 (&t)[G], const int (&cx)[G], int cy,
-                                             int cz, const KParams& kp, Sums<Acc, KERNEL> (&r)[G])
+// Returns the source slots each target is evaluated against (the windows
+// rounded up to whole four-source trips) in the counting copy (COUNT), else 0.
+template <int WT, int G, bool DENSE, class Acc, int KERNEL, bool COUNT = false>
+__device__ __forceinline__ uint32_t direct_group(const InteractArgs& a, const SysDesc& d, uint32_t (*win)[WT],
+                                                 unsigned col, const float4 (&t)[G], const int (&cx)[G], int cy,
+                                                 int cz, const KParams& kp, Sums<Acc, KERNEL> (&r)[G])
 {
     static_assert(G % 2 == 0, "targets go in packed pairs");
     constexpr bool WIDE = G >= 4;
     int nw = 0;
+    uint32_t slots = 0;
     {
         uint32_t ulo[9], uhi[9];
 #pragma unroll
@@ -1462,8 +1465,10 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
                 // a row's sentinel) and adds zeros.  (Measured: faster for
                 // four targets, slower for two, whose extra slot per window
                 // costs more than the wider loads save.)
-                win[2 * nw][col] = WIDE ? ulo[rr] & ~1u : ulo[rr];
+                const uint32_t lo = WIDE ? ulo[rr] & ~1u : ulo[rr];
+                win[2 * nw][col] = lo;
                 win[2 * nw + 1][col] = uhi[rr];
+                if constexpr (COUNT) slots += (uhi[rr] - lo + 3u) & ~3u;
                 ++nw;
             }
     }
@@ -1473,7 +1478,7 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     if (!PI_BOUNDS(a.ctrl, nw > 0 ? 0 : 1, 1, CS_DIRECT_WIN)) {
 #pragma unroll
         for (int k = 0; k < G; ++k) r[k] = Sums<Acc, KERNEL>();
-        return;
+        return 0u;
     }
 #endif
     const float rc2 = d.rc2;
@@ -1516,6 +1521,17 @@ __device__ __forceinline__ void direct_group(const InteractArgs& a, const SysDes
     } while (wa < we);
 #pragma unroll
     for (int k = 0; k < G; ++k) ps[k / 2].to(r[k], (k & 1) != 0);
+    return slots;
+}
+
+// Adds a thread's counted evaluations to the control block (the counting
+// copy of the direct kernels, PI_OPT_COUNT_EVALS: one atomic per thread).
+template <bool COUNT>
+__device__ __forceinline__ void add_evals(const InteractArgs& a, unsigned long long ev)
+{
+    if constexpr (COUNT) {
+        if (ev) atomicAdd(&a.ctrl->evals, ev);
+    }
 }
 
 // The first P slot k0 of this thread's group of `per` consecutive slots
@@ -1538,7 +1554,7 @@ __device__ __forceinline__ void group_slots(const InteractArgs& a, uint32_t per,
 
 // Slots ka and ka + 1 of P below kend (either may be a sentinel or past
 // the end).
-template <int WT, bool DENSE, class Acc, int KERNEL>
+template <int WT, bool DENSE, class Acc, int KERNEL, bool COUNT = false>
 __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t (*win)[WT], unsigned col,
                                                  uint32_t ka, uint32_t kend)
 {
@@ -1571,7 +1587,8 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
         const float4 t[2] = {ta, together ? t1 : ta};
         const int cx[2] = {cxa, together ? cxb : cxa};
         Sums<Acc, KERNEL> r[2];
-        direct_group<WT, 2, DENSE>(a, d, win, col, t, cx, cy, cz, kp, r);
+        const uint32_t slots = direct_group<WT, 2, DENSE, Acc, KERNEL, COUNT>(a, d, win, col, t, cx, cy, cz, kp, r);
+        add_evals<COUNT>(a, (unsigned long long)slots * (together ? 2u : 1u));
         store_out(a, __float_as_uint(ta.w), r[0]);
         if (together) store_out(a, __float_as_uint(t1.w), r[1]);
     }
@@ -1585,18 +1602,18 @@ __device__ __forceinline__ void direct_slot_pair(const InteractArgs& a, uint32_t
         const float4 t[2] = {t1, t1};
         const int cx[2] = {cx1, cx1};
         Sums<Acc, KERNEL> r[2];
-        direct_group<WT, 2, DENSE>(a, d1, win, col, t, cx, cy1, cz1, kp1, r);
+        add_evals<COUNT>(a, direct_group<WT, 2, DENSE, Acc, KERNEL, COUNT>(a, d1, win, col, t, cx, cy1, cz1, kp1, r));
         store_out(a, __float_as_uint(t1.w), r[0]);
     }
 }
 
 // The slot pair with exact window bounds in dense cells, out of line so that
 // the common path keeps its code and registers.
-template <class Acc, int KERNEL>
+template <class Acc, int KERNEL, bool COUNT = false>
 __device__ __noinline__ void direct_slot_pair_dense(const InteractArgs& a, uint32_t (*win)[DIRECT_THREADS],
                                                     unsigned col, uint32_t ka, uint32_t kend)
 {
-    direct_slot_pair<DIRECT_THREADS, true, Acc, KERNEL>(a, win, col, ka, kend);
+    direct_slot_pair<DIRECT_THREADS, true, Acc, KERNEL, COUNT>(a, win, col, ka, kend);
 }
 
 // Resident CTAs per SM the direct kernel's registers are capped for.  The
@@ -1611,8 +1628,9 @@ __host__ __device__ constexpr int direct_min_blocks()
     return (std::is_same<Acc, PlainAcc>::value && (KERNEL == KERNEL_GAUSSIAN || KERNEL == KERNEL_LOWFLOP)) ? 8 : 6;
 }
 
-// Targets of P slots 2p and 2p + 1 per thread.
-template <class Acc, int KERNEL>
+// Targets of P slots 2p and 2p + 1 per thread.  COUNT: the copy that also
+// counts its evaluations (PI_OPT_COUNT_EVALS).
+template <class Acc, int KERNEL, bool COUNT = false>
 __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL>()))
     k_interact_direct(InteractArgs a)
 {
@@ -1632,9 +1650,9 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct_min_blocks<Acc, KERNEL
     uint32_t k0, kend;
     group_slots(a, 2u, k0, kend);
     if (mpc > DENSE_CELL)
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
+        direct_slot_pair_dense<Acc, KERNEL, COUNT>(a, win, threadIdx.x, k0, kend);
     else
-        direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
+        direct_slot_pair<DIRECT_THREADS, false, Acc, KERNEL, COUNT>(a, win, threadIdx.x, k0, kend);
 }
 
 // Resident CTAs per SM the four-target direct kernel's registers are capped
@@ -1652,7 +1670,7 @@ __host__ __device__ constexpr int direct4_min_blocks()
 // X-row of one system unless some are sentinels (every row ends in
 // ROW_PADS of them), which repeat a real target and store nothing.  Grids
 // with dense cells take the slot pairs' dense path.
-template <class Acc, int KERNEL>
+template <class Acc, int KERNEL, bool COUNT = false>
 __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNEL>()))
     k_interact_direct4(InteractArgs a)
 {
@@ -1671,8 +1689,8 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     group_slots(a, 4u, k0, kend);
     if (k0 >= kend) return;
     if (mpc > DENSE_CELL) {
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0, kend);
-        direct_slot_pair_dense<Acc, KERNEL>(a, win, threadIdx.x, k0 + 2u, kend);
+        direct_slot_pair_dense<Acc, KERNEL, COUNT>(a, win, threadIdx.x, k0, kend);
+        direct_slot_pair_dense<Acc, KERNEL, COUNT>(a, win, threadIdx.x, k0 + 2u, kend);
         return;
     }
     constexpr uint32_t NONE = 0xffffffffu;
@@ -1699,10 +1717,20 @@ __global__ void __launch_bounds__(DIRECT_THREADS, (direct4_min_blocks<Acc, KERNE
     const int cz = axis_cell(tf.z, g.lo[2], g.inv_w[2], g.n[2]);
     const KParams kp = kparams(a, sid);
     Sums<Acc, KERNEL> r[4];
-    direct_group<DIRECT_THREADS, 4, false>(a, d, win, threadIdx.x, t, cx, cy, cz, kp, r);
+    const uint32_t slots =
+        direct_group<DIRECT_THREADS, 4, false, Acc, KERNEL, COUNT>(a, d, win, threadIdx.x, t, cx, cy, cz, kp, r);
+    add_evals<COUNT>(a, (unsigned long long)slots * ((v[0] ? 1u : 0u) + (v[1] ? 1u : 0u) + (v[2] ? 1u : 0u) +
+                                              (v[3] ? 1u : 0u)));
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (v[k]) store_out(a, __float_as_uint(t[k].w), r[k]);
+}
+
+// The forms with a counting copy of the direct kernels (PI_OPT_COUNT_EVALS).
+template <class Acc, int KERNEL>
+constexpr bool counted_form()
+{
+    return std::is_same<Acc, PlainAcc>::value && (KERNEL == KERNEL_GAUSSIAN || KERNEL == KERNEL_GAUSSIAN_FINE);
 }
 
 // Blocks of a direct launch: over all of P, or a.range_blocks for a launch
@@ -1718,6 +1746,15 @@ template <class Acc, int KERNEL>
 void launch_direct4_one(const InteractArgs& a, cudaStream_t s)
 {
     // an error is left for cudaGetLastError
+    // the counting copy exists for the plain Gaussian sums (the windows, and
+    // so the count, do not depend on the kernel K or the precision)
+    if constexpr (counted_form<Acc, KERNEL>()) {
+        if (a.count_evals) {
+            (void)launch_dependent(k_interact_direct4<Acc, KERNEL, true>, dim3(direct_grid(a, 4)),
+                                   dim3(DIRECT_THREADS), 0, s, a);
+            return;
+        }
+    }
     (void)launch_dependent(k_interact_direct4<Acc, KERNEL>, dim3(direct_grid(a, 4)), dim3(DIRECT_THREADS), 0, s, a);
 }
 
@@ -1725,6 +1762,13 @@ template <class Acc, int KERNEL>
 void launch_direct_one(const InteractArgs& a, cudaStream_t s)
 {
     // an error is left for cudaGetLastError
+    if constexpr (counted_form<Acc, KERNEL>()) {
+        if (a.count_evals) {
+            (void)launch_dependent(k_interact_direct<Acc, KERNEL, true>, dim3(direct_grid(a, 2)),
+                                   dim3(DIRECT_THREADS), 0, s, a);
+            return;
+        }
+    }
     (void)launch_dependent(k_interact_direct<Acc, KERNEL>, dim3(direct_grid(a, 2)), dim3(DIRECT_THREADS), 0, s, a);
 }
 

@@ -47,8 +47,9 @@ struct Ctrl {
     uint32_t check_site;    // debug builds: the first failed bounds check (CheckSite)
     uint32_t pad0;
     unsigned long long ovf; // bucketed binning: overflow buckets, count << 40 | their particles
+    unsigned long long evals; // direct kernels: target-source evaluations (PI_OPT_COUNT_EVALS)
     uint32_t tickets[3];    // scan tile tickets of a step's second to fourth scans (radix binning)
-    uint32_t pad[51];       // the control block is 256 bytes
+    uint32_t pad[49];       // the control block is 256 bytes
 };
 
 // Grid geometry.  inv_w[d] = fl32(n[d] / (hi[d] - lo[d])) computed in FP64.
@@ -483,6 +484,7 @@ struct InteractArgs {
     const uint32_t* rblock;
     int nranges;
     unsigned range_blocks;
+    int count_evals;        // direct kernels: add their evaluations to ctrl->evals
 };
 
 // Each adds the number of kernels it launched to *launches.

@@ -55,3 +55,22 @@ def test_host_side_argument_checks():
     assert L.pi_bin(None, None, None, None, 0, None) == binding.PI_ERR_INVALID_ARG
     assert L.pi_interact(None, 1.0, None, None, None, None, None, 0, None) == binding.PI_ERR_INVALID_ARG
     assert L.pi_destroy(None) == binding.PI_OK
+
+
+def test_destroyed_handles_are_refused_before_the_library_sees_them():
+    """A context or server handle passes as its pointer until it is
+    destroyed; afterwards the binding refuses it, so no call hands freed
+    memory to the library (checked against a host C function)."""
+    libc = ctypes.CDLL(None)
+    libc.strlen.argtypes = [ctypes.c_void_p]
+    libc.strlen.restype = ctypes.c_size_t
+    buf = ctypes.create_string_buffer(b"seven!!")
+    h = binding.Handle(ctypes.addressof(buf), "context")
+    assert libc.strlen(h) == 7
+    h._close()
+    try:
+        libc.strlen(h)
+    except ctypes.ArgumentError as e:
+        assert "destroyed" in str(e)
+    else:
+        raise AssertionError("a destroyed handle was passed on")
