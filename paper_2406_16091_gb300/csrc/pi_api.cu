@@ -653,7 +653,7 @@ pi_status pi_batch_bin(pi_ctx* ctx, const float* x, const float* y, const float*
                                        ctx->sy, ctx->sz, ctx->ctrl, ctx->num_sms, s));
         PI_TRY(pi::launch_radix_rank(keys[fin], nn, sy, C, ctx->offsets, ctx->perm, ctx->sx, ctx->sy, ctx->sz,
                                      ctx->counts, ctx->P, ctx->xbins, ctx->ctrl, ctx->num_sms, s));
-        ctx->launches += 5 + 3 * (rp.passes - 1);
+        ctx->launches += 3 * rp.passes + 3;  // zero, keys, per pass (count,) scan, split, gather, rank
         ctx->n = total;
         ctx->binned = 1;
         return PI_OK;

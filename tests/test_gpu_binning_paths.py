@@ -94,3 +94,29 @@ def test_binning_repeats_and_recovers_after_an_error(path):
     bad[17] = np.float32(1.5)
     g = run_gpu(bad, y, z, w.lo, w.hi, w.rc, w.h, binning=path)
     assert g["status"] == B.PI_ERR_OUT_OF_BOX
+
+
+@pytest.mark.parametrize("name,path,launches", [
+    ("small", B.PI_BIN_PER_PARTICLE, 5),        # zero, hist, scan, scatter, stabilise
+    ("small", B.PI_BIN_BUCKETED, 6),            # zero, count, scan, scatter, cells, big
+    ("one_digit_pass", B.PI_BIN_RADIX, 6),      # zero, keys, scan, split, gather, rank
+    ("small", B.PI_BIN_RADIX, 9),               # 2^12 cells: two digit passes
+    ("three_digit_passes", B.PI_BIN_RADIX, 12),
+])
+def test_launch_count_per_binning_path(name, path, launches):
+    """pi_launch_count (the bench's gpu_launches) adds exactly the kernels
+    each binning path launches."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    x, y, z, lo, hi, rc, h = CASES[name]()
+    s = torch.cuda.current_stream()
+    ctx = B.pi_create(lo, hi, rc, len(x))
+    try:
+        B.pi_set_option(ctx, B.PI_OPT_BINNING, path)
+        t = [torch.from_numpy(a).to(dev) for a in (x, y, z)]
+        before = B.pi_launch_count(ctx)
+        B.pi_bin(ctx, *t, len(x), s)
+        assert B.pi_launch_count(ctx) - before == launches
+        assert B.pi_sync_status(ctx, s)[0] == B.PI_OK
+    finally:
+        B.pi_destroy(ctx)
