@@ -125,8 +125,9 @@ enum {
      * pi_eval_count reads; 0 (default) counts nothing.  The copy exists for
      * the Gaussian kernel in PI_PREC_FP32 (the windows, and so the count,
      * depend on the positions and r_c only); other kernels, the Kahan mode,
-     * the staged shapes and Alg. 1 count nothing.  The count restarts at
-     * every pi_bin.  Results do not depend on it. */
+     * the staged shapes, Alg. 1 and pi_autotune's timed trials count
+     * nothing.  The count restarts at every pi_bin.  Results do not depend
+     * on it. */
     PI_OPT_COUNT_EVALS = 8
 };
 enum { PI_TILE_AUTO = -1 };

@@ -919,7 +919,7 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
     DeviceScope ds(ctx->device);
     if (ds.err != cudaSuccess) return cuda_fail(ds.err, "pi_autotune: set device");
     cudaStream_t st = (cudaStream_t)stream;
-    const int saved_algo = ctx->algo, saved_tile = ctx->tile;
+    const int saved_algo = ctx->algo, saved_tile = ctx->tile, saved_count = ctx->count_evals;
     const std::vector<int> saved_plan = ctx->sys_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PI_TRY(cudaEventCreate(&e0));
@@ -929,6 +929,7 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
         return cuda_fail(ce, "pi_autotune: event");
     }
     pi_status result = PI_OK;
+    ctx->count_evals = 0;  // the trials time the ordinary kernels and count nothing
     // median milliseconds of the interaction as the context stands: one
     // untimed run, then `reps` timed ones
     auto median_ms = [&](float& med) {
@@ -1001,6 +1002,7 @@ pi_status pi_autotune(pi_ctx* ctx, const float* h, float* S, float* Vx, float* V
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->count_evals = saved_count;
     if (result != PI_OK || best_c < 0) {
         ctx->algo = saved_algo;
         ctx->tile = saved_tile;
