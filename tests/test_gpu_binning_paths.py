@@ -58,6 +58,8 @@ CASES = {
     "three_digit_passes": lambda: (*W.uniform(150000, 8), (0, 0, 0), (1, 1, 1), 1.0 / 81, 1.0 / 162),
     # 4^3 cells: one radix pass of 6 bits
     "one_digit_pass": lambda: (*W.uniform(30000, 9), (0, 0, 0), (1, 1, 1), 0.25, 0.125),
+    # the bench's workload at full size (2,097,152 particles, 64^3 cells)
+    "scale_full": lambda: _workload(W.SCALE),
 }
 
 PATHS = (B.PI_BIN_RADIX, B.PI_BIN_BUCKETED, B.PI_BIN_PER_PARTICLE)
